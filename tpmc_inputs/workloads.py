@@ -1,0 +1,117 @@
+"""Seeded synthetic TPMC workloads: free-stream states, attitudes and seeds.
+
+The paper's verification runs (§III.C) use T_inf = 922 K, T_W = 300 K and
+1e7 particles per case; the workloads below follow the benchmark
+configurations (atomic oxygen, T_inf = 1000 K) and also keep the paper's
+922 K case.  Nothing here computes any part of the method: these are the
+inputs both the oracle and the CUDA library receive.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import meshes
+
+AMU = 1.66053906660e-27  # kg
+K_B = 1.380649e-23       # J/K
+M_OXYGEN = 16.0 * AMU
+
+
+def stream_speed(S: float, T_inf: float, m: float = M_OXYGEN) -> float:
+    """Bulk speed V that gives the speed ratio S = V / sqrt(2 k T / m) (Nomenclature)."""
+    return S * math.sqrt(2.0 * K_B * T_inf / m)
+
+
+def base_state(S=7.5, T_inf=1000.0, T_W=300.0, n=1.0e15, m=M_OXYGEN):
+    return dict(n=n, T_inf=T_inf, m=m, V=stream_speed(S, T_inf, m), T_W=T_W)
+
+
+def icosphere_case(N=100_000, seed=20131213):
+    """Sphere R = 1 m as a 1,280-triangle icosphere in a CV of radius 1.5 m; S = 7.5; diffuse; FP64."""
+    xyz, tri = meshes.icosphere(3, 1.0)
+    st = base_state(S=7.5)
+    return dict(name="icosphere-1280-S7.5-fp64", xyz=xyz, tri=tri, N=N,
+                params=dict(**st, dir=(0.0, 0.0, 1.0), eps_diffuse=1.0, A_ref=math.pi, ref_point=(0, 0, 0),
+                            r_cv=1.5, center=(0, 0, 0), max_bounces=64, seed=seed),
+                precision="fp64")
+
+
+def plate_alpha_dir(alpha_rad: float):
+    """Flow direction making angle alpha with the plate normal (+z), in the x-z plane."""
+    return (math.sin(alpha_rad), 0.0, -math.cos(alpha_rad))
+
+
+def cylinder_alpha_dir(alpha_rad: float):
+    """Flow direction making angle alpha with the cylinder axis (+z), in the x-z plane."""
+    return (math.sin(alpha_rad), 0.0, -math.cos(alpha_rad))
+
+
+def sweep_cases(shape: str, N_each=10_000_000, n_alpha=32, S_values=(2.0, 5.0, 10.0), eps_values=(0.0, 1.0)):
+    """Plate (2 triangles) or closed cylinder (4,096 triangles) over alpha in [0, 90] deg x S x GSI.
+
+    Returns (xyz, tri, list of case dicts).  Seeds: 1000 + case index.
+    """
+    if shape == "plate":
+        xyz, tri = meshes.plate(1.0)
+        A_ref = 1.0
+        dir_fn = plate_alpha_dir
+    elif shape == "cylinder":
+        xyz, tri = meshes.cylinder(0.5, 2.0, 128, 15)
+        A_ref = 2.0 * 0.5 * 2.0
+        dir_fn = cylinder_alpha_dir
+    else:
+        raise ValueError(shape)
+    c, rb = meshes.bounding_sphere(xyz)
+    cases = []
+    k = 0
+    for eps in eps_values:
+        for S in S_values:
+            for i in range(n_alpha):
+                alpha = math.radians(90.0 * i / (n_alpha - 1))
+                st = base_state(S=S)
+                cases.append(dict(alpha=alpha, S=S, eps=eps, N=N_each,
+                                  params=dict(**st, dir=dir_fn(alpha), eps_diffuse=eps, A_ref=A_ref,
+                                              ref_point=(0, 0, 0), r_cv=1.05 * rb, center=tuple(c),
+                                              max_bounces=64, seed=1000 + k)))
+                k += 1
+    return xyz, tri, cases
+
+
+def satellite_case(N=100_000_000, target_triangles=60_000, seed=7):
+    """Concave synthetic satellite, flow -x into the dish, Maxwell 0.9 diffuse, S = 7."""
+    xyz, tri = meshes.satellite(target_triangles)
+    c, rb = meshes.bounding_sphere(xyz)
+    st = base_state(S=7.0)
+    return dict(name=f"satellite-{tri.shape[0]}-S7", xyz=xyz, tri=tri, N=N,
+                params=dict(**st, dir=(-1.0, 0.0, 0.0), eps_diffuse=0.9, A_ref=2.0, ref_point=(0, 0, 0),
+                            r_cv=1.05 * rb, center=tuple(c), max_bounces=64, seed=seed),
+                precision="fp32")
+
+
+def attitude_grid(n_yaw=32, n_pitch=32):
+    """Yaw, pitch over a 32 x 32 grid of [-90, 90) deg; flow into the body along -(cos p cos y, cos p sin y, sin p)."""
+    dirs = []
+    for i in range(n_yaw):
+        yaw = math.radians(-90.0 + 180.0 * i / n_yaw)
+        for j in range(n_pitch):
+            pitch = math.radians(-90.0 + 180.0 * j / n_pitch)
+            dirs.append((-math.cos(pitch) * math.cos(yaw), -math.cos(pitch) * math.sin(yaw), -math.sin(pitch)))
+    return np.array(dirs, dtype=np.float64)
+
+
+def serving_stream(n_queries=1000, rate_per_s=100.0, seed=1, N_range=(1e5, 1e8)):
+    """Poisson arrivals with log-uniform particle counts, random attitudes and S ~ U[3, 12]."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate_per_s, n_queries)
+    t = np.cumsum(gaps)
+    lo, hi = math.log(N_range[0]), math.log(N_range[1])
+    N = np.exp(rng.uniform(lo, hi, n_queries)).astype(np.int64)
+    v = rng.normal(size=(n_queries, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    S = rng.uniform(3.0, 12.0, n_queries)
+    mesh_idx = rng.integers(0, 4, n_queries)
+    seeds = rng.integers(1, 2**63 - 1, n_queries, dtype=np.int64)
+    return [dict(t_arrival=float(t[i]), N=int(N[i]), dir=tuple(v[i]), S=float(S[i]), mesh=int(mesh_idx[i]),
+                 seed=int(seeds[i])) for i in range(n_queries)]
