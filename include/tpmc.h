@@ -1,0 +1,226 @@
+/*
+ * tpmc.h -- C ABI of the GB300 test-particle Monte Carlo (TPMC) library.
+ *
+ * The library computes the free-molecular force, torque and drag coefficient
+ * of a triangulated body by the method of Parham & Barba, "Finding the Force
+ * -- Consistent Particle Seeding for Satellite Aerodynamics" (arXiv 1312.3691):
+ *
+ *   1. free-stream particles are seeded on a spherical control volume (CV)
+ *      with the number flux of Eq. 10, the latitude law g(phi|S) of Eq. 11,
+ *      the velocity component laws of Eq. 14a-c, and the Rodrigues rotation
+ *      of Eq. 15 into body coordinates (§III.A);
+ *   2. each particle is ray traced to its closest hit on the surface, re-emitted
+ *      by the gas-surface interaction model and traced again until it leaves
+ *      (multiple reflections and self-shadowing, §II.A);
+ *   3. the momentum differences, scaled by the particle weight Gamma/N times
+ *      the molecular mass (§II.A), sum to the force; C_D follows Eq. 1.
+ *
+ * Conventions for every entry point:
+ *   - every call returns a tpmc_status; nothing aborts or throws across the ABI;
+ *   - pointers named h_* or documented "host" are host memory, d_* are device
+ *     memory of the context's GPU; the caller owns every buffer it passes;
+ *   - inputs are copied; meshes and their BVHs are owned by the context until
+ *     tpmc_mesh_unload or tpmc_destroy;
+ *   - a failed call leaves the context usable and sets tpmc_last_error();
+ *   - calls on one context are serialised by an internal mutex (thread safe);
+ *     GPU work runs on the context's stream (tpmc_set_stream).
+ *
+ * Units: SI (m, s, kg, K, N, N m).  Velocities inside the library are in
+ * units of the most probable thermal speed c_mp = sqrt(2 k_B T_inf / m).
+ */
+#ifndef TPMC_H
+#define TPMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TPMC_OK = 0,
+  TPMC_EINVAL = 1,     /* invalid argument (non-finite, out of range, bad mesh) */
+  TPMC_ENOMEM = 2,     /* device memory or the context's memory budget exhausted */
+  TPMC_EBUSY = 3,      /* serving queue full: retry after a poll */
+  TPMC_ETIMEOUT = 4,   /* tpmc_poll: the query has not finished within the timeout */
+  TPMC_ECUDA = 5,      /* a CUDA runtime call failed (message in tpmc_last_error) */
+  TPMC_ENOTFOUND = 6   /* unknown mesh id or query id */
+} tpmc_status;
+
+typedef struct tpmc_ctx tpmc_ctx;
+typedef uint32_t tpmc_mesh_id;
+typedef uint64_t tpmc_query_id;
+
+/* Arithmetic of the per-particle path.  FP32: seeding, traversal, intersection
+ * and re-emission in float; FP64 only for the flux normalisation (set-up) and
+ * the final force/C_D reduction.  FP64: everything in double. */
+enum { TPMC_FP32 = 0, TPMC_FP64 = 1 };
+
+/* One free-molecular query (§II.A; §III.C; Table 1 of the paper). */
+typedef struct {
+  double n;             /* free-stream number density, 1/m^3 (> 0)                      */
+  double T_inf;         /* free-stream temperature, K (> 0)                             */
+  double m;             /* molecular mass, kg (> 0)                                     */
+  double V;             /* bulk speed, m/s (> 0); S = V / c_mp is derived, never passed */
+  double dir[3];        /* flow direction in body coordinates (normalised by the library) */
+  double T_W;           /* wall temperature, K (> 0)                                    */
+  double eps_diffuse;   /* Maxwell accommodation: fraction re-emitted diffusely, [0,1]  */
+  double A_ref;         /* C_D reference area, m^2 (> 0)                                */
+  double ref_point[3];  /* torque reference point, m                                    */
+  double r_cv;          /* CV radius, m; <= 0: 1.05 x the mesh's bounding radius       */
+  double center[3];     /* CV centre, m (ignored when r_cv <= 0: bounding-sphere centre) */
+  uint32_t max_bounces; /* hits per particle before it is stopped (>= 1), e.g. 64      */
+  uint32_t precision;   /* TPMC_FP32 or TPMC_FP64                                       */
+  uint64_t seed;        /* Philox key                                                   */
+  uint32_t stream_id;   /* Philox counter word 2 (distinguishes runs sharing a seed)   */
+  uint32_t want_panels; /* 1: keep per-triangle loads for tpmc_panels                   */
+} tpmc_params;
+
+/* Result of one query.  force/torque in N and N m; CD = force . Vhat / (q_inf A_ref). */
+typedef struct {
+  double force[3], torque[3];
+  double CD, CD_sigma;          /* C_D and its Monte Carlo standard error               */
+  double S, S_W;                /* speed ratios V/c_mp and V/c_W                        */
+  double gamma;                 /* molecules per second entering the CV (Eq. 10)        */
+  double weight;                /* molecules per second per simulated particle (Gamma/N) */
+  double q_inf;                 /* dynamic pressure n m V^2 / 2, Pa                     */
+  double c_mp;                  /* most probable thermal speed, m/s                     */
+  double r_cv, center[3];       /* control volume used                                  */
+  double fixed_quantum;         /* value of one unit of the int64 sums (c_mp units)     */
+  int64_t sum_dv_q[3];          /* sum over hits of (v_in - v_out), fixed point         */
+  int64_t sum_rdv_q[3];         /* sum over hits of (r_hit - ref) x (v_in - v_out)      */
+  uint64_t n_particles, n_hits, n_hit_particles, n_truncated;
+  uint64_t n_node_visits, n_tri_tests; /* traversal work (counted when enabled)         */
+  tpmc_query_id query_id;       /* handle for tpmc_panels (want_panels = 1)             */
+  double ms;                    /* wall time of the call or, when served, latency       */
+  int32_t status;               /* tpmc_status of this query                            */
+  int32_t pad_;
+} tpmc_result;
+
+/* Per-particle records for verification (host buffers, each may be NULL). */
+typedef struct {
+  double* pos;          /* [N][3] seeded position, body frame, m                        */
+  double* vel;          /* [N][3] seeded velocity, c_mp units                           */
+  double* dv;           /* [N][3] sum over the particle's hits of (v_in - v_out)        */
+  uint32_t* n_hits;     /* [N] hits of the particle                                     */
+  uint32_t* truncated;  /* [N] 1 when stopped at max_bounces                            */
+  uint32_t* tri;        /* [N][K] triangle index of hit b (b < K), 0xFFFFFFFF after     */
+  uint32_t K;           /* hits recorded per particle (<= 64)                           */
+} tpmc_records;
+
+typedef struct {
+  uint32_t n_tri, n_vert, n_nodes, depth;
+  uint32_t n_skipped;           /* zero-area triangles (never hit)                      */
+  uint32_t leaf_max;            /* largest leaf                                          */
+  double bound_center[3], bound_radius;
+  uint64_t device_bytes;
+} tpmc_mesh_stats;
+
+/* Launch schedule of the trace kernel (chosen by tpmc_tune or set by hand). */
+typedef struct {
+  uint32_t block;               /* threads per block (multiple of 32)                   */
+  uint32_t blocks_per_sm;       /* resident blocks per SM (grid = SMs x this)           */
+  uint32_t chunk;               /* particle ids a warp takes per fetch (0: automatic)   */
+  uint32_t smem_nodes;          /* BVH nodes staged in shared memory                    */
+} tpmc_launch;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Creates a context on CUDA device `device` that may hold at most
+ * mem_budget_bytes of device memory (0: 90 % of the free memory).
+ * Errors: EINVAL (bad device), ECUDA. */
+tpmc_status tpmc_create(int device, size_t mem_budget_bytes, tpmc_ctx** out);
+
+/* Waits for the context's work, frees everything it owns. NULL is a no-op. */
+tpmc_status tpmc_destroy(tpmc_ctx* ctx);
+
+/* Makes later GPU work run on `cuda_stream` (a cudaStream_t; NULL = the
+ * context's own stream).  The caller keeps the stream alive. */
+tpmc_status tpmc_set_stream(tpmc_ctx* ctx, void* cuda_stream);
+
+/* Thread-local message describing the last failure on this thread. */
+const char* tpmc_last_error(const tpmc_ctx* ctx);
+
+/* Enables (1) or disables (0) the traversal counters n_node_visits and
+ * n_tri_tests in later results. */
+tpmc_status tpmc_set_counters(tpmc_ctx* ctx, int enable);
+
+/* ---- geometry (§II.A: "satellite surfaces are represented by a triangulation") */
+
+/* Copies the mesh (xyz: host [n_vert][3] m; tri: host [n_tri][3] vertex
+ * indices), builds its bounding-volume hierarchy on the host and keeps both on
+ * the device.  Triangles are two-sided; the winding fixes the sign of the
+ * geometric normal used for panel pressure.  Zero-area triangles are kept in
+ * the numbering but never hit (counted in tpmc_mesh_stats.n_skipped).
+ * Errors: EINVAL (n_vert = 0 with n_tri > 0, index out of range, non-finite
+ * coordinate, n_tri > 2^24), ENOMEM. */
+tpmc_status tpmc_mesh_load(tpmc_ctx* ctx, const double* xyz, uint32_t n_vert, const uint32_t* tri,
+                           uint32_t n_tri, tpmc_mesh_id* out);
+tpmc_status tpmc_mesh_unload(tpmc_ctx* ctx, tpmc_mesh_id mesh);
+tpmc_status tpmc_mesh_info(tpmc_ctx* ctx, tpmc_mesh_id mesh, tpmc_mesh_stats* out);
+
+/* ---- the hot path ------------------------------------------------------- */
+
+/* Traces N particles of one query and returns its result (host), blocking.
+ * Particle ids 0..N-1 index the Philox counters, so the result depends only
+ * on (mesh, params, N), never on the schedule.
+ * Errors: EINVAL (non-finite or non-positive n, T_inf, m, V, T_W, A_ref; eps
+ * outside [0,1]; zero dir; max_bounces = 0; N = 0 or N > 2^34; a mesh vertex
+ * outside the given CV; a fixed-point overflow bound that no quantum >= 2^-40
+ * satisfies), ENOTFOUND, ENOMEM, ECUDA. */
+tpmc_status tpmc_trace(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* params, uint64_t N,
+                       tpmc_result* out);
+
+/* Per-triangle pressure and shear of a finished query run with want_panels:
+ * pressure_i = -F_i . n_i / A_i, shear_i = |F_i - (F_i . n_i) n_i| / A_i
+ * (Pa; n_i the geometric unit normal, F_i the force on triangle i).  Host
+ * buffers of n_tri doubles (either may be NULL).  Releases the query's panel
+ * memory.  Errors: ENOTFOUND, EINVAL (n_tri mismatch). */
+tpmc_status tpmc_panels(tpmc_ctx* ctx, tpmc_query_id query, double* pressure, double* shear, uint32_t n_tri);
+
+/* Same as tpmc_trace and also fills per-particle records (verification).
+ * Errors as tpmc_trace, plus EINVAL for K > 64 or N > 2^26. */
+tpmc_status tpmc_trace_records(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* params, uint64_t N,
+                               tpmc_records* records, tpmc_result* out);
+
+/* Batched sweep: K queries that differ from `base` only in flow direction and
+ * speed ratio, in one persistent launch.  h_dirs: host [K][3]; h_S: host [K]
+ * speed ratios (V = S c_mp); item k uses stream_id = base->stream_id + k.
+ * Per-panel loads are not kept.  Results in h_out[K].
+ * Errors as tpmc_trace; EINVAL for K = 0. */
+tpmc_status tpmc_sweep(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* base, const double* h_dirs,
+                       const double* h_S, uint32_t K, uint64_t N_each, tpmc_result* h_out);
+
+/* Device-resident form of tpmc_sweep: d_dirs, d_S and d_out are device
+ * buffers; the call only enqueues work on the context's stream and returns.
+ * Per-item input errors are reported in d_out[k].status. */
+tpmc_status tpmc_sweep_device(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* base, const double* d_dirs,
+                              const double* d_S, uint32_t K, uint64_t N_each, tpmc_result* d_out);
+
+/* ---- serving: continuous batching over resident meshes -------------------- */
+
+/* Queues a query; a scheduler thread admits it when a slot and memory are
+ * free and traces it in launches shared with the other queries in flight.
+ * Errors: EINVAL/ENOTFOUND as tpmc_trace, EBUSY when the queue is full. */
+tpmc_status tpmc_submit(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* params, uint64_t N,
+                        tpmc_query_id* out);
+
+/* Waits up to timeout_ms (0: do not wait; < 0: forever) for a submitted query
+ * and returns its result (out->ms is the latency from submit to completion).
+ * Errors: ETIMEOUT (not finished; poll again), ENOTFOUND. */
+tpmc_status tpmc_poll(tpmc_ctx* ctx, tpmc_query_id query, int timeout_ms, tpmc_result* out);
+
+/* ---- schedule ------------------------------------------------------------ */
+
+/* Measures candidate schedules on `mesh` with short launches and keeps the
+ * fastest for meshes of its size class and this precision. */
+tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* params, uint64_t N_trial,
+                      tpmc_launch* best);
+tpmc_status tpmc_set_launch(tpmc_ctx* ctx, const tpmc_launch* cfg);
+tpmc_status tpmc_get_launch(tpmc_ctx* ctx, tpmc_mesh_id mesh, uint32_t precision, tpmc_launch* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPMC_H */

@@ -66,9 +66,11 @@ void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-// Word -> uniform on (0,1): the top 24 bits plus one half, times 2^-24.
-// Exact in both float and double, never 0 and never 1.
-double uniform_from_word(uint32_t w) { return ((double)(w >> 8) + 0.5) * 0x1p-24; }
+// Word -> uniform on (0,1): the top 23 bits plus one half, times 2^-23, i.e.
+// (2k+1) 2^-24 with 2k+1 < 2^24.  It is exactly representable in float as well
+// as double, so a float consumer and a double consumer see the same number;
+// never 0 and never 1 (range [2^-24, 1 - 2^-24]).
+double uniform_from_word(uint32_t w) { return ((double)(w >> 9) + 0.5) * 0x1p-23; }
 
 // Draw layout (the paper uses "random" draws without naming a generator):
 //   key     = (seed low 32 bits, seed high 32 bits)
@@ -176,7 +178,7 @@ double normal_speed_cdf(double x, double s) {
 }
 
 double normal_speed_inverse(double u, double s) {
-  const double hi = std::max(s, 0.0) + 12.0;  // F(hi) = 1 to far below 2^-25
+  const double hi = std::max(s, 0.0) + 12.0;  // 1 - F(hi) is far below the smallest uniform, 2^-24
   return bisect_cdf([s](double x) { return normal_speed_cdf(x, s); }, u, 0.0, hi);
 }
 

@@ -33,10 +33,15 @@ def test_philox_known_answers(orc):
 
 
 def test_uniform_mapping(orc):
-    assert orc.uniform(0) == 2.0 ** -25
-    assert orc.uniform(0xFFFFFFFF) == 1.0 - 2.0 ** -25
-    assert orc.uniform(0x100) == 1.5 * 2.0 ** -24
-    assert orc.uniform(0xFF) == 2.0 ** -25  # low 8 bits are dropped
+    assert orc.uniform(0) == 2.0 ** -24
+    assert orc.uniform(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+    assert orc.uniform(0x200) == 1.5 * 2.0 ** -23
+    assert orc.uniform(0x1FF) == 2.0 ** -24  # low 9 bits are dropped
+    # every value is exactly representable in float32
+    rng = np.random.default_rng(0)
+    for w in list(rng.integers(0, 2 ** 32, 2000)) + [0, 2 ** 31, 2 ** 32 - 1]:
+        u = orc.uniform(int(w))
+        assert float(np.float32(u)) == u
 
 
 # ------------------------------------------------------------------ Gamma
@@ -105,7 +110,7 @@ def test_position_cdf_matches_quadrature_and_inverts(orc, S):
     for x in [-0.9, -0.3, 0.0, 0.2, 0.6, 0.95]:
         val, _ = integrate.quad(lambda y: orc.h_x(y, S), -1.0, x, epsabs=1e-15, epsrel=1e-12, limit=200)
         assert abs(orc.position_cdf(x, S) - val) < 1e-12
-    for u in [2.0 ** -25, 1e-4, 0.004, 0.3, 0.5, 0.9, 1 - 2.0 ** -25]:
+    for u in [2.0 ** -24, 1e-4, 0.004, 0.3, 0.5, 0.9, 1 - 2.0 ** -24]:
         x = orc.position_inverse(u, S)
         assert -1.0 <= x <= 1.0
         assert abs(orc.position_cdf(x, S) - u) < 1e-14
@@ -124,7 +129,7 @@ def test_normal_speed_normaliser_and_cdf(orc, s):
     for x in [0.05, 0.5, 1.0, max(s, 0) + 0.3, max(s, 0) + 2.0]:
         val, _ = integrate.quad(lambda y: orc.normal_speed_pdf(y, s), 0, x, epsabs=1e-15, epsrel=1e-12, limit=400)
         assert abs(orc.normal_speed_cdf(x, s) - val) < 1e-9
-    for u in [2.0 ** -25, 0.01, 0.5, 0.99, 1 - 2.0 ** -25]:
+    for u in [2.0 ** -24, 0.01, 0.5, 0.99, 1 - 2.0 ** -24]:
         x = orc.normal_speed_inverse(u, s)
         assert x > 0
         assert abs(orc.normal_speed_cdf(x, s) - u) < 1e-12
