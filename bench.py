@@ -1,0 +1,421 @@
+#!/usr/bin/env python3
+"""Benchmark of the TPMC hot path on GB300.
+
+Workload (one step): the plate / closed-cylinder sweep -- a 1 x 1 m plate
+(2 triangles) and a closed cylinder R = 0.5 m, L = 2 m (4,096 triangles), each
+over 32 angles of attack in [0, 90] deg x S in {2, 5, 10} x {specular, diffuse}
+re-emission, 1e7 particles per case (384 cases, 3.84e9 particles), atomic
+oxygen at T_inf = 1000 K, T_W = 300 K, FP32 traversal with FP64 set-up and
+reduction.  One step is four batched sweep launches (mesh x re-emission), each
+covering 96 cases in one persistent launch.
+
+value: traced particles per second with meshes resident on the device (CUDA
+events around each step on the launching stream; a 256 MiB L2 flush between
+steps, outside the timed intervals).  e2e: the same metric through the public
+API with host buffers (mesh upload and BVH build, host inputs, host results).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from tpmc_inputs import workloads as W  # noqa: E402
+
+METRIC = "traced particles/s on 1 GB300 (% roofline); C_D err vs oracle; serve p50/p99 ms"
+UNIT = "particles/s"
+WORKLOAD = "plate(2 tri)+cylinder(4096 tri) sweep: 32 alpha x S{2,5,10} x {specular,diffuse}, 1e7 particles/case"
+N_EACH = 10_000_000
+FP32_LANES_PER_SM = 128
+# Algorithmic FP32 work per unit (FMA = 2 flops; add, mul, min, max, compare = 1).
+FLOPS_PER_NODE_VISIT = 50    # two child boxes: 6 FMA + 6 min/max + 6 min/max + 1 compare each
+FLOPS_PER_TRI_TEST = 45      # watertight test: 9 sub, 6 FMA, 9 mul/sub, 5 det/T, signs, 1 div
+FLOPS_PER_PARTICLE = 300     # seeding: two inverse-CDF solves, Box-Muller, rotations
+FLOPS_PER_HIT = 60           # re-emission, momentum difference, torque, quantisation
+# DRAM bytes per trace launch from an ncu capture, valid only for the kernel
+# source it was taken on (keyed by the SHA-256 of kernels.cu).
+TRACE_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    with open(os.path.join(ROOT, "paper_1312_3691_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def groups():
+    """The four sweep groups of one step: (shape, eps, xyz, tri, base params, dirs[96], S[96])."""
+    out = []
+    for shape in ("plate", "cylinder"):
+        for eps in (0.0, 1.0):
+            xyz, tri, cases = W.sweep_cases(shape, N_each=N_EACH, eps_values=(eps,))
+            dirs = np.array([c["params"]["dir"] for c in cases])
+            S = np.array([c["S"] for c in cases])
+            base = dict(cases[0]["params"])
+            out.append(dict(shape=shape, eps=eps, xyz=xyz, tri=tri, base=base, dirs=dirs, S=S, cases=cases))
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------- CPU side
+def cpu_baseline_and_cd_error(results_by_group, budget_s=12.0):
+    """The FP64 oracle timed on the host cores on a bounded sample of the same
+    workload, and the C_D error of the GPU results against the oracle's exact
+    (panel-sum) expectation for every case."""
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    gs = groups()
+    rates = {}
+    sample_desc = []
+    for shape, per_case in (("plate", 250_000), ("cylinder", 60_000)):
+        t_total, n_total = 0.0, 0
+        for g in gs:
+            if g["shape"] != shape:
+                continue
+            om = oracle.Mesh(g["xyz"], g["tri"])
+            for ci in (10, 50):
+                c = g["cases"][ci]
+                p = oracle.make_params(**c["params"], threads=threads)
+                t0 = time.perf_counter()
+                oracle.trace(om, p, c["N"], pid_begin=0, count=per_case)
+                t_total += time.perf_counter() - t0
+                n_total += per_case
+        rates[shape] = n_total / t_total
+        sample_desc.append(f"{shape}: first {per_case} ids of 4 cases")
+    # the workload traces equal particle counts on both meshes
+    rate = 1.0 / (0.5 / rates["plate"] + 0.5 / rates["cylinder"])
+    cd = None
+    if results_by_group is not None:
+        zs, rels = [], []
+        for g, res in zip(gs, results_by_group):
+            for c, r in zip(g["cases"], res):
+                Vhat = np.asarray(c["params"]["dir"])
+                F = oracle.panel_sum(g["xyz"], g["tri"], Vhat, c["S"], c["eps"], math.sqrt(300.0 / 1000.0),
+                                     two_sided=(g["shape"] == "plate"))
+                ref = F @ Vhat / (0.5 * c["S"] ** 2 * c["params"]["A_ref"])
+                err = abs(r["CD"] - ref)
+                if r["CD_sigma"] > 0:
+                    zs.append(err / r["CD_sigma"])
+                rels.append(err / max(abs(ref), 1e-12))
+        cd = {"reference": "oracle panel-sum expectation (exact for these convex meshes)",
+              "n_cases": len(rels), "max_abs_z": max(zs) if zs else None,
+              "frac_within_3sigma_plus_1e-4": float(np.mean([z <= 3.0 for z in zs])) if zs else None,
+              "max_rel": max(rels), "median_rel": float(np.median(rels))}
+    base = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "; ".join(sample_desc) + f"; plate {rates['plate']:.4g}/s, cylinder {rates['cylinder']:.4g}/s,"
+                      " combined for equal particle counts"}
+    return base, cd
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle timed as it stands on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    gs = groups()
+    meshes = {g["shape"]: oracle.Mesh(g["xyz"], g["tri"]) for g in gs}
+    sample = {"plate": 60_000, "cylinder": 15_000}
+
+    def step(k):
+        t = {"plate": 0.0, "cylinder": 0.0}
+        n = {"plate": 0, "cylinder": 0}
+        for g in gs:
+            c = g["cases"][(7 * k + 3) % len(g["cases"])]
+            p = oracle.make_params(**c["params"], threads=threads)
+            t0 = time.perf_counter()
+            oracle.trace(meshes[g["shape"]], p, c["N"], pid_begin=0, count=sample[g["shape"]])
+            t[g["shape"]] += time.perf_counter() - t0
+            n[g["shape"]] += sample[g["shape"]]
+        return t, n
+
+    for k in range(args.warmup):
+        step(k)
+    tp = tc = 0.0
+    np_ = nc = 0
+    t_start = time.perf_counter()
+    for k in range(args.steps):
+        t, n = step(args.warmup + k)
+        tp += t["plate"]; tc += t["cylinder"]; np_ += n["plate"]; nc += n["cylinder"]
+    wall = time.perf_counter() - t_start
+    rate = 1.0 / (0.5 / (np_ / tp) + 0.5 / (nc / tc))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "particles_per_case": N_EACH},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"per step: first {sample['plate']} ids of 2 plate cases and "
+                                   f"{sample['cylinder']} ids of 2 cylinder cases; rates combined for equal counts"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU side
+def run_ours(args):
+    import torch
+
+    from paper_1312_3691_gb300 import tpmc as T
+    from paper_1312_3691_gb300.build import build
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if rank == 0:
+        build()
+    if dist is not None:
+        dist.barrier()
+    build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    ctx = T.tpmc_create(local)
+    stream = torch.cuda.current_stream(dev)
+    T.tpmc_set_stream(ctx, stream)
+    gs = groups()
+    K = len(gs[0]["cases"])
+    mesh_ids = {}
+    for g in gs:
+        if g["shape"] not in mesh_ids:
+            mesh_ids[g["shape"]] = T.tpmc_mesh_load(ctx, g["xyz"], g["tri"])
+    d_in = []
+    for gi, g in enumerate(gs):
+        # ranks trace independent streams of the same workload (weak scaling)
+        base = T.make_params(**g["base"], stream_id=rank * 4096 + gi * 128)
+        d_in.append((mesh_ids[g["shape"]], base,
+                     torch.tensor(g["dirs"], dtype=torch.float64, device=dev),
+                     torch.tensor(g["S"], dtype=torch.float64, device=dev),
+                     torch.zeros(K * T.RESULT_BYTES, dtype=torch.uint8, device=dev)))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(events=None):
+        for i, (mid, base, dd, ds, out) in enumerate(d_in):
+            if events is not None:
+                events[i][0].record(stream)
+            T.tpmc_sweep_device(ctx, mid, base, dd, ds, K, N_EACH, out)
+            if events is not None:
+                events[i][1].record(stream)
+
+    # counters pass (outside timing): algorithmic work per step
+    T.tpmc_set_counters(ctx, True)
+    step()
+    torch.cuda.synchronize(dev)
+    T.tpmc_set_counters(ctx, False)
+    work = {"particles": 0, "hits": 0, "nodes": 0, "tris": 0}
+    for (_, _, _, _, out) in d_in:
+        for r in T.results_from_bytes(out.cpu().numpy().tobytes(), K):
+            assert r["status"] == 0, r
+            work["particles"] += r["n_particles"]
+            work["hits"] += r["n_hits"]
+            work["nodes"] += r["n_node_visits"]
+            work["tris"] += r["n_tri_tests"]
+    flops_per_step = (FLOPS_PER_NODE_VISIT * work["nodes"] + FLOPS_PER_TRI_TEST * work["tris"] +
+                      FLOPS_PER_PARTICLE * work["particles"] + FLOPS_PER_HIT * work["hits"])
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    uuid = str(getattr(props, "uuid", "") or "")
+    sampler = ClockSampler(uuid if uuid.startswith("GPU-") else (f"GPU-{uuid}" if uuid else local))
+    sampler.start()
+    time.sleep(0.3)
+    step_ms, launch_ms = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in d_in]
+        step(ev)
+        torch.cuda.synchronize(dev)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        launch_ms += ms
+        step_ms.append(sum(ms))
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    t_step = sum(step_ms) / len(step_ms)
+    particles_step = work["particles"]
+    if dist is not None:
+        t = torch.tensor([t_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    value = world * particles_step / (t_step / 1e3)
+
+    # results of the last timed step
+    results_by_group = [T.results_from_bytes(out.cpu().numpy().tobytes(), K) for (*_, out) in d_in]
+
+    # end to end through the public API with host buffers
+    e2e_ms = []
+    h2d = d2h = 0
+    T.tpmc_set_stream(ctx, None)
+    for k in range(max(1, args.e2e_steps)):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ids = {}
+        h2d = d2h = 0
+        for g in gs:
+            if g["shape"] not in ids:
+                ids[g["shape"]] = T.tpmc_mesh_load(ctx, g["xyz"], g["tri"])
+                h2d += T.tpmc_mesh_info(ctx, ids[g["shape"]])["device_bytes"]
+            base = T.make_params(**g["base"], stream_id=rank * 4096 + 7)
+            res = T.tpmc_sweep(ctx, ids[g["shape"]], base, g["dirs"], g["S"], N_EACH)
+            h2d += g["dirs"].nbytes + g["S"].nbytes
+            d2h += len(res) * T.RESULT_BYTES
+        for i in ids.values():
+            T.tpmc_mesh_unload(ctx, i)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_t = statistics.mean(e2e_ms)
+    if dist is not None:
+        t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = world * particles_step / (e2e_t / 1e3)
+
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    launch_avg_ms = statistics.mean(launch_ms)
+    flops_per_launch = flops_per_step / len(d_in)
+    achieved = flops_per_launch / (launch_avg_ms / 1e3) / 1e12
+    traffic = TRACE_TRAFFIC.get(kernel_source_hash())
+
+    if rank == 0:
+        cpu_base, cd_err = (None, None)
+        if not args.no_cpu_baseline:
+            cpu_base, cd_err = cpu_baseline_and_cd_error(results_by_group)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (procedural meshes; paper prints no absolute throughput)",
+            "config": {"workload": WORKLOAD, "particles_per_step": particles_step, "cases": 4 * K,
+                       "launches_per_step": len(d_in), "l2": "256 MiB flush between steps, outside timed intervals",
+                       "precision": "FP32 traversal, FP64 set-up and reduction"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "ms_per_step": e2e_t, "includes": "mesh upload + BVH build, host inputs, host results"},
+            "gpu_launches": args.steps * len(d_in) * 3,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tflops, "traffic": traffic,
+                         "kernel": "trace_kernel<float>",
+                         "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
+                                       f"(FMA) x {sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
+                         "work_per_step": work},
+            "clocks": clocks,
+            "cpu_baseline": cpu_base,
+            "cd_error": cd_err,
+        }
+        print(json.dumps(line), flush=True)
+    T.tpmc_destroy(ctx)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -85,7 +85,7 @@ class Records(ctypes.Structure):
         ("dv", ctypes.POINTER(ctypes.c_double)), ("n_hits", ctypes.POINTER(ctypes.c_uint32)),
         ("truncated", ctypes.POINTER(ctypes.c_uint32)), ("tri", ctypes.POINTER(ctypes.c_uint32)),
         ("bary", ctypes.POINTER(ctypes.c_double)), ("cosi", ctypes.POINTER(ctypes.c_double)),
-        ("K", ctypes.c_uint32),
+        ("edge", ctypes.POINTER(ctypes.c_double)), ("K", ctypes.c_uint32),
     ]
 
 
@@ -284,10 +284,11 @@ def trace(mesh: Mesh, params: Params, N_total: int, pid_begin: int = 0, count: i
             "pos": np.zeros((count, 3)), "vel": np.zeros((count, 3)), "dv": np.zeros((count, 3)),
             "n_hits": np.zeros(count, np.uint32), "truncated": np.zeros(count, np.uint32),
             "tri": np.full((count, K), 0xFFFFFFFF, np.uint32), "bary": np.ones((count, K)),
-            "cosi": np.ones((count, K)),
+            "cosi": np.ones((count, K)), "edge": np.full((count, K), np.inf),
         }
         rec = Records(_pd(recd["pos"]), _pd(recd["vel"]), _pd(recd["dv"]), _pu32(recd["n_hits"]),
-                      _pu32(recd["truncated"]), _pu32(recd["tri"]), _pd(recd["bary"]), _pd(recd["cosi"]), K)
+                      _pu32(recd["truncated"]), _pu32(recd["tri"]), _pd(recd["bary"]), _pd(recd["cosi"]),
+                      _pd(recd["edge"]), K)
     rc = lib().orc_trace(mesh._h, ctypes.byref(params), int(N_total), int(pid_begin), int(count),
                          ctypes.byref(res), _pd(panel) if panels else None,
                          ctypes.byref(rec) if records else None)

@@ -438,6 +438,7 @@ typedef struct {
   uint32_t* tri;    // [count][K] triangle hit at bounce b (b < K)
   double* bary;     // [count][K] smallest barycentric coordinate of that hit
   double* cosi;     // [count][K] |cos| of the incidence angle of that hit
+  double* edge;     // [count][K] distance (m) from that hit point to the triangle's nearest edge
   uint32_t K;
 } orc_records;
 
@@ -701,6 +702,15 @@ int orc_trace(const void* mesh_handle, const orc_params* p, uint64_t N_total, ui
           if (rec->tri) rec->tri[(size_t)k * rec->K + b] = i;
           if (rec->bary) rec->bary[(size_t)k * rec->K + b] = std::min({hit.u, hit.v, 1.0 - hit.u - hit.v});
           if (rec->cosi) rec->cosi[(size_t)k * rec->K + b] = std::fabs(dot(unit(v), m.nrm[i]));
+          if (rec->edge) {
+            // distance to the edge opposite vertex j = (barycentric of j) x (height over that edge)
+            const double twoA = 2.0 * m.area[i];
+            const double w0 = 1.0 - hit.u - hit.v;
+            const double d0 = w0 * twoA / norm(m.e2[i] - m.e1[i]);
+            const double d1 = hit.u * twoA / norm(m.e2[i]);
+            const double d2 = hit.v * twoA / norm(m.e1[i]);
+            rec->edge[(size_t)k * rec->K + b] = std::min({d0, d1, d2});
+          }
         }
         ++nh;
         pos = hp;

@@ -1,0 +1,597 @@
+// Host runtime behind the C ABI of include/tpmc.h: contexts, resident meshes,
+// memory admission, query set-up, launches and result read-back.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "runtime.h"
+
+namespace tpmc {
+
+thread_local std::string g_last_error;
+
+tpmc_status fail(tpmc_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+tpmc_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(TPMC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------ allocation
+tpmc_status Ctx::alloc(void** p, size_t bytes, const char* what) {
+  *p = nullptr;
+  if (bytes == 0) return TPMC_OK;
+  if (used + bytes > budget)
+    return fail(TPMC_ENOMEM, std::string(what) + ": memory budget exceeded (" + std::to_string(used + bytes) +
+                                 " > " + std::to_string(budget) + " bytes)");
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(TPMC_ENOMEM, std::string(what) + ": cudaMalloc: " + cudaGetErrorString(e));
+  }
+  sizes[*p] = bytes;
+  used += bytes;
+  return TPMC_OK;
+}
+
+void Ctx::release(void* p) {
+  if (!p) return;
+  auto it = sizes.find(p);
+  if (it != sizes.end()) {
+    used -= it->second;
+    sizes.erase(it);
+  }
+  cudaFree(p);
+}
+
+tpmc_status Ctx::grow(Scratch& s, size_t bytes, const char* what) {
+  if (s.cap >= bytes) return TPMC_OK;
+  release(s.ptr);
+  s.ptr = nullptr;
+  s.cap = 0;
+  size_t want = std::max(bytes, (size_t)256);
+  tpmc_status st = alloc(&s.ptr, want, what);
+  if (st == TPMC_OK) s.cap = want;
+  return st;
+}
+
+// ---------------------------------------------------------------- params
+tpmc_status validate_params(const tpmc_params* p) {
+  if (!p) return fail(TPMC_EINVAL, "params is NULL");
+  const double pos[] = {p->n, p->T_inf, p->m, p->V, p->T_W, p->A_ref};
+  const char* names[] = {"n", "T_inf", "m", "V", "T_W", "A_ref"};
+  for (int i = 0; i < 6; ++i)
+    if (!(std::isfinite(pos[i]) && pos[i] > 0.0)) return fail(TPMC_EINVAL, std::string(names[i]) + " must be finite and > 0");
+  if (!(p->eps_diffuse >= 0.0 && p->eps_diffuse <= 1.0)) return fail(TPMC_EINVAL, "eps_diffuse must be in [0, 1]");
+  const double dn = std::sqrt(p->dir[0] * p->dir[0] + p->dir[1] * p->dir[1] + p->dir[2] * p->dir[2]);
+  if (!(std::isfinite(dn) && dn > 0.0)) return fail(TPMC_EINVAL, "dir must be finite and non-zero");
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(p->ref_point[i]) || !std::isfinite(p->center[i])) return fail(TPMC_EINVAL, "non-finite point");
+  if (!std::isfinite(p->r_cv)) return fail(TPMC_EINVAL, "r_cv must be finite");
+  if (p->max_bounces < 1) return fail(TPMC_EINVAL, "max_bounces must be >= 1");
+  if (p->precision != TPMC_FP32 && p->precision != TPMC_FP64) return fail(TPMC_EINVAL, "unknown precision");
+  return TPMC_OK;
+}
+
+tpmc_status fill_query(const MeshRec& m, const tpmc_params* p, uint64_t N, QueryDev* q) {
+  std::memset(q, 0, sizeof(*q));
+  q->n = p->n; q->T_inf = p->T_inf; q->m = p->m; q->V = p->V;
+  for (int i = 0; i < 3; ++i) { q->dir[i] = p->dir[i]; q->ref[i] = p->ref_point[i]; }
+  q->T_W = p->T_W; q->eps = p->eps_diffuse; q->A_ref = p->A_ref;
+  if (p->r_cv <= 0.0) {
+    for (int i = 0; i < 3; ++i) q->center[i] = m.center[i];
+    q->r_cv = m.radius > 0.0 ? 1.05 * m.radius : 1.0;
+  } else {
+    for (int i = 0; i < 3; ++i) q->center[i] = p->center[i];
+    q->r_cv = p->r_cv;
+    // the body must lie strictly inside the control volume
+    double far2 = 0.0;
+    for (uint64_t k = 0; k < m.h_tri.size(); ++k) {
+      const double* v = &m.h_xyz[3 * (size_t)m.h_tri[k]];
+      double d2 = 0.0;
+      for (int i = 0; i < 3; ++i) d2 += (v[i] - q->center[i]) * (v[i] - q->center[i]);
+      far2 = std::max(far2, d2);
+    }
+    if (!(std::sqrt(far2) < q->r_cv)) return fail(TPMC_EINVAL, "the mesh is not strictly inside the control volume");
+  }
+  double dref = 0.0;
+  for (int i = 0; i < 3; ++i) dref += (m.center[i] - q->ref[i]) * (m.center[i] - q->ref[i]);
+  q->rmax = std::sqrt(dref) + m.radius;
+  q->N = N;
+  q->seed = p->seed;
+  q->stream_id = p->stream_id;
+  q->max_bounces = p->max_bounces;
+  q->precision = p->precision;
+  q->panel = nullptr;
+  return TPMC_OK;
+}
+
+LaunchCfg Ctx::schedule(const MeshRec& m, uint32_t precision, uint64_t total) {
+  LaunchCfg cfg;
+  const uint64_t key = tune_key(m.dev.n_tri, precision);
+  auto it = tuned.find(key);
+  if (manual_launch) cfg = manual;
+  else if (it != tuned.end()) cfg = it->second;
+  else {
+    cfg.block = 128;
+    cfg.smem_nodes = std::min<uint32_t>(m.dev.n_nodes, precision == TPMC_FP64 ? 256u : 512u);
+    cfg.blocks_per_sm = 0;
+    cfg.chunk = 0;
+  }
+  cfg.smem_nodes = std::min<uint32_t>(cfg.smem_nodes, m.dev.n_nodes);
+  const int maxb = trace_max_blocks_per_sm(precision, cfg, m.dev.n_nodes);
+  if (cfg.blocks_per_sm == 0 || (int)cfg.blocks_per_sm > maxb) cfg.blocks_per_sm = std::max(1, maxb);
+  if (cfg.chunk == 0) {
+    const uint64_t warps = (uint64_t)num_sms * cfg.blocks_per_sm * (cfg.block / 32);
+    uint64_t ch = total / std::max<uint64_t>(1, warps * 16);
+    ch = (ch / 32) * 32;
+    cfg.chunk = (uint32_t)std::min<uint64_t>(1024, std::max<uint64_t>(32, ch));
+  }
+  return cfg;
+}
+
+// One batched run: nq queries prepared on the device from `base` (+ dirs/S)
+// or uploaded one by one, traced together, finalised into d_out.
+tpmc_status Ctx::run(const MeshRec& m, const QueryDev* h_queries, uint32_t nq, const QueryDev* h_base,
+                     const double* d_dirs, const double* d_S, const ItemDev* h_items, uint32_t n_items, uint64_t total,
+                     uint32_t precision, tpmc_result* d_out, const RecordsDev* rec) {
+  tpmc_status st;
+  if ((st = grow(s_queries, sizeof(QueryDev) * (size_t)nq, "queries")) != TPMC_OK) return st;
+  if ((st = grow(s_acc, sizeof(AccDev) * (size_t)nq, "accumulators")) != TPMC_OK) return st;
+  if ((st = grow(s_items, sizeof(ItemDev) * (size_t)std::max(nq, n_items), "work items")) != TPMC_OK) return st;
+  if ((st = grow(s_misc, 256, "counters")) != TPMC_OK) return st;
+  if ((st = grow(s_base, sizeof(QueryDev), "base query")) != TPMC_OK) return st;
+  QueryDev* d_queries = (QueryDev*)s_queries.ptr;
+  AccDev* d_acc = (AccDev*)s_acc.ptr;
+  ItemDev* d_items = (ItemDev*)s_items.ptr;
+  unsigned long long* d_counter = (unsigned long long*)s_misc.ptr;
+  int* d_err = (int*)((char*)s_misc.ptr + 64);
+  cudaError_t e;
+  // Host sources here are pageable, so each copy is staged before the call
+  // returns and the caller's structs may be reused at once.
+  if (h_base) {
+    if ((e = cudaMemcpyAsync(s_base.ptr, h_base, sizeof(QueryDev), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+      return cuda_fail(e, "upload base query");
+  } else {
+    if ((e = cudaMemcpyAsync(d_queries, h_queries, sizeof(QueryDev) * nq, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+      return cuda_fail(e, "upload queries");
+    if ((e = cudaMemcpyAsync(d_items, h_items, sizeof(ItemDev) * n_items, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+      return cuda_fail(e, "upload items");
+  }
+  if ((e = cudaMemsetAsync(d_acc, 0, sizeof(AccDev) * nq, stream)) != cudaSuccess) return cuda_fail(e, "clear acc");
+  if ((e = cudaMemsetAsync(s_misc.ptr, 0, 128, stream)) != cudaSuccess) return cuda_fail(e, "clear counter");
+  if ((e = launch_setup(d_queries, nq, h_base ? (const QueryDev*)s_base.ptr : nullptr, d_dirs, d_S,
+                        h_base ? d_items : nullptr, nullptr, stream)) != cudaSuccess)
+    return cuda_fail(e, "setup kernel");
+  TraceArgs a{};
+  a.mesh = m.dev;
+  a.queries = d_queries;
+  a.acc = d_acc;
+  a.items = d_items;
+  a.n_items = h_base ? nq : n_items;
+  a.total = total;
+  a.counter = d_counter;
+  a.error = d_err;
+  a.count_work = counters ? 1u : 0u;
+  if (rec) a.rec = *rec;
+  const LaunchCfg cfg = schedule(m, precision, total);
+  a.chunk = cfg.chunk;
+  a.smem_nodes = cfg.smem_nodes;
+  last_cfg = cfg;
+  if (total > 0 && (e = launch_trace(a, precision, cfg, num_sms, stream)) != cudaSuccess) return cuda_fail(e, "trace kernel");
+  if ((e = launch_finalize(d_queries, d_acc, nq, nullptr, d_out, stream)) != cudaSuccess)
+    return cuda_fail(e, "finalize kernel");
+  if ((e = cudaMemcpyAsync(h_err_word, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+    return cuda_fail(e, "read error word");
+  return TPMC_OK;
+}
+
+tpmc_status Ctx::check_error_word() {
+  if (*h_err_word != 0) {
+    const int w = *h_err_word;
+    *h_err_word = 0;
+    return fail(TPMC_ECUDA, "trace kernel reported error word " + std::to_string(w) + " (traversal stack overflow)");
+  }
+  return TPMC_OK;
+}
+
+Ctx::~Ctx() {
+  if (serve) stop_serving(this);
+  for (auto& kv : panels) release(kv.second.d_panel);
+  for (auto& kv : meshes) release(kv.second.d_block);
+  for (Scratch* s : {&s_queries, &s_acc, &s_items, &s_misc, &s_base, &s_out, &s_in})
+    release(s->ptr);
+  if (h_pinned) cudaFreeHost(h_pinned);
+  if (own_stream) cudaStreamDestroy(own_stream);
+}
+
+}  // namespace tpmc
+
+using namespace tpmc;
+
+// =========================================================================
+extern "C" {
+
+tpmc_status tpmc_create(int device, size_t mem_budget_bytes, tpmc_ctx** out) {
+  if (!out) return fail(TPMC_EINVAL, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= n) return fail(TPMC_EINVAL, "no such CUDA device");
+  if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  std::unique_ptr<Ctx> c(new Ctx());
+  c->device = device;
+  cudaDeviceProp prop;
+  if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  c->num_sms = prop.multiProcessorCount;
+  size_t free_b = 0, total_b = 0;
+  if ((e = cudaMemGetInfo(&free_b, &total_b)) != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
+  c->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)(0.9 * (double)free_b);
+  if ((e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamCreate");
+  c->stream = c->own_stream;
+  if ((e = cudaMallocHost(&c->h_pinned, 4096)) != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+  c->h_err_word = (int*)c->h_pinned;
+  *c->h_err_word = 0;
+  *out = reinterpret_cast<tpmc_ctx*>(c.release());
+  return TPMC_OK;
+}
+
+tpmc_status tpmc_destroy(tpmc_ctx* ctx) {
+  if (!ctx) return TPMC_OK;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  delete c;
+  return TPMC_OK;
+}
+
+tpmc_status tpmc_set_stream(tpmc_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return fail(TPMC_EINVAL, "ctx is NULL");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  c->stream = cuda_stream ? (cudaStream_t)cuda_stream : c->own_stream;
+  return TPMC_OK;
+}
+
+const char* tpmc_last_error(const tpmc_ctx*) { return g_last_error.c_str(); }
+
+tpmc_status tpmc_set_counters(tpmc_ctx* ctx, int enable) {
+  if (!ctx) return fail(TPMC_EINVAL, "ctx is NULL");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  c->counters = enable != 0;
+  return TPMC_OK;
+}
+
+tpmc_status tpmc_mesh_load(tpmc_ctx* ctx, const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t n_tri,
+                           tpmc_mesh_id* out) {
+  if (!ctx || !out) return fail(TPMC_EINVAL, "NULL argument");
+  if ((n_vert > 0 && !xyz) || (n_tri > 0 && !tri)) return fail(TPMC_EINVAL, "NULL mesh array");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  BvhBuild b;
+  const char* err = nullptr;
+  if (!build_bvh(xyz, n_vert, tri, n_tri, 4, &b, &err)) {
+    b.release();
+    return fail(TPMC_EINVAL, err);
+  }
+  MeshRec m;
+  const size_t sz_nodes = b.n_nodes * 16 * sizeof(float);
+  const size_t sz_tris = (size_t)b.n_leaf_tris * 12 * sizeof(float);
+  const size_t sz_tris64 = (size_t)b.n_leaf_tris * 12 * sizeof(double);
+  const size_t sz_fr = (size_t)n_tri * 8 * sizeof(float);
+  const size_t sz_fr64 = (size_t)n_tri * 8 * sizeof(double);
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t total = al(sz_nodes) + al(sz_tris) + al(sz_tris64) + al(sz_fr) + al(sz_fr64);
+  tpmc_status st = c->alloc(&m.d_block, std::max(total, (size_t)256), "mesh");
+  if (st != TPMC_OK) { b.release(); return st; }
+  char* base = (char*)m.d_block;
+  size_t off = 0;
+  auto place = [&](size_t sz) { char* p = base + off; off += al(sz); return p; };
+  char* p_nodes = place(sz_nodes);
+  char* p_tris = place(sz_tris);
+  char* p_tris64 = place(sz_tris64);
+  char* p_fr = place(sz_fr);
+  char* p_fr64 = place(sz_fr64);
+  cudaError_t e = cudaSuccess;
+  if (sz_nodes) e = cudaMemcpy(p_nodes, b.nodes, sz_nodes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && sz_tris) e = cudaMemcpy(p_tris, b.tris, sz_tris, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && sz_tris64) e = cudaMemcpy(p_tris64, b.tris64, sz_tris64, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && sz_fr) e = cudaMemcpy(p_fr, b.frames, sz_fr, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && sz_fr64) e = cudaMemcpy(p_fr64, b.frames64, sz_fr64, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    c->release(m.d_block);
+    b.release();
+    return cuda_fail(e, "upload mesh");
+  }
+  m.dev.nodes = (const float4*)p_nodes;
+  m.dev.tris = (const float4*)p_tris;
+  m.dev.tris64 = (const double*)p_tris64;
+  m.dev.frames = (const float4*)p_fr;
+  m.dev.frames64 = (const double*)p_fr64;
+  m.dev.n_nodes = (uint32_t)b.n_nodes;
+  m.dev.n_tri = n_tri;
+  m.dev.n_tri_leaf = b.n_leaf_tris;
+  m.dev.scene_radius = (float)b.radius;
+  for (int i = 0; i < 3; ++i) m.center[i] = b.center[i];
+  m.radius = b.radius;
+  m.depth = b.depth;
+  m.leaf_max = b.leaf_max;
+  m.n_skipped = b.n_skipped;
+  m.n_vert = n_vert;
+  m.bytes = total;
+  m.h_xyz.assign(xyz, xyz + 3 * (size_t)n_vert);
+  m.h_tri.assign(tri, tri + 3 * (size_t)n_tri);
+  b.release();
+  const tpmc_mesh_id id = c->next_mesh++;
+  c->meshes[id] = std::move(m);
+  *out = id;
+  return TPMC_OK;
+}
+
+tpmc_status tpmc_mesh_unload(tpmc_ctx* ctx, tpmc_mesh_id mesh) {
+  if (!ctx) return fail(TPMC_EINVAL, "ctx is NULL");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  auto it = c->meshes.find(mesh);
+  if (it == c->meshes.end()) return fail(TPMC_ENOTFOUND, "unknown mesh id");
+  if (it->second.in_use > 0) return fail(TPMC_EBUSY, "mesh is used by queries in flight");
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  c->release(it->second.d_block);
+  c->meshes.erase(it);
+  return TPMC_OK;
+}
+
+tpmc_status tpmc_mesh_info(tpmc_ctx* ctx, tpmc_mesh_id mesh, tpmc_mesh_stats* out) {
+  if (!ctx || !out) return fail(TPMC_EINVAL, "NULL argument");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  auto it = c->meshes.find(mesh);
+  if (it == c->meshes.end()) return fail(TPMC_ENOTFOUND, "unknown mesh id");
+  const MeshRec& m = it->second;
+  std::memset(out, 0, sizeof(*out));
+  out->n_tri = m.dev.n_tri;
+  out->n_vert = m.n_vert;
+  out->n_nodes = m.dev.n_nodes;
+  out->depth = m.depth;
+  out->n_skipped = m.n_skipped;
+  out->leaf_max = m.leaf_max;
+  for (int i = 0; i < 3; ++i) out->bound_center[i] = m.center[i];
+  out->bound_radius = m.radius;
+  out->device_bytes = m.bytes;
+  return TPMC_OK;
+}
+
+static tpmc_status trace_common(Ctx* c, tpmc_mesh_id mesh, const tpmc_params* params, uint64_t N,
+                                tpmc_records* records, tpmc_result* out) {
+  if (!out) return fail(TPMC_EINVAL, "out is NULL");
+  tpmc_status st = validate_params(params);
+  if (st != TPMC_OK) return st;
+  if (N == 0 || N > (1ull << 34)) return fail(TPMC_EINVAL, "N must be in [1, 2^34]");
+  auto it = c->meshes.find(mesh);
+  if (it == c->meshes.end()) return fail(TPMC_ENOTFOUND, "unknown mesh id");
+  const MeshRec& m = it->second;
+  cudaSetDevice(c->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  QueryDev q;
+  if ((st = fill_query(m, params, N, &q)) != TPMC_OK) return st;
+  // per-triangle loads
+  void* d_panel = nullptr;
+  if (params->want_panels && m.dev.n_tri > 0) {
+    if ((st = c->alloc(&d_panel, (size_t)m.dev.n_tri * 3 * sizeof(long long), "panel loads")) != TPMC_OK) return st;
+    cudaMemsetAsync(d_panel, 0, (size_t)m.dev.n_tri * 3 * sizeof(long long), c->stream);
+    q.panel = (long long*)d_panel;
+  }
+  // records
+  RecordsDev rec;
+  void* d_rec = nullptr;
+  if (records) {
+    if (records->K > (uint32_t)kMaxRecordK || N > (1ull << 26)) {
+      c->release(d_panel);
+      return fail(TPMC_EINVAL, "records: K must be <= 64 and N <= 2^26");
+    }
+    const size_t K = std::max<uint32_t>(records->K, 1);
+    const size_t bytes = N * (9 * sizeof(double) + (2 + K) * sizeof(uint32_t));
+    if ((st = c->alloc(&d_rec, bytes, "records")) != TPMC_OK) { c->release(d_panel); return st; }
+    char* p = (char*)d_rec;
+    rec.pos = (double*)p; p += N * 3 * sizeof(double);
+    rec.vel = (double*)p; p += N * 3 * sizeof(double);
+    rec.dv = (double*)p; p += N * 3 * sizeof(double);
+    rec.n_hits = (uint32_t*)p; p += N * sizeof(uint32_t);
+    rec.truncated = (uint32_t*)p; p += N * sizeof(uint32_t);
+    rec.tri = (uint32_t*)p;
+    rec.K = records->K;
+    cudaMemsetAsync(rec.tri, 0xFF, N * K * sizeof(uint32_t), c->stream);
+  }
+  ItemDev item;
+  std::memset(&item, 0, sizeof(item));
+  item.g_begin = 0; item.pid_begin = 0; item.count = N; item.query = 0;
+  tpmc_status rs = c->grow(c->s_out, sizeof(tpmc_result), "result");
+  if (rs == TPMC_OK)
+    rs = c->run(m, &q, 1, nullptr, nullptr, nullptr, &item, 1, N, params->precision, (tpmc_result*)c->s_out.ptr,
+                records ? &rec : nullptr);
+  cudaError_t e = cudaSuccess;
+  if (rs == TPMC_OK) e = cudaMemcpyAsync(out, c->s_out.ptr, sizeof(tpmc_result), cudaMemcpyDeviceToHost, c->stream);
+  if (rs == TPMC_OK && e == cudaSuccess && records) {
+    const size_t K = records->K;
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+      if (dst && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream);
+    };
+    cp(records->pos, rec.pos, N * 3 * sizeof(double));
+    cp(records->vel, rec.vel, N * 3 * sizeof(double));
+    cp(records->dv, rec.dv, N * 3 * sizeof(double));
+    cp(records->n_hits, rec.n_hits, N * sizeof(uint32_t));
+    cp(records->truncated, rec.truncated, N * sizeof(uint32_t));
+    if (K) cp(records->tri, rec.tri, N * K * sizeof(uint32_t));
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (d_rec) c->release(d_rec);
+  if (rs != TPMC_OK || e != cudaSuccess) {
+    c->release(d_panel);
+    return rs != TPMC_OK ? rs : cuda_fail(e, "trace");
+  }
+  if ((st = c->check_error_word()) != TPMC_OK) { c->release(d_panel); return st; }
+  const auto t1 = std::chrono::steady_clock::now();
+  out->ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  if (out->status != TPMC_OK) {
+    c->release(d_panel);
+    return fail((tpmc_status)out->status, "query set-up rejected the parameters (S outside [0.01, 50] or fixed-point range)");
+  }
+  out->query_id = c->next_query++;
+  if (d_panel) {
+    PanelRec pr;
+    pr.d_panel = d_panel;
+    pr.query = q;
+    pr.mesh = mesh;
+    pr.n_tri = m.dev.n_tri;
+    // keep the set-up values the panel conversion needs
+    pr.query.gamma = out->gamma;
+    pr.query.m = params->m;
+    pr.query.c_mp = out->c_mp;
+    pr.query.quantum = out->fixed_quantum;
+    c->panels[out->query_id] = pr;
+  }
+  return TPMC_OK;
+}
+
+tpmc_status tpmc_trace(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* params, uint64_t N, tpmc_result* out) {
+  if (!ctx) return fail(TPMC_EINVAL, "ctx is NULL");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  return trace_common(c, mesh, params, N, nullptr, out);
+}
+
+tpmc_status tpmc_trace_records(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* params, uint64_t N,
+                               tpmc_records* records, tpmc_result* out) {
+  if (!ctx || !records) return fail(TPMC_EINVAL, "NULL argument");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  return trace_common(c, mesh, params, N, records, out);
+}
+
+tpmc_status tpmc_panels(tpmc_ctx* ctx, tpmc_query_id query, double* pressure, double* shear, uint32_t n_tri) {
+  if (!ctx) return fail(TPMC_EINVAL, "ctx is NULL");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  auto it = c->panels.find(query);
+  if (it == c->panels.end()) return fail(TPMC_ENOTFOUND, "no panel loads kept for this query");
+  PanelRec& pr = it->second;
+  if (n_tri != pr.n_tri) return fail(TPMC_EINVAL, "n_tri does not match the mesh");
+  auto mit = c->meshes.find(pr.mesh);
+  if (mit == c->meshes.end()) return fail(TPMC_ENOTFOUND, "the query's mesh was unloaded");
+  cudaSetDevice(c->device);
+  tpmc_status st;
+  if ((st = c->grow(c->s_in, sizeof(QueryDev), "panel query")) != TPMC_OK) return st;
+  void* d_pv = nullptr;
+  if ((st = c->alloc(&d_pv, (size_t)n_tri * 2 * sizeof(double), "panel output")) != TPMC_OK) return st;
+  double* d_p = (double*)d_pv;
+  double* d_s = d_p + n_tri;
+  cudaError_t e = cudaMemcpyAsync(c->s_in.ptr, &pr.query, sizeof(QueryDev), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = launch_panels((const QueryDev*)c->s_in.ptr, (const long long*)pr.d_panel, mit->second.dev.frames,
+                      mit->second.dev.frames64, n_tri, d_p, d_s, c->stream);
+  if (e == cudaSuccess && pressure) e = cudaMemcpyAsync(pressure, d_p, n_tri * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && shear) e = cudaMemcpyAsync(shear, d_s, n_tri * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  c->release(d_pv);
+  if (e != cudaSuccess) return cuda_fail(e, "panels");
+  c->release(pr.d_panel);
+  c->panels.erase(it);
+  return TPMC_OK;
+}
+
+static tpmc_status sweep_common(Ctx* c, tpmc_mesh_id mesh, const tpmc_params* base, const double* d_dirs,
+                                const double* d_S, uint32_t K, uint64_t N_each, tpmc_result* d_out) {
+  tpmc_status st = validate_params(base);
+  if (st != TPMC_OK) return st;
+  if (K == 0) return fail(TPMC_EINVAL, "K must be >= 1");
+  if (N_each == 0 || N_each > (1ull << 34)) return fail(TPMC_EINVAL, "N_each must be in [1, 2^34]");
+  if ((uint64_t)K * N_each > (1ull << 50)) return fail(TPMC_EINVAL, "K * N_each too large");
+  auto it = c->meshes.find(mesh);
+  if (it == c->meshes.end()) return fail(TPMC_ENOTFOUND, "unknown mesh id");
+  const MeshRec& m = it->second;
+  QueryDev q;
+  if ((st = fill_query(m, base, N_each, &q)) != TPMC_OK) return st;
+  return c->run(m, nullptr, K, &q, d_dirs, d_S, nullptr, 0, (uint64_t)K * N_each, base->precision, d_out, nullptr);
+}
+
+tpmc_status tpmc_sweep(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* base, const double* h_dirs,
+                       const double* h_S, uint32_t K, uint64_t N_each, tpmc_result* h_out) {
+  if (!ctx || !h_out) return fail(TPMC_EINVAL, "NULL argument");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  tpmc_status st;
+  const size_t in_bytes = (size_t)K * 4 * sizeof(double);
+  if ((st = c->grow(c->s_in, std::max(in_bytes, sizeof(QueryDev)), "sweep inputs")) != TPMC_OK) return st;
+  if ((st = c->grow(c->s_out, (size_t)K * sizeof(tpmc_result), "sweep results")) != TPMC_OK) return st;
+  double* d_dirs = h_dirs ? (double*)c->s_in.ptr : nullptr;
+  double* d_S = h_S ? (double*)c->s_in.ptr + 3 * (size_t)K : nullptr;
+  cudaError_t e = cudaSuccess;
+  if (h_dirs) e = cudaMemcpyAsync(d_dirs, h_dirs, (size_t)K * 3 * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && h_S) e = cudaMemcpyAsync(d_S, h_S, (size_t)K * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "upload sweep inputs");
+  if ((st = sweep_common(c, mesh, base, d_dirs, d_S, K, N_each, (tpmc_result*)c->s_out.ptr)) != TPMC_OK) return st;
+  e = cudaMemcpyAsync(h_out, c->s_out.ptr, (size_t)K * sizeof(tpmc_result), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sweep");
+  if ((st = c->check_error_word()) != TPMC_OK) return st;
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (uint32_t k = 0; k < K; ++k) h_out[k].ms = ms;
+  return TPMC_OK;
+}
+
+tpmc_status tpmc_sweep_device(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* base, const double* d_dirs,
+                              const double* d_S, uint32_t K, uint64_t N_each, tpmc_result* d_out) {
+  if (!ctx || !d_out) return fail(TPMC_EINVAL, "NULL argument");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  return sweep_common(c, mesh, base, d_dirs, d_S, K, N_each, d_out);
+}
+
+tpmc_status tpmc_set_launch(tpmc_ctx* ctx, const tpmc_launch* cfg) {
+  if (!ctx) return fail(TPMC_EINVAL, "ctx is NULL");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  if (!cfg) { c->manual_launch = false; return TPMC_OK; }
+  if (cfg->block == 0 || cfg->block % 32 != 0 || cfg->block > 256) return fail(TPMC_EINVAL, "block must be 32..256, multiple of 32");
+  if (cfg->chunk != 0 && (cfg->chunk % 32 != 0)) return fail(TPMC_EINVAL, "chunk must be a multiple of 32");
+  c->manual_launch = true;
+  c->manual.block = cfg->block;
+  c->manual.blocks_per_sm = cfg->blocks_per_sm;
+  c->manual.chunk = cfg->chunk;
+  c->manual.smem_nodes = cfg->smem_nodes;
+  return TPMC_OK;
+}
+
+tpmc_status tpmc_get_launch(tpmc_ctx* ctx, tpmc_mesh_id mesh, uint32_t precision, tpmc_launch* out) {
+  if (!ctx || !out) return fail(TPMC_EINVAL, "NULL argument");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  auto it = c->meshes.find(mesh);
+  if (it == c->meshes.end()) return fail(TPMC_ENOTFOUND, "unknown mesh id");
+  const LaunchCfg cfg = c->schedule(it->second, precision, 0);
+  out->block = cfg.block;
+  out->blocks_per_sm = cfg.blocks_per_sm;
+  out->chunk = cfg.chunk;
+  out->smem_nodes = cfg.smem_nodes;
+  return TPMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,860 @@
+// CUDA kernels of the TPMC hot path for sm_103a (GB300).
+//
+//   setup_kernel     FP64: free-stream set-up per query (Nomenclature; Eq. 10
+//                    flux; particle weight, §II.A), Rodrigues matrix (Eq. 15),
+//                    fixed-point scale, start table of the latitude inverse CDF.
+//   trace_kernel<R>  persistent, one warp = 32 particle slots refilled from a
+//                    global work counter by ballot; per slot: Philox draws,
+//                    seeding (Eq. 11, Eq. 14a-c, Eq. 15), BVH closest hit with a
+//                    watertight ray/triangle test (§II.A), Maxwell re-emission,
+//                    int64 fixed-point momentum sums, until the particle misses
+//                    or reaches max_bounces.  R = float (FP32 path) or double.
+//   finalize_kernel  FP64 reduction to force, torque, C_D and its error.
+//   panels_kernel    FP64 per-triangle pressure and shear.
+//
+// This file shares nothing with the CPU oracle; both follow the paper and the
+// published Philox4x32-10 definition (Salmon et al., SC'11).
+#include <algorithm>
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "tpmc_internal.h"
+
+namespace tpmc {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr double kBoltz = 1.380649e-23;
+constexpr double kSqrtPiD = 1.7724538509055160273;
+
+// ------------------------------------------------------------------ Philox
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// (k + 1/2) 2^-23 for the top 23 bits k: exact in float and double.
+template <typename R>
+__device__ __forceinline__ R uniform(uint32_t w) {
+  return (R)(w >> 9) * (R)1.1920928955078125e-07 + (R)5.9604644775390625e-08;
+}
+
+__device__ __forceinline__ uint4 draws(const QueryDev& q, uint64_t pid, uint32_t block) {
+  return philox4x32_10(make_uint4((uint32_t)pid, (uint32_t)(pid >> 32), q.stream_id, block),
+                       make_uint2((uint32_t)q.seed, (uint32_t)(q.seed >> 32)));
+}
+
+// ----------------------------------------------------------- math by type
+template <typename R> struct Fn;
+template <> struct Fn<float> {
+  static __device__ __forceinline__ float exp(float x) { return expf(x); }
+  static __device__ __forceinline__ float log(float x) { return logf(x); }
+  static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float erfc(float x) { return erfcf(x); }
+  static __device__ __forceinline__ float erfcx(float x) { return erfcxf(x); }
+  static __device__ __forceinline__ float ncdfinv(float x) { return normcdfinvf(x); }
+  static __device__ __forceinline__ void sincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+  static __device__ __forceinline__ float fabs(float x) { return fabsf(x); }
+  static constexpr float kTol = 2.5e-7f;
+  static constexpr int kIter = 12;
+};
+template <> struct Fn<double> {
+  static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
+  static __device__ __forceinline__ double log(double x) { return ::log(x); }
+  static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+  static __device__ __forceinline__ double erfc(double x) { return ::erfc(x); }
+  static __device__ __forceinline__ double erfcx(double x) { return ::erfcx(x); }
+  static __device__ __forceinline__ double ncdfinv(double x) { return ::normcdfinv(x); }
+  static __device__ __forceinline__ void sincospi(double x, double* s, double* c) { ::sincospi(x, s, c); }
+  static __device__ __forceinline__ double fabs(double x) { return ::fabs(x); }
+  static constexpr double kTol = 4e-16;
+  static constexpr int kIter = 40;
+};
+
+// Query constants in the path's precision.
+template <typename R> struct QC;
+template <> struct QC<float> {
+  float S, cw, r_cv, sqrtpi_4S, K1, Dinv, scale;
+  float Rm[9], vhat[3], center[3], ref[3];
+  __device__ __forceinline__ void load(const QueryDev& q) {
+    S = q.fS; cw = q.fcw; r_cv = q.fr_cv; sqrtpi_4S = q.fsqrtpi_4S; K1 = q.fK1; Dinv = q.fD_inv; scale = q.fscale;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Rm[i] = q.fR[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { vhat[i] = q.fvhat[i]; center[i] = q.fcenter[i]; ref[i] = q.fref[i]; }
+  }
+};
+template <> struct QC<double> {
+  double S, cw, r_cv, sqrtpi_4S, K1, Dinv, scale;
+  double Rm[9], vhat[3], center[3], ref[3];
+  __device__ __forceinline__ void load(const QueryDev& q) {
+    S = q.S; cw = q.cw; r_cv = q.r_cv; sqrtpi_4S = kSqrtPiD / (4.0 * q.S); K1 = q.K1; Dinv = 1.0 / q.Dnorm;
+    scale = 1.0 / q.quantum;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Rm[i] = q.R[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { vhat[i] = q.vhat[i]; center[i] = q.center[i]; ref[i] = q.ref[i]; }
+  }
+};
+
+// ------------------------------------------------------- seeding (§III.A)
+// Latitude law (Eq. 11) in x = sin(phi): CDF written with erfc(-S x) = 1 + erf(S x):
+//   H(x) = [ sqrt(pi)/(4S) (2 S^2 x^2 + 1) erfc(-S x) + (x/2) e^{-S^2 x^2} - K1 ] / D,
+//   K1 = sqrt(pi)/(4S) (2 S^2 + 1) erfc(S) - e^{-S^2}/2,  so H(-1) = 0 exactly in the algebra.
+// Its density h(x) = [e^{-S^2 x^2} + sqrt(pi) S x erfc(-S x)] / D.
+template <typename R>
+__device__ __forceinline__ R latitude_cdf(R x, R S, R sqrtpi_4S, R K1, R Dinv) {
+  const R Sx = S * x;
+  return (sqrtpi_4S * ((R)2 * Sx * Sx + (R)1) * Fn<R>::erfc(-Sx) + (R)0.5 * x * Fn<R>::exp(-Sx * Sx) - K1) * Dinv;
+}
+template <typename R>
+__device__ __forceinline__ R latitude_pdf(R x, R S, R Dinv) {
+  const R Sx = S * x;
+  return (Fn<R>::exp(-Sx * Sx) + (R)kSqrtPiD * Sx * Fn<R>::erfc(-Sx)) * Dinv;
+}
+
+// x = H^-1(u): start from the table knots around u, then safeguarded Newton.
+template <typename R>
+__device__ R latitude_inverse(R u, const QueryDev& q, const QC<R>& c) {
+  const float uf = (float)u * (float)kHTable;
+  const int j = min((int)uf, kHTable - 1);
+  const R t0 = (R)__ldg(&q.htab[j]), t1 = (R)__ldg(&q.htab[j + 1]);
+  R lo = fmax(t0 - (R)2e-6, (R)-1), hi = fmin(t1 + (R)2e-6, (R)1);
+  R x = t0 + (R)(uf - (float)j) * (t1 - t0);
+#pragma unroll 1
+  for (int it = 0; it < Fn<R>::kIter; ++it) {
+    const R f = latitude_cdf<R>(x, c.S, c.sqrtpi_4S, c.K1, c.Dinv) - u;
+    if (f == (R)0) break;
+    if (f < (R)0) lo = x; else hi = x;
+    const R d = latitude_pdf<R>(x, c.S, c.Dinv);
+    R xn = x - f / d;
+    if (!(xn > lo && xn < hi)) xn = (R)0.5 * (lo + hi);
+    const R step = Fn<R>::fabs(xn - x);
+    x = xn;
+    if (step <= Fn<R>::kTol * (Fn<R>::fabs(x) + (R)1e-3)) break;
+  }
+  return x;
+}
+
+// Inward normal speed (Eq. 14a, numerator read as 2 v_n/c_mp): x = v_n/c_mp > 0
+// with density 2 x e^{-(x-s)^2} / Z(s).  Solved through the survival function
+//   Q(x) = [e^{-y^2} + sqrt(pi) s erfc(y)] / Z(s),  y = x - s,   Q(x) = 1 - u,
+// which for s < 0 is evaluated as e^{-x(x-2s)} [1 + sqrt(pi) s erfcx(y)] / [1 + sqrt(pi) s erfcx(-s)].
+template <typename R>
+__device__ R normal_speed_inverse(R u, R s) {
+  const R target = (R)1 - u;  // exact for u = (2k+1) 2^-24
+  const R sp = (R)kSqrtPiD * s;
+  R zinv;
+  if (s >= (R)0) zinv = (R)1 / (Fn<R>::exp(-s * s) + sp * Fn<R>::erfc(-s));
+  else zinv = (R)1 / ((R)1 + sp * Fn<R>::erfcx(-s));
+  R lo = 0, hi = fmax(s, (R)0) + (R)6.5;
+  const R L = -Fn<R>::log(target);
+  R x;
+  if (s >= (R)1.5) x = s + (R)0.70710678118654752 * Fn<R>::ncdfinv(u) + (R)0.5 / s;
+  else if (s >= (R)0) x = (R)0.5 * s + Fn<R>::sqrt((R)0.25 * s * s + L);
+  else x = Fn<R>::sqrt(L) / ((R)1 - s);
+  if (!(x > lo && x < hi)) x = (R)0.5 * (lo + hi);
+#pragma unroll 1
+  for (int it = 0; it < Fn<R>::kIter; ++it) {
+    const R y = x - s;
+    R Q, p;
+    if (s >= (R)0) {
+      const R e = Fn<R>::exp(-y * y);
+      Q = (e + sp * Fn<R>::erfc(y)) * zinv;
+      p = (R)2 * x * e * zinv;
+    } else {
+      const R e = Fn<R>::exp(-x * (x - (R)2 * s));
+      Q = e * ((R)1 + sp * Fn<R>::erfcx(y)) * zinv;
+      p = (R)2 * x * e * zinv;
+    }
+    const R f = Q - target;  // Q decreases in x
+    if (f == (R)0) break;
+    if (f > (R)0) lo = x; else hi = x;
+    R xn = (p > (R)0) ? x + f / p : (R)0.5 * (lo + hi);
+    if (!(xn > lo && xn < hi)) xn = (R)0.5 * (lo + hi);
+    const R step = Fn<R>::fabs(xn - x);
+    x = xn;
+    if (step <= Fn<R>::kTol * (x + (R)1e-3)) break;
+  }
+  return x;
+}
+
+// Seed particle pid of query q: position on the CV (body frame, m) and
+// velocity (c_mp units).  Stream frame: flow along +z, upstream pole at -z;
+// local frame n (inward), t1 (tangential projection of the flow), t2 = t1 x n;
+// Eq. 14b-c tangential laws by Box-Muller; Eq. 15 rotation to the body frame.
+template <typename R>
+__device__ __forceinline__ void seed_particle(const QueryDev& q, const QC<R>& c, uint64_t pid, R pos[3],
+                                              R vel[3]) {
+  const uint4 w0 = draws(q, pid, 0);
+  const uint4 w1 = draws(q, pid, 1);
+  const R x = latitude_inverse<R>(uniform<R>(w0.x), q, c);
+  const R cphi = Fn<R>::sqrt(((R)1 - x) * ((R)1 + x));
+  R st, ct;
+  Fn<R>::sincospi((R)2 * uniform<R>(w0.y), &st, &ct);
+  const R vn = normal_speed_inverse<R>(uniform<R>(w0.z), c.S * x);
+  const R rad = Fn<R>::sqrt(-Fn<R>::log(uniform<R>(w0.w)));
+  R sa, ca;
+  Fn<R>::sincospi((R)2 * uniform<R>(w1.x), &sa, &ca);
+  const R vt1 = c.S * cphi + rad * ca;
+  const R vt2 = rad * sa;
+  // stream-frame vectors: out = (cphi ct, cphi st, -x), n = -out, t1 = (x ct, x st, cphi), t2 = (st, -ct, 0)
+  const R ps[3] = {cphi * ct, cphi * st, -x};
+  const R vs[3] = {-vn * cphi * ct + vt1 * x * ct + vt2 * st, -vn * cphi * st + vt1 * x * st - vt2 * ct,
+                   vn * x + vt1 * cphi};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const R rp = c.Rm[3 * i] * ps[0] + c.Rm[3 * i + 1] * ps[1] + c.Rm[3 * i + 2] * ps[2];
+    pos[i] = c.center[i] + c.r_cv * rp;
+    vel[i] = c.Rm[3 * i] * vs[0] + c.Rm[3 * i + 1] * vs[1] + c.Rm[3 * i + 2] * vs[2];
+  }
+}
+
+// --------------------------------------------------- closest hit (§II.A)
+template <typename R>
+__device__ __forceinline__ R pick(const R v[3], int k) {
+  return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]);
+}
+
+template <typename R> struct TriLoad;
+template <> struct TriLoad<float> {
+  static __device__ __forceinline__ uint32_t load(const MeshDev& m, uint32_t k, float A[3], float B[3], float C[3]) {
+    const float4 a = __ldg(&m.tris[3 * k]), b = __ldg(&m.tris[3 * k + 1]), c = __ldg(&m.tris[3 * k + 2]);
+    A[0] = a.x; A[1] = a.y; A[2] = a.z;
+    B[0] = b.x; B[1] = b.y; B[2] = b.z;
+    C[0] = c.x; C[1] = c.y; C[2] = c.z;
+    return __float_as_uint(a.w);
+  }
+};
+template <> struct TriLoad<double> {
+  static __device__ __forceinline__ uint32_t load(const MeshDev& m, uint32_t k, double A[3], double B[3],
+                                                  double C[3]) {
+    const double2* p = reinterpret_cast<const double2*>(m.tris64 + 12 * (size_t)k);
+    const double2 p0 = __ldg(p), p1 = __ldg(p + 1), p2 = __ldg(p + 2), p3 = __ldg(p + 3), p4 = __ldg(p + 4);
+    A[0] = p0.x; A[1] = p0.y; A[2] = p1.x;
+    B[0] = p1.y; B[1] = p2.x; B[2] = p2.y;
+    C[0] = p3.x; C[1] = p3.y; C[2] = p4.x;
+    return (uint32_t)p4.y;
+  }
+};
+
+// Edge function without contraction so that a shared edge evaluates to exactly
+// opposite values in its two triangles (watertightness).
+__device__ __forceinline__ float edge_fn(float a, float b, float c, float d) {
+  return __fsub_rn(__fmul_rn(a, b), __fmul_rn(c, d));
+}
+__device__ __forceinline__ double edge_fn(double a, double b, double c, double d) {
+  return __dsub_rn(__dmul_rn(a, b), __dmul_rn(c, d));
+}
+
+template <typename R>
+struct Ray {
+  R o[3], d[3], inv[3], oi[3];
+  R Sx, Sy, Sz;
+  int kx, ky, kz;
+  R tlo;
+};
+
+template <typename R>
+__device__ __forceinline__ void make_ray(Ray<R>& r, const R o[3], const R d[3], R tlo) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    r.o[i] = o[i];
+    r.d[i] = d[i];
+    const R di = Fn<R>::fabs(d[i]) < (R)1e-30 ? copysign((R)1e-30, d[i]) : d[i];
+    r.inv[i] = (R)1 / di;
+    r.oi[i] = o[i] * r.inv[i];
+  }
+  // Woop, Benthin & Wald (JCGT 2013): shear the ray onto +z of a permuted frame.
+  const R ax = Fn<R>::fabs(d[0]), ay = Fn<R>::fabs(d[1]), az = Fn<R>::fabs(d[2]);
+  int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+  int kx = kz == 2 ? 0 : kz + 1;
+  int ky = kx == 2 ? 0 : kx + 1;
+  if (pick(d, kz) < (R)0) { const int t = kx; kx = ky; ky = t; }
+  r.kx = kx; r.ky = ky; r.kz = kz;
+  r.Sz = (R)1 / pick(d, kz);
+  r.Sx = pick(d, kx) * r.Sz;
+  r.Sy = pick(d, ky) * r.Sz;
+  r.tlo = tlo;
+}
+
+// Watertight ray/triangle test; updates (tbest, best) by nearest t, then lower index.
+template <typename R>
+__device__ __forceinline__ void test_triangle(const Ray<R>& r, const R V0[3], const R V1[3], const R V2[3],
+                                              uint32_t id, R& tbest, uint32_t& best) {
+  R A[3], B[3], C[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { A[i] = V0[i] - r.o[i]; B[i] = V1[i] - r.o[i]; C[i] = V2[i] - r.o[i]; }
+  const R Akz = pick(A, r.kz), Bkz = pick(B, r.kz), Ckz = pick(C, r.kz);
+  const R Ax = pick(A, r.kx) - r.Sx * Akz, Ay = pick(A, r.ky) - r.Sy * Akz;
+  const R Bx = pick(B, r.kx) - r.Sx * Bkz, By = pick(B, r.ky) - r.Sy * Bkz;
+  const R Cx = pick(C, r.kx) - r.Sx * Ckz, Cy = pick(C, r.ky) - r.Sy * Ckz;
+  R U = edge_fn(Cx, By, Cy, Bx);
+  R V = edge_fn(Ax, Cy, Ay, Cx);
+  R W = edge_fn(Bx, Ay, By, Ax);
+  if (sizeof(R) == 4 && (U == (R)0 || V == (R)0 || W == (R)0)) {
+    // exact-product fallback in double on the edge itself
+    U = (R)((double)Cx * (double)By - (double)Cy * (double)Bx);
+    V = (R)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+    W = (R)((double)Bx * (double)Ay - (double)By * (double)Ax);
+  }
+  if ((U < (R)0 || V < (R)0 || W < (R)0) && (U > (R)0 || V > (R)0 || W > (R)0)) return;
+  R det = U + V + W;
+  if (det == (R)0) return;
+  R T = U * (r.Sz * Akz) + V * (r.Sz * Bkz) + W * (r.Sz * Ckz);
+  if (det < (R)0) { det = -det; T = -T; }
+  if (T <= r.tlo * det || T > tbest * det) return;
+  const R t = T / det;
+  if (t < tbest || (t == tbest && id < best)) { tbest = t; best = id; }
+}
+
+template <typename R>
+__device__ __forceinline__ void slab(R lo, R hi, R inv, R oi, R& tn, R& tf) {
+  const R a = lo * inv - oi, b = hi * inv - oi;
+  tn = fmin(a, b);
+  tf = fmax(a, b);
+}
+
+template <typename R>
+__device__ uint32_t closest_hit(const MeshDev& m, const float4* __restrict__ s_nodes, uint32_t smem_nodes,
+                                const Ray<R>& r, uint32_t last, R& t_hit, uint32_t& n_nodes, uint32_t& n_tris,
+                                int* err) {
+  uint32_t best = 0xFFFFFFFFu;
+  R tbest = (R)CUDART_INF;
+  if (m.n_nodes == 0) return best;
+  int stack_node[kMaxStack];
+  R stack_t[kMaxStack];
+  int sp = 0;
+  int cur = 0;
+  for (;;) {
+    if (cur >= 0) {
+      ++n_nodes;
+      float4 n0, n1, n2, n3;
+      if ((uint32_t)cur < smem_nodes) {
+        n0 = s_nodes[4 * cur]; n1 = s_nodes[4 * cur + 1]; n2 = s_nodes[4 * cur + 2]; n3 = s_nodes[4 * cur + 3];
+      } else {
+        const float4* g = m.nodes + 4 * (size_t)cur;
+        n0 = __ldg(g); n1 = __ldg(g + 1); n2 = __ldg(g + 2); n3 = __ldg(g + 3);
+      }
+      R a0, b0, a1, b1, a2, b2;
+      slab<R>((R)n0.x, (R)n0.y, r.inv[0], r.oi[0], a0, b0);
+      slab<R>((R)n0.z, (R)n0.w, r.inv[1], r.oi[1], a1, b1);
+      slab<R>((R)n2.x, (R)n2.y, r.inv[2], r.oi[2], a2, b2);
+      const R tmin0 = fmax(fmax(a0, a1), fmax(a2, r.tlo));
+      const R tmax0 = fmin(fmin(b0, b1), fmin(b2, tbest));
+      slab<R>((R)n1.x, (R)n1.y, r.inv[0], r.oi[0], a0, b0);
+      slab<R>((R)n1.z, (R)n1.w, r.inv[1], r.oi[1], a1, b1);
+      slab<R>((R)n2.z, (R)n2.w, r.inv[2], r.oi[2], a2, b2);
+      const R tmin1 = fmax(fmax(a0, a1), fmax(a2, r.tlo));
+      const R tmax1 = fmin(fmin(b0, b1), fmin(b2, tbest));
+      const bool h0 = tmin0 <= tmax0, h1 = tmin1 <= tmax1;
+      int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+      if (h0 && h1) {
+        R tfar = tmin1;
+        if (tmin1 < tmin0) { const int t = c0; c0 = c1; c1 = t; tfar = tmin0; }
+        if (sp >= kMaxStack) { atomicOr(err, 1); return 0xFFFFFFFFu; }
+        stack_node[sp] = c1;
+        stack_t[sp] = tfar;
+        ++sp;
+        cur = c0;
+        continue;
+      }
+      if (h0) { cur = c0; continue; }
+      if (h1) { cur = c1; continue; }
+    } else {
+      const uint32_t code = ~(uint32_t)cur;
+      const uint32_t first = code & 0xFFFFFFu, count = code >> 24;
+      for (uint32_t k = first; k < first + count; ++k) {
+        R V0[3], V1[3], V2[3];
+        const uint32_t id = TriLoad<R>::load(m, k, V0, V1, V2);
+        if (id == last) continue;
+        ++n_tris;
+        test_triangle<R>(r, V0, V1, V2, id, tbest, best);
+      }
+    }
+    // pop the next candidate whose entry distance is still below the best hit
+    for (;;) {
+      if (sp == 0) { t_hit = tbest; return best; }
+      --sp;
+      if (stack_t[sp] <= tbest) { cur = stack_node[sp]; break; }
+    }
+  }
+}
+
+// ------------------------------------------------ re-emission (§II.A)
+template <typename R> struct Frame;
+template <> struct Frame<float> {
+  static __device__ __forceinline__ void load(const MeshDev& m, uint32_t id, float n[3], float t1[3]) {
+    const float4 a = __ldg(&m.frames[2 * id]), b = __ldg(&m.frames[2 * id + 1]);
+    n[0] = a.x; n[1] = a.y; n[2] = a.z;
+    t1[0] = b.x; t1[1] = b.y; t1[2] = b.z;
+  }
+};
+template <> struct Frame<double> {
+  static __device__ __forceinline__ void load(const MeshDev& m, uint32_t id, double n[3], double t1[3]) {
+    const double* f = m.frames64 + 8 * (size_t)id;
+    n[0] = __ldg(f); n[1] = __ldg(f + 1); n[2] = __ldg(f + 2);
+    t1[0] = __ldg(f + 4); t1[1] = __ldg(f + 5); t1[2] = __ldg(f + 6);
+  }
+};
+
+// Maxwell model: with probability eps diffuse re-emission from the
+// flux-weighted half-range Maxwellian at T_W about the hit-side normal
+// (normal speed c_W sqrt(-ln u1), tangential c_W sqrt(-ln u2) at angle 2 pi u3
+// in the frame (t1, n x t1)); otherwise specular reflection.
+template <typename R>
+__device__ __forceinline__ void reemit(const QueryDev& q, const QC<R>& c, uint64_t pid, uint32_t bounce,
+                                       const R n[3], const R t1[3], R v[3]) {
+  const uint4 w = draws(q, pid, 2 + bounce);
+  const R vdn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+  if (uniform<double>(w.x) < q.eps) {
+    const R sgn = vdn < (R)0 ? (R)1 : (R)-1;
+    const R vn = c.cw * Fn<R>::sqrt(-Fn<R>::log(uniform<R>(w.y)));
+    const R vt = c.cw * Fn<R>::sqrt(-Fn<R>::log(uniform<R>(w.z)));
+    R s, co;
+    Fn<R>::sincospi((R)2 * uniform<R>(w.w), &s, &co);
+    const R t2[3] = {n[1] * t1[2] - n[2] * t1[1], n[2] * t1[0] - n[0] * t1[2], n[0] * t1[1] - n[1] * t1[0]};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = sgn * vn * n[i] + vt * (co * t1[i] + s * t2[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = v[i] - (R)2 * vdn * n[i];
+  }
+}
+
+__device__ __forceinline__ long long quantize(float x) { return __float2ll_rn(x); }
+__device__ __forceinline__ long long quantize(double x) { return __double2ll_rn(x); }
+
+// Per-lane partial sums for the query the lane is working on.
+struct LaneAcc {
+  long long F[3], T[3];
+  uint32_t hits, hit_particles, truncated, particles, nodes, tris;
+  double d2;
+  int q;
+};
+
+__device__ __forceinline__ void lane_reset(LaneAcc& a, int q) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { a.F[i] = 0; a.T[i] = 0; }
+  a.hits = a.hit_particles = a.truncated = a.particles = a.nodes = a.tris = 0;
+  a.d2 = 0.0;
+  a.q = q;
+}
+
+__device__ __forceinline__ void lane_flush(AccDev* acc, LaneAcc& a) {
+  if (a.q < 0 || a.particles == 0) return;
+  AccDev& A = acc[a.q];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (a.F[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&A.F[i]), (unsigned long long)a.F[i]);
+    if (a.T[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&A.T[i]), (unsigned long long)a.T[i]);
+  }
+  if (a.hits) atomicAdd(&A.hits, (unsigned long long)a.hits);
+  if (a.hit_particles) atomicAdd(&A.hit_particles, (unsigned long long)a.hit_particles);
+  if (a.truncated) atomicAdd(&A.truncated, (unsigned long long)a.truncated);
+  atomicAdd(&A.particles, (unsigned long long)a.particles);
+  if (a.nodes) atomicAdd(&A.nodes, (unsigned long long)a.nodes);
+  if (a.tris) atomicAdd(&A.tris, (unsigned long long)a.tris);
+  if (a.d2 != 0.0) atomicAdd(&A.d2, a.d2);
+}
+
+// Work index g -> item (binary search over item starts).
+__device__ __forceinline__ uint32_t find_item(const ItemDev* items, uint32_t n_items, uint64_t g) {
+  uint32_t lo = 0, hi = n_items;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(&items[mid].g_begin) <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// --------------------------------------------------------- trace kernel
+template <typename R>
+__global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
+  extern __shared__ float4 s_nodes[];
+  const uint32_t n_stage = min(a.smem_nodes, a.mesh.n_nodes);
+  for (uint32_t i = threadIdx.x; i < 4 * n_stage; i += blockDim.x) s_nodes[i] = __ldg(&a.mesh.nodes[i]);
+  __syncthreads();
+
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  LaneAcc acc;
+  lane_reset(acc, -1);
+
+  // particle slot
+  bool active = false;
+  uint64_t pid = 0;
+  int qi = -1;
+  uint32_t bounce = 0, last = 0xFFFFFFFFu;
+  R pos[3], vel[3], dvp[3];
+  QC<R> c;
+  const QueryDev* q = nullptr;
+
+  // warp-private pool of work indices
+  uint64_t pool_base = 0;
+  uint32_t pool_rem = 0;
+  bool drained = false;
+
+  for (;;) {
+    unsigned need = __ballot_sync(kFull, !active);
+    if (need != 0u && !drained) {
+      uint64_t my_g = ~0ull;
+      while (need != 0u) {
+        if (pool_rem == 0) {
+          unsigned long long base = 0;
+          if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)a.chunk);
+          base = __shfl_sync(kFull, base, 0);
+          if (base >= a.total) { drained = true; break; }
+          pool_base = base;
+          const uint64_t left = a.total - base;
+          pool_rem = left < (uint64_t)a.chunk ? (uint32_t)left : a.chunk;
+        }
+        const uint32_t n = __popc(need);
+        const uint32_t take = min(n, pool_rem);
+        const uint32_t rank = __popc(need & lt_mask);
+        if (((need >> lane) & 1u) && rank < take) my_g = pool_base + rank;
+        for (uint32_t k = 0; k < take; ++k) need &= need - 1u;
+        pool_base += take;
+        pool_rem -= take;
+      }
+      if (my_g != ~0ull) {
+        const uint32_t it = find_item(a.items, a.n_items, my_g);
+        const ItemDev item = a.items[it];
+        const int nq = (int)item.query;
+        if (nq != qi) {
+          if (nq != acc.q) { lane_flush(a.acc, acc); lane_reset(acc, nq); }
+          qi = nq;
+          q = &a.queries[qi];
+          c.load(*q);
+        }
+        pid = item.pid_begin + (my_g - item.g_begin);
+        seed_particle<R>(*q, c, pid, pos, vel);
+        if (a.rec.pos != nullptr) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            a.rec.pos[3 * pid + i] = (double)pos[i];
+            a.rec.vel[3 * pid + i] = (double)vel[i];
+          }
+        }
+        active = true;
+        bounce = 0;
+        last = 0xFFFFFFFFu;
+        dvp[0] = dvp[1] = dvp[2] = (R)0;
+      }
+    }
+    if (!__any_sync(kFull, active)) break;
+    if (!active) continue;
+
+    // one free flight: closest hit along the current velocity
+    Ray<R> ray;
+    const R speed = Fn<R>::sqrt(vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
+    // smallest accepted hit distance: 1e-6 m in float, 1e-9 m in double (t is in m per c_mp unit)
+    const R tlo = (sizeof(R) == 4 ? (R)1e-6 : (R)1e-9) / speed;
+    make_ray<R>(ray, pos, vel, tlo);
+    R t_hit = 0;
+    uint32_t n_nodes = 0, n_tris = 0;
+    const uint32_t hit = closest_hit<R>(a.mesh, s_nodes, n_stage, ray, last, t_hit, n_nodes, n_tris, a.error);
+    if (a.count_work) { acc.nodes += n_nodes; acc.tris += n_tris; }
+    bool done = false;
+    if (hit == 0xFFFFFFFFu) {
+      done = true;
+    } else {
+      R nrm[3], t1[3], hp[3], v_in[3];
+      Frame<R>::load(a.mesh, hit, nrm, t1);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) { hp[i] = pos[i] + t_hit * vel[i]; v_in[i] = vel[i]; }
+      reemit<R>(*q, c, pid, bounce, nrm, t1, vel);
+      R dv[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) { dv[i] = v_in[i] - vel[i]; dvp[i] += dv[i]; }
+      const R r0 = hp[0] - c.ref[0], r1 = hp[1] - c.ref[1], r2 = hp[2] - c.ref[2];
+      const R tq[3] = {r1 * dv[2] - r2 * dv[1], r2 * dv[0] - r0 * dv[2], r0 * dv[1] - r1 * dv[0]};
+      long long qf[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        qf[i] = quantize(dv[i] * c.scale);
+        acc.F[i] += qf[i];
+        acc.T[i] += quantize(tq[i] * c.scale);
+      }
+      if (q->panel != nullptr) {
+        long long* pp = q->panel + 3 * (size_t)hit;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          if (qf[i]) atomicAdd(reinterpret_cast<unsigned long long*>(pp + i), (unsigned long long)qf[i]);
+      }
+      if (a.rec.tri != nullptr && bounce < a.rec.K) a.rec.tri[(size_t)pid * a.rec.K + bounce] = hit;
+      ++acc.hits;
+      if (bounce == 0) ++acc.hit_particles;
+      ++bounce;
+      last = hit;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) pos[i] = hp[i];
+      if (bounce >= q->max_bounces) { done = true; ++acc.truncated; }
+    }
+    if (done) {
+      const R d = dvp[0] * c.vhat[0] + dvp[1] * c.vhat[1] + dvp[2] * c.vhat[2];
+      acc.d2 += (double)d * (double)d;
+      ++acc.particles;
+      if (a.rec.n_hits != nullptr) {
+        a.rec.n_hits[pid] = bounce;
+        a.rec.truncated[pid] = (bounce >= q->max_bounces && hit != 0xFFFFFFFFu) ? 1u : 0u;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) a.rec.dv[3 * pid + i] = (double)dvp[i];
+      }
+      active = false;
+    }
+  }
+  lane_flush(a.acc, acc);
+}
+
+// ---------------------------------------------------------- set-up kernel
+__device__ double latitude_cdf_d(double x, double S, double K1, double D) {
+  const double Sx = S * x;
+  return (kSqrtPiD / (4.0 * S) * (2.0 * Sx * Sx + 1.0) * erfc(-Sx) + 0.5 * x * exp(-Sx * Sx) - K1) / D;
+}
+__device__ double latitude_pdf_d(double x, double S, double D) {
+  const double Sx = S * x;
+  return (exp(-Sx * Sx) + kSqrtPiD * Sx * erfc(-Sx)) / D;
+}
+
+// Block b prepares query b.  With `base` set, query b is a copy of *base whose
+// direction / speed ratio come from dirs[b] / Svals[b] (when given) and whose
+// Philox stream is base->stream_id + b; with `items` set, it also writes work
+// item b = particles [0, N) of query b at work indices [b N, (b+1) N).
+__global__ void setup_kernel(QueryDev* qs, const QueryDev* base, const double* dirs, const double* Svals,
+                             ItemDev* items, const uint32_t* slots) {
+  QueryDev& q = qs[slots != nullptr ? slots[blockIdx.x] : blockIdx.x];
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int st = TPMC_OK;
+    if (base != nullptr) {
+      q = *base;
+      q.stream_id = base->stream_id + blockIdx.x;
+    }
+    if (items != nullptr) {
+      ItemDev it;
+      it.g_begin = (uint64_t)blockIdx.x * q.N;
+      it.pid_begin = 0;
+      it.count = q.N;
+      it.query = blockIdx.x;
+      it.pad = 0;
+      items[blockIdx.x] = it;
+    }
+    if (dirs != nullptr)
+      for (int i = 0; i < 3; ++i) q.dir[i] = dirs[3 * blockIdx.x + i];
+    const double c = sqrt(2.0 * kBoltz * q.T_inf / q.m);
+    if (Svals != nullptr) q.V = Svals[blockIdx.x] * c;
+    const double dn = sqrt(q.dir[0] * q.dir[0] + q.dir[1] * q.dir[1] + q.dir[2] * q.dir[2]);
+    if (!(isfinite(q.V) && q.V > 0.0) || !(isfinite(dn) && dn > 0.0)) st = TPMC_EINVAL;
+    const double S = q.V / c;
+    if (!(S >= 0.01 && S <= 50.0)) st = TPMC_EINVAL;
+    if (st == TPMC_OK) {
+      q.S = S;
+      q.c_mp = c;
+      q.cw = sqrt(q.T_W / q.T_inf);
+      double vh[3];
+      for (int i = 0; i < 3; ++i) { vh[i] = q.dir[i] / dn; q.vhat[i] = vh[i]; }
+      // Eq. 15: rotation about u = z x Vhat by beta = acos(z . Vhat), carrying +z onto Vhat.
+      const double ux = -vh[1], uy = vh[0];  // z x Vhat = (-Vy, Vx, 0)
+      const double sb = sqrt(ux * ux + uy * uy);
+      const double cb = fmin(1.0, fmax(-1.0, vh[2]));
+      double Rm[9];
+      if (sb < 1e-12) {
+        const double sg = cb > 0.0 ? 1.0 : -1.0;  // identity, or a half turn about x
+        Rm[0] = 1; Rm[1] = 0; Rm[2] = 0; Rm[3] = 0; Rm[4] = sg; Rm[5] = 0; Rm[6] = 0; Rm[7] = 0; Rm[8] = sg;
+      } else {
+        const double kx = ux / sb, ky = uy / sb;  // unit axis (kx, ky, 0)
+        const double beta = acos(cb);
+        const double cs = cos(beta), sn = sin(beta), oc = 1.0 - cs;
+        Rm[0] = cs + kx * kx * oc; Rm[1] = kx * ky * oc;      Rm[2] = ky * sn;
+        Rm[3] = kx * ky * oc;      Rm[4] = cs + ky * ky * oc; Rm[5] = -kx * sn;
+        Rm[6] = -ky * sn;          Rm[7] = kx * sn;           Rm[8] = cs;
+      }
+      for (int i = 0; i < 9; ++i) { q.R[i] = Rm[i]; q.fR[i] = (float)Rm[i]; }
+      const double eS = exp(-S * S), erS = erf(S);
+      q.Dnorm = eS + kSqrtPiD * (1.0 + 2.0 * S * S) * erS / (2.0 * S);
+      q.K1 = kSqrtPiD / (4.0 * S) * (2.0 * S * S + 1.0) * erfc(S) - 0.5 * eS;
+      q.gamma = (kSqrtPiD * eS + (CUDART_PI / (2.0 * S) + CUDART_PI * S) * erS) * c * q.n * q.r_cv * q.r_cv;
+      q.q_inf = 0.5 * q.n * q.m * q.V * q.V;
+      // fixed point: worst case |v| <= max(S + 8, 8 c_W/c), so every int64 sum fits for
+      // N * max_bounces hits of |dv| <= 2 |v|max and lever arms <= rmax.
+      const double vmax = fmax(S + 8.0, 8.0 * q.cw);
+      const double bound = (double)q.N * (double)q.max_bounces * 2.0 * 1.7320508075688772 * vmax * fmax(1.0, q.rmax);
+      int shift = (int)floor(62.0 - log2(bound));
+      shift = min(shift, 32);
+      if (shift < 8) st = TPMC_EINVAL;
+      q.shift = shift;
+      q.quantum = ldexp(1.0, -shift);
+      q.fS = (float)S;
+      q.fcw = (float)q.cw;
+      q.fr_cv = (float)q.r_cv;
+      q.fsqrtpi_4S = (float)(kSqrtPiD / (4.0 * S));
+      q.fK1 = (float)q.K1;
+      q.fD_inv = (float)(1.0 / q.Dnorm);
+      q.fscale = (float)ldexp(1.0, shift);
+      for (int i = 0; i < 3; ++i) {
+        q.fvhat[i] = (float)vh[i];
+        q.fcenter[i] = (float)q.center[i];
+        q.fref[i] = (float)q.ref[i];
+      }
+    }
+    q.status = st;
+    s_ok = st == TPMC_OK;
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  const double S = q.S, K1 = q.K1, D = q.Dnorm;
+  for (int j = threadIdx.x; j <= kHTable; j += blockDim.x) {
+    double x;
+    if (j == 0) x = -1.0;
+    else if (j == kHTable) x = 1.0;
+    else {
+      const double u = (double)j / kHTable;
+      double lo = -1.0, hi = 1.0;
+      x = 2.0 * u - 1.0;
+      for (int it = 0; it < 200; ++it) {
+        const double f = latitude_cdf_d(x, S, K1, D) - u;
+        if (f == 0.0) break;
+        if (f < 0.0) lo = x; else hi = x;
+        double xn = x - f / latitude_pdf_d(x, S, D);
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        const double step = fabs(xn - x);
+        x = xn;
+        if (step < 1e-15) break;
+      }
+    }
+    q.htab[j] = (float)x;
+  }
+}
+
+// -------------------------------------------------------- final reduction
+// Thread i reduces query slots[i] (or i) into out[i].
+__global__ void finalize_kernel(const QueryDev* qs, const AccDev* acc, uint32_t nq, const uint32_t* slots,
+                                tpmc_result* out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  const uint32_t qi = slots != nullptr ? slots[i] : i;
+  const QueryDev& q = qs[qi];
+  const AccDev& A = acc[qi];
+  tpmc_result r;
+  memset(&r, 0, sizeof(r));
+  r.status = q.status;
+  if (q.status == TPMC_OK) {
+    const double Np = (double)A.particles;
+    double sdv[3], srdv[3];
+    for (int k = 0; k < 3; ++k) {
+      sdv[k] = (double)A.F[k] * q.quantum;
+      srdv[k] = (double)A.T[k] * q.quantum;
+      r.sum_dv_q[k] = A.F[k];
+      r.sum_rdv_q[k] = A.T[k];
+    }
+    // force = (Gamma/N) m c sum(dv) (§II.A); C_D = F . Vhat / (q_inf A_ref) (Eq. 1)
+    const double scale = Np > 0 ? q.gamma / Np * q.m * q.c_mp : 0.0;
+    for (int k = 0; k < 3; ++k) { r.force[k] = scale * sdv[k]; r.torque[k] = scale * srdv[k]; }
+    r.CD = (r.force[0] * q.vhat[0] + r.force[1] * q.vhat[1] + r.force[2] * q.vhat[2]) / (q.q_inf * q.A_ref);
+    const double mean = Np > 0 ? (sdv[0] * q.vhat[0] + sdv[1] * q.vhat[1] + sdv[2] * q.vhat[2]) / Np : 0.0;
+    const double var = Np > 1 ? fmax(0.0, (A.d2 - Np * mean * mean) / (Np - 1.0)) : 0.0;
+    r.CD_sigma = Np > 0 ? q.gamma * q.m * q.c_mp / (q.q_inf * q.A_ref) * sqrt(var / Np) : 0.0;
+    r.S = q.S;
+    r.S_W = q.S / q.cw;
+    r.gamma = q.gamma;
+    r.weight = Np > 0 ? q.gamma / Np : 0.0;
+    r.q_inf = q.q_inf;
+    r.c_mp = q.c_mp;
+    r.r_cv = q.r_cv;
+    for (int k = 0; k < 3; ++k) r.center[k] = q.center[k];
+    r.fixed_quantum = q.quantum;
+    r.n_particles = A.particles;
+    r.n_hits = A.hits;
+    r.n_hit_particles = A.hit_particles;
+    r.n_truncated = A.truncated;
+    r.n_node_visits = A.nodes;
+    r.n_tri_tests = A.tris;
+    if (A.particles != q.N) r.status = TPMC_ECUDA;
+  }
+  out[i] = r;
+}
+
+__global__ void panels_kernel(const QueryDev* q, const long long* panel, const double* frames64, uint32_t n_tri,
+                              double* pressure, double* shear) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_tri) return;
+  const double* f = frames64 + 8 * (size_t)i;
+  const double area = f[3];
+  double p = 0.0, s = 0.0;
+  if (area > 0.0) {
+    const double scale = q->gamma / (double)q->N * q->m * q->c_mp * q->quantum;
+    double F[3];
+    for (int k = 0; k < 3; ++k) F[k] = scale * (double)panel[3 * (size_t)i + k];
+    const double fn = F[0] * f[0] + F[1] * f[1] + F[2] * f[2];
+    p = -fn / area;
+    const double tx = F[0] - fn * f[0], ty = F[1] - fn * f[1], tz = F[2] - fn * f[2];
+    s = sqrt(tx * tx + ty * ty + tz * tz) / area;
+  }
+  if (pressure) pressure[i] = p;
+  if (shear) shear[i] = s;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers
+cudaError_t launch_setup(QueryDev* d_queries, uint32_t nq, const QueryDev* d_base, const double* d_dirs,
+                         const double* d_S, ItemDev* d_items, const uint32_t* d_slots, cudaStream_t stream) {
+  if (nq == 0) return cudaSuccess;
+  setup_kernel<<<nq, 160, 0, stream>>>(d_queries, d_base, d_dirs, d_S, d_items, d_slots);
+  return cudaGetLastError();
+}
+
+size_t trace_smem_bytes(const LaunchCfg& cfg, uint32_t n_nodes) {
+  return (size_t)std::min(cfg.smem_nodes, n_nodes) * 4 * sizeof(float4);
+}
+
+int trace_max_blocks_per_sm(uint32_t precision, const LaunchCfg& cfg, uint32_t n_nodes) {
+  int nb = 0;
+  const size_t smem = trace_smem_bytes(cfg, n_nodes);
+  if (precision == TPMC_FP64)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_kernel<double>, cfg.block, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_kernel<float>, cfg.block, smem);
+  return nb;
+}
+
+cudaError_t launch_trace(const TraceArgs& args, uint32_t precision, const LaunchCfg& cfg, int num_sms,
+                         cudaStream_t stream) {
+  const size_t smem = trace_smem_bytes(cfg, args.mesh.n_nodes);
+  const uint32_t grid = (uint32_t)num_sms * cfg.blocks_per_sm;
+  if (precision == TPMC_FP64) {
+    cudaFuncSetAttribute(trace_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    trace_kernel<double><<<grid, cfg.block, smem, stream>>>(args);
+  } else {
+    cudaFuncSetAttribute(trace_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    trace_kernel<float><<<grid, cfg.block, smem, stream>>>(args);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const QueryDev* d_queries, const AccDev* d_acc, uint32_t nq, const uint32_t* d_slots,
+                            tpmc_result* d_out, cudaStream_t stream) {
+  if (nq == 0) return cudaSuccess;
+  finalize_kernel<<<(nq + 127) / 128, 128, 0, stream>>>(d_queries, d_acc, nq, d_slots, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_panels(const QueryDev* d_query, const long long* d_panel, const float4*, const double* frames64,
+                          uint32_t n_tri, double* d_pressure, double* d_shear, cudaStream_t stream) {
+  if (n_tri == 0) return cudaSuccess;
+  panels_kernel<<<(n_tri + 255) / 256, 256, 0, stream>>>(d_query, d_panel, frames64, n_tri, d_pressure, d_shear);
+  return cudaGetLastError();
+}
+
+}  // namespace tpmc

@@ -1,0 +1,91 @@
+// Host-side context of the TPMC library (not part of the ABI).
+#pragma once
+
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "tpmc_internal.h"
+
+namespace tpmc {
+
+extern thread_local std::string g_last_error;
+tpmc_status fail(tpmc_status st, const std::string& msg);
+tpmc_status cuda_fail(cudaError_t e, const char* where);
+tpmc_status validate_params(const tpmc_params* p);
+
+struct MeshRec {
+  MeshDev dev;
+  void* d_block = nullptr;     // one device allocation holding every mesh array
+  size_t bytes = 0;
+  double center[3] = {0, 0, 0}, radius = 0;
+  uint32_t depth = 0, leaf_max = 0, n_skipped = 0, n_vert = 0;
+  std::vector<double> h_xyz;   // host copy for the control-volume containment check
+  std::vector<uint32_t> h_tri;
+  int in_use = 0;              // queries in flight on this mesh (serving)
+};
+
+struct PanelRec {
+  void* d_panel = nullptr;     // [n_tri][3] int64 fixed-point sums
+  QueryDev query;              // set-up values needed for the conversion
+  tpmc_mesh_id mesh = 0;
+  uint32_t n_tri = 0;
+};
+
+struct Scratch {
+  void* ptr = nullptr;
+  size_t cap = 0;
+};
+
+struct ServeState;  // serve.cpp
+
+tpmc_status fill_query(const MeshRec& m, const tpmc_params* p, uint64_t N, QueryDev* q);
+
+inline uint64_t tune_key(uint32_t n_tri, uint32_t precision) {
+  // size classes: powers of 4 of the triangle count
+  uint32_t cls = 0;
+  while (n_tri > 1 && cls < 16) { n_tri >>= 2; ++cls; }
+  return ((uint64_t)precision << 32) | cls;
+}
+
+struct Ctx {
+  int device = 0;
+  int num_sms = 1;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0, used = 0;
+  std::map<void*, size_t> sizes;
+  std::recursive_mutex mu;
+  std::map<tpmc_mesh_id, MeshRec> meshes;
+  tpmc_mesh_id next_mesh = 1;
+  std::map<tpmc_query_id, PanelRec> panels;
+  tpmc_query_id next_query = 1;
+  bool counters = false;
+  bool manual_launch = false;
+  LaunchCfg manual;
+  LaunchCfg last_cfg;
+  std::map<uint64_t, LaunchCfg> tuned;
+  Scratch s_queries, s_acc, s_items, s_misc, s_base, s_out, s_in;
+  void* h_pinned = nullptr;
+  int* h_err_word = nullptr;
+  ServeState* serve = nullptr;
+
+  tpmc_status alloc(void** p, size_t bytes, const char* what);
+  void release(void* p);
+  tpmc_status grow(Scratch& s, size_t bytes, const char* what);
+  LaunchCfg schedule(const MeshRec& m, uint32_t precision, uint64_t total);
+  tpmc_status run(const MeshRec& m, const QueryDev* h_queries, uint32_t nq, const QueryDev* h_base,
+                  const double* d_dirs, const double* d_S, const ItemDev* h_items, uint32_t n_items,
+                  uint64_t total, uint32_t precision, tpmc_result* d_out, const RecordsDev* rec);
+  tpmc_status check_error_word();
+  ~Ctx();
+};
+
+void stop_serving(Ctx* c);
+
+}  // namespace tpmc

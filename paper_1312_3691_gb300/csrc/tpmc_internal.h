@@ -1,0 +1,150 @@
+// Internal layout shared by the host runtime (api.cpp, bvh.cpp, serve.cpp)
+// and the CUDA kernels (kernels.cu).  Not part of the ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/tpmc.h"
+
+namespace tpmc {
+
+// Knots of the start table for the inverse of the latitude CDF: x_j =
+// H^-1(j / kHTable), j = 0..kHTable (Eq. 11 integrated; the table only seeds
+// Newton's method, the root is solved to float or double precision).
+constexpr int kHTable = 128;
+constexpr int kMaxStack = 64;    // BVH traversal stack (the builder keeps depth below)
+constexpr int kMaxRecordK = 64;  // hits recorded per particle in verification runs
+
+// ---------------------------------------------------------------- mesh (device)
+// BVH node (64 bytes, both children's boxes in one node):
+//   n0 = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
+//   n1 = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//   n2 = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+//   n3 = (child0, child1, 0, 0) as int bits.  child >= 0: inner node index;
+//        child < 0: leaf ~(count << 24 | first), triangles [first, first+count)
+//        of the leaf-ordered triangle arrays; count <= 127.
+// Nodes are numbered breadth first, so nodes [0, k) are the top of the tree
+// and can be staged in shared memory as a block.
+struct MeshDev {
+  const float4* nodes = nullptr;    // [n_nodes][4]
+  const float4* tris = nullptr;     // [n_tri_leaf][3]: (v0, id bits), (v1, 0), (v2, 0)
+  const double* tris64 = nullptr;   // [n_tri_leaf][12]: v0, v1, v2, id, 0, 0
+  const float4* frames = nullptr;   // [n_tri][2] by input index: (n, area), (t1, 0)
+  const double* frames64 = nullptr; // [n_tri][8] by input index: n, area, t1, 0
+  uint32_t n_nodes = 0;
+  uint32_t n_tri = 0;               // input numbering (panel arrays use it)
+  uint32_t n_tri_leaf = 0;          // triangles referenced by leaves (zero-area ones dropped)
+  float scene_radius = 1.0f;
+};
+
+// ------------------------------------------------------------- query (device)
+// One query: inputs copied from tpmc_params, derived values written by the
+// FP64 set-up kernel (flux normalisation, rotation, start table).
+struct QueryDev {
+  // inputs
+  double n, T_inf, m, V, dir[3], T_W, eps, A_ref, ref[3], r_cv, center[3];
+  double rmax;            // bound on |hit point - ref| (mesh extent seen from ref)
+  uint64_t N;             // particles of this query (ids 0..N-1)
+  uint64_t seed;
+  uint32_t stream_id, max_bounces;
+  uint32_t precision;
+  uint32_t pad0;
+  long long* panel;       // [n_tri][3] fixed-point per-triangle sums, or null
+  // derived by the set-up kernel
+  double S, cw, c_mp, gamma, q_inf, Dnorm, K1, vhat[3], R[9];
+  double quantum;         // 2^-shift
+  int32_t shift;          // fixed-point scale 2^shift
+  int32_t status;         // tpmc_status of the set-up
+  float fS, fcw, fr_cv, fsqrtpi_4S, fK1, fD_inv, fscale;
+  float fR[9], fvhat[3], fcenter[3], fref[3];
+  float htab[kHTable + 1];
+};
+
+// Work item: particles [pid_begin, pid_begin + count) of query `query`,
+// occupying global work indices [g_begin, g_begin + count).
+struct ItemDev {
+  uint64_t g_begin;
+  uint64_t pid_begin;
+  uint64_t count;
+  uint32_t query;
+  uint32_t pad;
+};
+
+// Per-query accumulators (device, zeroed before a launch).
+struct AccDev {
+  long long F[3];           // sum of (v_in - v_out), units quantum * c_mp
+  long long T[3];           // sum of (r - ref) x (v_in - v_out), units quantum * m * c_mp
+  unsigned long long hits, hit_particles, truncated, particles, nodes, tris;
+  double d2;                // sum over particles of (their dv . Vhat)^2
+  double pad;
+};
+
+struct RecordsDev {
+  double* pos = nullptr;
+  double* vel = nullptr;
+  double* dv = nullptr;
+  uint32_t* n_hits = nullptr;
+  uint32_t* truncated = nullptr;
+  uint32_t* tri = nullptr;
+  uint32_t K = 0;
+};
+
+struct TraceArgs {
+  MeshDev mesh;
+  const QueryDev* queries;
+  AccDev* acc;
+  const ItemDev* items;
+  uint32_t n_items;
+  uint32_t chunk;             // ids a warp takes per fetch
+  uint32_t smem_nodes;        // nodes staged in shared memory
+  uint32_t count_work;        // 1: count node visits and triangle tests
+  uint64_t total;             // sum of item counts
+  unsigned long long* counter;  // global work counter (zeroed before launch)
+  int* error;                 // device error word (stack overflow)
+  RecordsDev rec;
+};
+
+struct LaunchCfg {
+  uint32_t block = 128;
+  uint32_t blocks_per_sm = 4;
+  uint32_t chunk = 0;
+  uint32_t smem_nodes = 512;
+};
+
+// ------------------------------------------------------------ host launchers
+cudaError_t launch_setup(QueryDev* d_queries, uint32_t nq, const QueryDev* d_base, const double* d_dirs,
+                         const double* d_S, ItemDev* d_items, const uint32_t* d_slots, cudaStream_t stream);
+cudaError_t launch_trace(const TraceArgs& args, uint32_t precision, const LaunchCfg& cfg, int num_sms,
+                         cudaStream_t stream);
+cudaError_t launch_finalize(const QueryDev* d_queries, const AccDev* d_acc, uint32_t nq, const uint32_t* d_slots,
+                            tpmc_result* d_out, cudaStream_t stream);
+cudaError_t launch_panels(const QueryDev* d_query, const long long* d_panel, const float4* frames,
+                          const double* frames64, uint32_t n_tri, double* d_pressure, double* d_shear,
+                          cudaStream_t stream);
+size_t trace_smem_bytes(const LaunchCfg& cfg, uint32_t n_nodes);
+int trace_max_blocks_per_sm(uint32_t precision, const LaunchCfg& cfg, uint32_t n_nodes);
+
+// ---------------------------------------------------------------- BVH (host)
+struct BvhBuild {
+  std::size_t n_nodes = 0;
+  uint32_t depth = 0, leaf_max = 0, n_skipped = 0;
+  // host copies ready for upload
+  float* nodes = nullptr;    // [n_nodes * 16]
+  float* tris = nullptr;     // [n_leaf_tris * 12]
+  double* tris64 = nullptr;  // [n_leaf_tris * 12]
+  float* frames = nullptr;   // [n_tri * 8]
+  double* frames64 = nullptr;// [n_tri * 8]
+  uint32_t n_leaf_tris = 0;
+  double center[3] = {0, 0, 0}, radius = 0;
+  void release();
+};
+
+// Builds a binned-SAH BVH over the mesh.  Returns false (with a message) on
+// invalid input.
+bool build_bvh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t n_tri, uint32_t max_leaf,
+               BvhBuild* out, const char** err);
+
+}  // namespace tpmc

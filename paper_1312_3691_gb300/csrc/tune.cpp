@@ -1,0 +1,91 @@
+// Autotuner of the trace kernel's launch schedule.
+//
+// Candidates: threads per block, shared-memory BVH nodes, resident blocks per
+// SM and the warp fetch size.  Each is timed with CUDA events on a short run of
+// the caller's query; the fastest is kept for the mesh's size class (powers of
+// 4 of the triangle count) and precision, and later launches on meshes of that
+// class use it.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "runtime.h"
+
+using namespace tpmc;
+
+extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* params, uint64_t N_trial,
+                                 tpmc_launch* best) {
+  if (!ctx) return fail(TPMC_EINVAL, "ctx is NULL");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  tpmc_status st = validate_params(params);
+  if (st != TPMC_OK) return st;
+  if (N_trial == 0 || N_trial > (1ull << 30)) return fail(TPMC_EINVAL, "N_trial must be in [1, 2^30]");
+  auto it = c->meshes.find(mesh);
+  if (it == c->meshes.end()) return fail(TPMC_ENOTFOUND, "unknown mesh id");
+  const MeshRec& m = it->second;
+  cudaSetDevice(c->device);
+  QueryDev q;
+  if ((st = fill_query(m, params, N_trial, &q)) != TPMC_OK) return st;
+  ItemDev item;
+  std::memset(&item, 0, sizeof(item));
+  item.count = N_trial;
+  if ((st = c->grow(c->s_out, sizeof(tpmc_result), "result")) != TPMC_OK) return st;
+
+  std::vector<LaunchCfg> cands;
+  const uint32_t nn = m.dev.n_nodes;
+  for (uint32_t block : {64u, 128u, 256u})
+    for (uint32_t sm_nodes : {0u, 256u, 1024u}) {
+      if (sm_nodes > 0 && sm_nodes >= 4 * std::max(nn, 1u) && sm_nodes != 256u) continue;
+      for (uint32_t occ_div : {1u, 2u})
+        for (uint32_t chunk : {0u, 256u}) {
+          LaunchCfg cfg;
+          cfg.block = block;
+          cfg.smem_nodes = std::min(sm_nodes, nn);
+          const int maxb = trace_max_blocks_per_sm(params->precision, cfg, nn);
+          if (maxb < 1) continue;
+          cfg.blocks_per_sm = std::max(1u, (uint32_t)maxb / occ_div);
+          cfg.chunk = chunk;
+          cands.push_back(cfg);
+        }
+    }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const bool had_manual = c->manual_launch;
+  const LaunchCfg old_manual = c->manual;
+  float best_ms = 1e30f;
+  LaunchCfg best_cfg;
+  for (int pass = 0; pass < 2; ++pass) {  // pass 0 warms caches and clocks
+    for (const LaunchCfg& cfg : cands) {
+      c->manual_launch = true;
+      c->manual = cfg;
+      cudaEventRecord(e0, c->stream);
+      st = c->run(m, &q, 1, nullptr, nullptr, nullptr, &item, 1, N_trial, params->precision,
+                  (tpmc_result*)c->s_out.ptr, nullptr);
+      cudaEventRecord(e1, c->stream);
+      if (st != TPMC_OK) break;
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) { st = cuda_fail(e, "tune"); break; }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (pass == 1 && ms < best_ms) { best_ms = ms; best_cfg = c->last_cfg; }
+    }
+    if (st != TPMC_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->manual_launch = had_manual;
+  c->manual = old_manual;
+  if (st != TPMC_OK) return st;
+  if ((st = c->check_error_word()) != TPMC_OK) return st;
+  best_cfg.chunk = 0 == best_cfg.chunk ? 0 : best_cfg.chunk;
+  c->tuned[tune_key(m.dev.n_tri, params->precision)] = best_cfg;
+  if (best) {
+    best->block = best_cfg.block;
+    best->blocks_per_sm = best_cfg.blocks_per_sm;
+    best->chunk = best_cfg.chunk;
+    best->smem_nodes = best_cfg.smem_nodes;
+  }
+  return TPMC_OK;
+}

