@@ -177,9 +177,19 @@ double normal_speed_cdf(double x, double s) {
          normal_speed_norm(s);
 }
 
+// Survival function 1 - F(x) = [e^{-(x-s)^2} + sqrt(pi) s erfc(x-s)] / Z(s) of the same law.
+double normal_speed_survival(double x, double s) {
+  if (x <= 0.0) return 1.0;
+  return (std::exp(-(x - s) * (x - s)) + kSqrtPi * s * std::erfc(x - s)) / normal_speed_norm(s);
+}
+
+// Inverse transform F(x) = u.  Above the median F rounds to 1 in double
+// before the root is resolved, so there the same equation is solved as
+// 1 - F(x) = 1 - u on the survival function (1 - u is exact for these u).
 double normal_speed_inverse(double u, double s) {
   const double hi = std::max(s, 0.0) + 12.0;  // 1 - F(hi) is far below the smallest uniform, 2^-24
-  return bisect_cdf([s](double x) { return normal_speed_cdf(x, s); }, u, 0.0, hi);
+  if (u <= 0.5) return bisect_cdf([s](double x) { return normal_speed_cdf(x, s); }, u, 0.0, hi);
+  return bisect_cdf([s](double x) { return -normal_speed_survival(x, s); }, -(1.0 - u), 0.0, hi);
 }
 
 // Per-area fluxes onto a surface element whose inward-normal speed ratio is s

@@ -133,6 +133,10 @@ def test_normal_speed_normaliser_and_cdf(orc, s):
         x = orc.normal_speed_inverse(u, s)
         assert x > 0
         assert abs(orc.normal_speed_cdf(x, s) - u) < 1e-12
+    # upper tail: the root is resolved to double precision (complement of F, by quadrature)
+    x = orc.normal_speed_inverse(1 - 2.0 ** -24, s)
+    surv, _ = integrate.quad(lambda y: 2 * y * math.exp(-(y - s) ** 2), x, x + 12, epsabs=0, epsrel=1e-13, limit=200)
+    assert abs(surv / orc.normal_speed_norm(s) - 2.0 ** -24) < 1e-9 * 2.0 ** -24
 
 
 # --------------------------------------- joint seeding law (independent sampler)
