@@ -258,7 +258,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     props = torch.cuda.get_device_properties(dev)
     ctx = T.tpmc_create(local)
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated stream: the library launches on it and the CUDA events are recorded on it
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     T.tpmc_set_stream(ctx, stream)
     gs = groups()
     K = len(gs[0]["cases"])

@@ -65,7 +65,8 @@ template <> struct Fn<float> {
   static __device__ __forceinline__ float ncdfinv(float x) { return normcdfinvf(x); }
   static __device__ __forceinline__ void sincospi(float x, float* s, float* c) { sincospif(x, s, c); }
   static __device__ __forceinline__ float fabs(float x) { return fabsf(x); }
-  static constexpr float kTol = 2.5e-7f;
+  static constexpr float kTolLat = 5e-7f;    // latitude: ~5e-7 m on a 1 m control volume
+  static constexpr float kTolSpeed = 1e-6f;  // normal speed: at the float noise floor of the tail forms
   static constexpr int kIter = 12;
 };
 template <> struct Fn<double> {
@@ -77,7 +78,8 @@ template <> struct Fn<double> {
   static __device__ __forceinline__ double ncdfinv(double x) { return ::normcdfinv(x); }
   static __device__ __forceinline__ void sincospi(double x, double* s, double* c) { ::sincospi(x, s, c); }
   static __device__ __forceinline__ double fabs(double x) { return ::fabs(x); }
-  static constexpr double kTol = 4e-16;
+  static constexpr double kTolLat = 1e-14;
+  static constexpr double kTolSpeed = 1e-14;
   static constexpr int kIter = 40;
 };
 
@@ -123,7 +125,9 @@ __device__ __forceinline__ R latitude_pdf(R x, R S, R Dinv) {
   return (Fn<R>::exp(-Sx * Sx) + (R)kSqrtPiD * Sx * Fn<R>::erfc(-Sx)) * Dinv;
 }
 
-// x = H^-1(u): start from the table knots around u, then safeguarded Newton.
+// x = H^-1(u): start from the table knots around u, then safeguarded Newton;
+// in the lower tail (u < 1/16, where H falls off like a Gaussian tail at
+// large S) Newton runs on log H, which converges in a few steps from far away.
 template <typename R>
 __device__ R latitude_inverse(R u, const QueryDev& q, const QC<R>& c) {
   const float uf = (float)u * (float)kHTable;
@@ -131,62 +135,130 @@ __device__ R latitude_inverse(R u, const QueryDev& q, const QC<R>& c) {
   const R t0 = (R)__ldg(&q.htab[j]), t1 = (R)__ldg(&q.htab[j + 1]);
   R lo = fmax(t0 - (R)2e-6, (R)-1), hi = fmin(t1 + (R)2e-6, (R)1);
   R x = t0 + (R)(uf - (float)j) * (t1 - t0);
+  const bool logmode = u < (R)0.0625;
+  const R lu = logmode ? Fn<R>::log(u) : (R)0;
 #pragma unroll 1
   for (int it = 0; it < Fn<R>::kIter; ++it) {
-    const R f = latitude_cdf<R>(x, c.S, c.sqrtpi_4S, c.K1, c.Dinv) - u;
+    const R H = latitude_cdf<R>(x, c.S, c.sqrtpi_4S, c.K1, c.Dinv);
+    const R h = latitude_pdf<R>(x, c.S, c.Dinv);
+    R f, dx;
+    if (logmode) {
+      if (!(H > (R)0)) { lo = x; x = (R)0.5 * (lo + hi); continue; }
+      f = Fn<R>::log(H) - lu;
+      dx = -f * H / h;
+    } else {
+      f = H - u;
+      dx = -f / h;
+    }
     if (f == (R)0) break;
     if (f < (R)0) lo = x; else hi = x;
-    const R d = latitude_pdf<R>(x, c.S, c.Dinv);
-    R xn = x - f / d;
-    if (!(xn > lo && xn < hi)) xn = (R)0.5 * (lo + hi);
-    const R step = Fn<R>::fabs(xn - x);
-    x = xn;
-    if (step <= Fn<R>::kTol * (Fn<R>::fabs(x) + (R)1e-3)) break;
+    // converged: a smaller step would round back onto x (and onto the bracket end)
+    if (Fn<R>::fabs(dx) <= Fn<R>::kTolLat * (Fn<R>::fabs(x) + (R)1e-3)) { x += dx; break; }
+    x += dx;
+    if (!(x > lo && x < hi)) x = (R)0.5 * (lo + hi);
   }
-  return x;
+  return fmin(fmax(x, (R)-1), (R)1);
 }
 
 // Inward normal speed (Eq. 14a, numerator read as 2 v_n/c_mp): x = v_n/c_mp > 0
-// with density 2 x e^{-(x-s)^2} / Z(s).  Solved through the survival function
-//   Q(x) = [e^{-y^2} + sqrt(pi) s erfc(y)] / Z(s),  y = x - s,   Q(x) = 1 - u,
-// which for s < 0 is evaluated as e^{-x(x-2s)} [1 + sqrt(pi) s erfcx(y)] / [1 + sqrt(pi) s erfcx(-s)].
+// with density p(x) = 2 x e^{-(x-s)^2} / Z(s), Z(s) = e^{-s^2} + sqrt(pi) s erfc(-s).
+// The root of F(x) = u is found on the smaller tail, so that the solved
+// probability keeps its digits in float:
+//   u > 1/2: Q(x) = 1 - F(x) = [e^{-y^2} + sqrt(pi) s erfc(y)] / Z, y = x - s
+//            (for s < 0 as e^{-x(x-2s)} [1 + sqrt(pi) s erfcx(y)] / [1 + sqrt(pi) s erfcx(-s)]);
+//   u <= 1/2: F(x) by 4-point Gauss-Legendre on [0, x] near x = 0 (F ~ x^2 there), else
+//            F = [g(s - x) - g(s)] / Z with g(w) = sqrt(pi) s erfc(w) - e^{-w^2}
+//            (for s < 0 as 1 - Q).
+// Newton runs on log Q (additive steps) or log F (multiplicative steps in x,
+// exact for the x^2 law near 0), inside a bisection bracket.
 template <typename R>
 __device__ R normal_speed_inverse(R u, R s) {
-  const R target = (R)1 - u;  // exact for u = (2k+1) 2^-24
   const R sp = (R)kSqrtPiD * s;
-  R zinv;
-  if (s >= (R)0) zinv = (R)1 / (Fn<R>::exp(-s * s) + sp * Fn<R>::erfc(-s));
-  else zinv = (R)1 / ((R)1 + sp * Fn<R>::erfcx(-s));
+  const bool upper = u > (R)0.5;
+  const R target = upper ? (R)1 - u : u;  // 1 - u is exact for u = (2k+1) 2^-24
+  const R lt = Fn<R>::log(target);
+  R Z, Zs;  // Z, and Zs = Z e^{s^2} when s < 0
+  if (s >= (R)0) { Z = Fn<R>::exp(-s * s) + sp * Fn<R>::erfc(-s); Zs = Z; }
+  else { Zs = (R)1 + sp * Fn<R>::erfcx(-s); Z = Zs; }
+  const R xq = fmin((R)0.05, (R)0.3 / ((R)1 + Fn<R>::fabs(s)));
+  const R g_s = sp * Fn<R>::erfc(s) - Fn<R>::exp(-s * s);
   R lo = 0, hi = fmax(s, (R)0) + (R)6.5;
-  const R L = -Fn<R>::log(target);
+  const R L = -Fn<R>::log((R)1 - u);
   R x;
   if (s >= (R)1.5) x = s + (R)0.70710678118654752 * Fn<R>::ncdfinv(u) + (R)0.5 / s;
   else if (s >= (R)0) x = (R)0.5 * s + Fn<R>::sqrt((R)0.25 * s * s + L);
   else x = Fn<R>::sqrt(L) / ((R)1 - s);
+  if (!upper && !(x > lo)) {
+    // small-x asymptote F ~ x^2 e^{-s^2} / Z
+    const R zes = s < (R)0 ? Zs : (s < (R)9 ? Z * Fn<R>::exp(s * s) : (R)1e30);
+    x = Fn<R>::sqrt(u * zes);
+  }
   if (!(x > lo && x < hi)) x = (R)0.5 * (lo + hi);
 #pragma unroll 1
   for (int it = 0; it < Fn<R>::kIter; ++it) {
     const R y = x - s;
-    R Q, p;
+    R T, p;
     if (s >= (R)0) {
       const R e = Fn<R>::exp(-y * y);
-      Q = (e + sp * Fn<R>::erfc(y)) * zinv;
-      p = (R)2 * x * e * zinv;
+      p = (R)2 * x * e / Z;
+      if (upper) {
+        T = (e + sp * Fn<R>::erfc(y)) / Z;
+      } else if (x < xq) {
+        const R gx[4] = {(R)0.06943184420297371, (R)0.33000947820757187, (R)0.6699905217924281, (R)0.9305681557970262};
+        const R gw[4] = {(R)0.17392742256872692, (R)0.3260725774312731, (R)0.3260725774312731, (R)0.17392742256872692};
+        R acc = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const R t = x * gx[k];
+          acc += gw[k] * (R)2 * t * Fn<R>::exp(-(t - s) * (t - s));
+        }
+        T = x * acc / Z;
+      } else {
+        const R w = s - x;
+        T = ((sp * Fn<R>::erfc(w) - Fn<R>::exp(-w * w)) - g_s) / Z;
+      }
     } else {
       const R e = Fn<R>::exp(-x * (x - (R)2 * s));
-      Q = e * ((R)1 + sp * Fn<R>::erfcx(y)) * zinv;
-      p = (R)2 * x * e * zinv;
+      p = (R)2 * x * e / Zs;
+      if (upper) {
+        T = e * ((R)1 + sp * Fn<R>::erfcx(y)) / Zs;
+      } else if (x < xq) {
+        const R gx[4] = {(R)0.06943184420297371, (R)0.33000947820757187, (R)0.6699905217924281, (R)0.9305681557970262};
+        const R gw[4] = {(R)0.17392742256872692, (R)0.3260725774312731, (R)0.3260725774312731, (R)0.17392742256872692};
+        R acc = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const R t = x * gx[k];
+          acc += gw[k] * (R)2 * t * Fn<R>::exp(-t * (t - (R)2 * s));
+        }
+        T = x * acc / Zs;
+      } else {
+        T = (Zs - e * ((R)1 + sp * Fn<R>::erfcx(y))) / Zs;
+      }
     }
-    const R f = Q - target;  // Q decreases in x
+    if (!(T > (R)0)) {
+      // underflow or cancellation: x lies deep in the solved tail
+      if (upper) hi = x; else lo = x;
+      x = (R)0.5 * (lo + hi);
+      continue;
+    }
+    const R f = Fn<R>::log(T) - lt;
     if (f == (R)0) break;
-    if (f > (R)0) lo = x; else hi = x;
-    R xn = (p > (R)0) ? x + f / p : (R)0.5 * (lo + hi);
-    if (!(xn > lo && xn < hi)) xn = (R)0.5 * (lo + hi);
-    const R step = Fn<R>::fabs(xn - x);
-    x = xn;
-    if (step <= Fn<R>::kTol * (x + (R)1e-3)) break;
+    R dx;
+    if (upper) {  // Q decreases in x
+      if (f > (R)0) lo = x; else hi = x;
+      if (!(p > (R)0)) { x = (R)0.5 * (lo + hi); continue; }
+      dx = f * T / p;
+    } else {      // F increases in x; Newton in log x
+      if (f < (R)0) lo = x; else hi = x;
+      if (!(p > (R)0)) { x = (R)0.5 * (lo + hi); continue; }
+      dx = x * (Fn<R>::exp(-f * T / (x * p)) - (R)1);
+    }
+    if (Fn<R>::fabs(dx) <= Fn<R>::kTolSpeed * (x + (R)1e-3)) { x += dx; break; }
+    x += dx;
+    if (!(x > lo && x < hi)) x = (R)0.5 * (lo + hi);
   }
-  return x;
+  return fmax(x, (R)0);
 }
 
 // Seed particle pid of query q: position on the CV (body frame, m) and
