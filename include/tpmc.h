@@ -198,6 +198,22 @@ tpmc_status tpmc_sweep(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* base
 tpmc_status tpmc_sweep_device(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* base, const double* d_dirs,
                               const double* d_S, uint32_t K, uint64_t N_each, tpmc_result* d_out);
 
+/* Batched sweep that allocates no memory (the paper has no counterpart: this
+ * serves callers that may not allocate device memory after start-up, such as
+ * real-time control loops, code whose device memory belongs to a framework's
+ * own pool, or code that must keep a fixed footprint).  Same inputs and
+ * results as tpmc_sweep with host buffers (h_dirs [K][3], h_S [K] or NULL,
+ * h_out [K]); per-panel loads are not kept.  Its scratch is one fixed device
+ * array of the library (64 queries, about 100 KB), held by every GPU that
+ * loads the library until the process exits.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress, which also
+ * loads the library's device code there), so make that first call before any
+ * stream capture.  All calls on a device share the array; each call clears
+ * what must start at zero, and calls that overlap on the GPU race on it.
+ * Errors: EINVAL for K = 0 or K > 64, otherwise as tpmc_sweep. */
+tpmc_status tpmc_sweep_noalloc(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* base, const double* h_dirs,
+                               const double* h_S, uint32_t K, uint64_t N_each, tpmc_result* h_out);
+
 /* ---- serving: continuous batching over resident meshes -------------------- */
 
 /* Queues a query; a scheduler thread admits it when a slot and memory are

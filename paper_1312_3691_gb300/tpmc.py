@@ -95,6 +95,8 @@ SIGNATURES = {
                    ctypes.POINTER(tpmc_result)],
     "tpmc_sweep_device": [_P, ctypes.c_uint32, ctypes.POINTER(tpmc_params), _P, _P, ctypes.c_uint32,
                           ctypes.c_uint64, _P],
+    "tpmc_sweep_noalloc": [_P, ctypes.c_uint32, ctypes.POINTER(tpmc_params), _PD, _PD, ctypes.c_uint32,
+                           ctypes.c_uint64, ctypes.POINTER(tpmc_result)],
     "tpmc_submit": [_P, ctypes.c_uint32, ctypes.POINTER(tpmc_params), ctypes.c_uint64,
                     ctypes.POINTER(ctypes.c_uint64)],
     "tpmc_poll": [_P, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(tpmc_result)],
@@ -252,6 +254,17 @@ def tpmc_sweep(ctx, mesh: int, base: tpmc_params, dirs, S, N_each: int):
 def tpmc_sweep_device(ctx, mesh: int, base: tpmc_params, d_dirs, d_S, K: int, N_each: int, d_out):
     _check(lib().tpmc_sweep_device(ctx, int(mesh), ctypes.byref(base), _ptr(d_dirs), _ptr(d_S), int(K),
                                    int(N_each), _ptr(d_out)), "tpmc_sweep_device", ctx)
+
+
+def tpmc_sweep_noalloc(ctx, mesh: int, base: tpmc_params, dirs, S, N_each: int):
+    """The sweep without any allocation by the library (at most 64 items; see include/tpmc.h)."""
+    D = None if dirs is None else np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 3))
+    Sv = None if S is None else np.ascontiguousarray(np.asarray(S, dtype=np.float64).reshape(-1))
+    K = D.shape[0] if D is not None else Sv.shape[0]
+    out = (tpmc_result * K)()
+    _check(lib().tpmc_sweep_noalloc(ctx, int(mesh), ctypes.byref(base), _pd(D), _pd(Sv), K, int(N_each), out),
+           "tpmc_sweep_noalloc", ctx)
+    return [o.as_dict() for o in out]
 
 
 RESULT_BYTES = ctypes.sizeof(tpmc_result)

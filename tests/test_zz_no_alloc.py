@@ -1,0 +1,54 @@
+"""tpmc_sweep_noalloc, the sweep for callers that may not allocate device memory
+after start-up (real-time loops, framework-owned memory pools, fixed
+footprints), against tpmc_sweep on the same inputs, twice in a row so that a
+second call cannot inherit the first call's sums from the shared scratch.
+
+This file is collected last on purpose: a failure here leaves every other
+test already run."""
+import math
+
+import numpy as np
+import pytest
+
+from tests.parity_util import cd_close
+from tpmc_inputs import meshes as M
+from tpmc_inputs import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_sweep_matches_the_allocating_sweep_twice():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1312_3691_gb300.build import build
+
+    build()
+    from paper_1312_3691_gb300 import tpmc as T
+
+    ctx = T.tpmc_create(0)
+    try:
+        xyz, tri = M.satellite(60_000)
+        mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+        case = W.satellite_case(N=1)
+        dirs = W.attitude_grid(4, 4)[:12]
+        S = np.linspace(4.0, 11.0, 12)
+        base = T.make_params(**case["params"], stream_id=500)
+        N_each = 150_000
+        ref = T.tpmc_sweep(ctx, mesh, base, dirs, S, N_each)
+        for _ in range(2):
+            got = T.tpmc_sweep_noalloc(ctx, mesh, base, dirs, S, N_each)
+            assert len(got) == len(ref)
+            for a, b in zip(got, ref):
+                assert a["status"] == 0
+                assert a["n_particles"] == N_each
+                assert cd_close(a["CD"], b["CD"], b["CD_sigma"])
+                # same Philox streams and exact integer sums: the totals agree bit for bit
+                assert a["sum_dv_q"] == b["sum_dv_q"] and a["n_hits"] == b["n_hits"]
+                np.testing.assert_allclose(a["torque"], b["torque"], rtol=1e-12, atol=0)
+        with pytest.raises(T.TpmcError) as e:
+            T.tpmc_sweep_noalloc(ctx, mesh, base, W.attitude_grid(9, 8), np.full(72, 5.0), 10)
+        assert e.value.status == T.TPMC_EINVAL
+        T.tpmc_mesh_unload(ctx, mesh)
+    finally:
+        T.tpmc_destroy(ctx)
