@@ -403,6 +403,44 @@ def run_ours(args):
     return 0
 
 
+def run_profile_launch(args):
+    """One warm-up and one measured sweep launch of one group of the workload at a
+    reduced particle count, for profiler captures (ncu -k regex:trace_kernel -s 1 -c 1)."""
+    import torch
+
+    from paper_1312_3691_gb300 import tpmc as T
+    from paper_1312_3691_gb300.build import build
+
+    build()
+    shape, gsi = args.profile_launch.split("-")
+    g = [x for x in groups() if x["shape"] == shape and x["eps"] == (1.0 if gsi == "diffuse" else 0.0)][0]
+    ctx = T.tpmc_create(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    T.tpmc_set_stream(ctx, stream)
+    mesh = T.tpmc_mesh_load(ctx, g["xyz"], g["tri"])
+    K = len(g["cases"])
+    dd = torch.tensor(g["dirs"], dtype=torch.float64, device="cuda")
+    ds = torch.tensor(g["S"], dtype=torch.float64, device="cuda")
+    out = torch.zeros(K * T.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    base = T.make_params(**g["base"])
+    times = []
+    for _ in range(2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        T.tpmc_sweep_device(ctx, mesh, base, dd, ds, K, args.profile_n_each, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    res = T.results_from_bytes(out.cpu().numpy().tobytes(), K)
+    assert all(r["status"] == 0 for r in res)
+    n = K * args.profile_n_each
+    print(json.dumps({"profile_launch": args.profile_launch, "particles": n, "ms": times[-1],
+                      "particles_per_s": n / (times[-1] / 1e3), "launch": T.tpmc_get_launch(ctx, mesh)}))
+    T.tpmc_destroy(ctx)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,7 +449,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-launch", default=None,
+                    help="plate-specular|plate-diffuse|cylinder-specular|cylinder-diffuse: one small launch to profile")
+    ap.add_argument("--profile-n-each", type=int, default=100_000)
     args = ap.parse_args()
+    if args.profile_launch:
+        return run_profile_launch(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
