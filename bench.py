@@ -424,6 +424,9 @@ def run_profile_launch(args):
     ds = torch.tensor(g["S"], dtype=torch.float64, device="cuda")
     out = torch.zeros(K * T.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     base = T.make_params(**g["base"])
+    if args.launch:
+        b, bps, ch, sn = (int(x) for x in args.launch.split(","))
+        T.tpmc_set_launch(ctx, block=b, blocks_per_sm=bps, chunk=ch, smem_nodes=sn)
     times = []
     for _ in range(2):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -452,6 +455,7 @@ def main():
     ap.add_argument("--profile-launch", default=None,
                     help="plate-specular|plate-diffuse|cylinder-specular|cylinder-diffuse: one small launch to profile")
     ap.add_argument("--profile-n-each", type=int, default=100_000)
+    ap.add_argument("--launch", default=None, help="block,blocks_per_sm,chunk,smem_nodes for --profile-launch")
     args = ap.parse_args()
     if args.profile_launch:
         return run_profile_launch(args)

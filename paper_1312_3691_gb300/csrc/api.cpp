@@ -124,7 +124,7 @@ LaunchCfg Ctx::schedule(const MeshRec& m, uint32_t precision, uint64_t total) {
   else if (it != tuned.end()) cfg = it->second;
   else {
     cfg.block = 128;
-    cfg.smem_nodes = std::min<uint32_t>(m.dev.n_nodes, precision == TPMC_FP64 ? 256u : 512u);
+    cfg.smem_nodes = 0;  // the hot top of the tree stays in L1; shared-memory staging costs bank conflicts
     cfg.blocks_per_sm = 0;
     cfg.chunk = 0;
   }
@@ -183,6 +183,7 @@ tpmc_status Ctx::run(const MeshRec& m, const QueryDev* h_queries, uint32_t nq, c
   a.counter = d_counter;
   a.error = d_err;
   a.count_work = counters ? 1u : 0u;
+  a.vn_table = vn_table;
   if (rec) a.rec = *rec;
   const LaunchCfg cfg = schedule(m, precision, total);
   a.chunk = cfg.chunk;
@@ -211,6 +212,7 @@ Ctx::~Ctx() {
   for (auto& kv : meshes) release(kv.second.d_block);
   for (Scratch* s : {&s_queries, &s_acc, &s_items, &s_misc, &s_base, &s_out, &s_in})
     release(s->ptr);
+  release(vn_table);
   if (h_pinned) cudaFreeHost(h_pinned);
   if (own_stream) cudaStreamDestroy(own_stream);
 }
@@ -242,6 +244,14 @@ tpmc_status tpmc_create(int device, size_t mem_budget_bytes, tpmc_ctx** out) {
     return cuda_fail(e, "cudaStreamCreate");
   c->stream = c->own_stream;
   if ((e = cudaMallocHost(&c->h_pinned, 4096)) != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+  {
+    void* t = nullptr;
+    tpmc_status st = c->alloc(&t, sizeof(float) * kVnNS * kVnNZ, "normal-speed table");
+    if (st != TPMC_OK) return st;
+    c->vn_table = (float*)t;
+    if ((e = launch_vn_table(c->vn_table, c->stream)) != cudaSuccess) return cuda_fail(e, "normal-speed table");
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(e, "normal-speed table");
+  }
   c->h_err_word = (int*)c->h_pinned;
   *c->h_err_word = 0;
   *out = reinterpret_cast<tpmc_ctx*>(c.release());

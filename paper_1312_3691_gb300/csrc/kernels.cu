@@ -65,9 +65,6 @@ template <> struct Fn<float> {
   static __device__ __forceinline__ float ncdfinv(float x) { return normcdfinvf(x); }
   static __device__ __forceinline__ void sincospi(float x, float* s, float* c) { sincospif(x, s, c); }
   static __device__ __forceinline__ float fabs(float x) { return fabsf(x); }
-  static constexpr float kTolLat = 5e-7f;    // latitude: ~5e-7 m on a 1 m control volume
-  static constexpr float kTolSpeed = 1e-6f;  // normal speed: at the float noise floor of the tail forms
-  static constexpr int kIter = 12;
 };
 template <> struct Fn<double> {
   static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
@@ -125,39 +122,52 @@ __device__ __forceinline__ R latitude_pdf(R x, R S, R Dinv) {
   return (Fn<R>::exp(-Sx * Sx) + (R)kSqrtPiD * Sx * Fn<R>::erfc(-Sx)) * Dinv;
 }
 
-// x = H^-1(u): start from the table knots around u, then safeguarded Newton;
-// in the lower tail (u < 1/16, where H falls off like a Gaussian tail at
-// large S) Newton runs on log H, which converges in a few steps from far away.
+// Interpolated start from a table laid out in z = Phi^-1(u).
+__device__ __forceinline__ float z_table_start(const float* tab, int n, float z, float z_lo, float z_step) {
+  const float f = (z - z_lo) / z_step;
+  const int j = min(max((int)floorf(f), 0), n - 2);
+  const float w = fminf(fmaxf(f - (float)j, 0.0f), 1.0f);
+  return (1.0f - w) * __ldg(&tab[j]) + w * __ldg(&tab[j + 1]);
+}
+
+// x = H^-1(u).  Float: start from the query's table at z = Phi^-1(u) (error
+// ~1e-4), then one Newton step (error ~1e-7 over all tails, S >= 0.5): a
+// fixed step count keeps the warp converged.  Double: the same start, then a
+// safeguarded Newton loop (on log H in the lower tail) to double precision.
 template <typename R>
 __device__ R latitude_inverse(R u, const QueryDev& q, const QC<R>& c) {
-  const float uf = (float)u * (float)kHTable;
-  const int j = min((int)uf, kHTable - 1);
-  const R t0 = (R)__ldg(&q.htab[j]), t1 = (R)__ldg(&q.htab[j + 1]);
-  R lo = fmax(t0 - (R)2e-6, (R)-1), hi = fmin(t1 + (R)2e-6, (R)1);
-  R x = t0 + (R)(uf - (float)j) * (t1 - t0);
-  const bool logmode = u < (R)0.0625;
-  const R lu = logmode ? Fn<R>::log(u) : (R)0;
-#pragma unroll 1
-  for (int it = 0; it < Fn<R>::kIter; ++it) {
+  const float z = normcdfinvf((float)u);
+  R x = (R)z_table_start(q.htab, kHTable + 1, z, (float)kZLo, (float)((kZHi - kZLo) / kHTable));
+  if constexpr (sizeof(R) == 4) {
     const R H = latitude_cdf<R>(x, c.S, c.sqrtpi_4S, c.K1, c.Dinv);
     const R h = latitude_pdf<R>(x, c.S, c.Dinv);
-    R f, dx;
-    if (logmode) {
-      if (!(H > (R)0)) { lo = x; x = (R)0.5 * (lo + hi); continue; }
-      f = Fn<R>::log(H) - lu;
-      dx = -f * H / h;
-    } else {
-      f = H - u;
-      dx = -f / h;
+    if (h > (R)0) x -= (H - u) / h;
+    return fmin(fmax(x, (R)-1), (R)1);
+  } else {
+    R lo = -1, hi = 1;
+    const bool logmode = u < (R)0.0625;
+    const R lu = logmode ? Fn<R>::log(u) : (R)0;
+#pragma unroll 1
+    for (int it = 0; it < Fn<R>::kIter; ++it) {
+      const R H = latitude_cdf<R>(x, c.S, c.sqrtpi_4S, c.K1, c.Dinv);
+      const R h = latitude_pdf<R>(x, c.S, c.Dinv);
+      R f, dx;
+      if (logmode) {
+        if (!(H > (R)0)) { lo = x; x = (R)0.5 * (lo + hi); continue; }
+        f = Fn<R>::log(H) - lu;
+        dx = -f * H / h;
+      } else {
+        f = H - u;
+        dx = -f / h;
+      }
+      if (f == (R)0) break;
+      if (f < (R)0) lo = x; else hi = x;
+      if (Fn<R>::fabs(dx) <= Fn<R>::kTolLat * (Fn<R>::fabs(x) + (R)1e-3)) { x += dx; break; }
+      x += dx;
+      if (!(x > lo && x < hi)) x = (R)0.5 * (lo + hi);
     }
-    if (f == (R)0) break;
-    if (f < (R)0) lo = x; else hi = x;
-    // converged: a smaller step would round back onto x (and onto the bracket end)
-    if (Fn<R>::fabs(dx) <= Fn<R>::kTolLat * (Fn<R>::fabs(x) + (R)1e-3)) { x += dx; break; }
-    x += dx;
-    if (!(x > lo && x < hi)) x = (R)0.5 * (lo + hi);
+    return fmin(fmax(x, (R)-1), (R)1);
   }
-  return fmin(fmax(x, (R)-1), (R)1);
 }
 
 // Inward normal speed (Eq. 14a, numerator read as 2 v_n/c_mp): x = v_n/c_mp > 0
@@ -172,7 +182,7 @@ __device__ R latitude_inverse(R u, const QueryDev& q, const QC<R>& c) {
 // Newton runs on log Q (additive steps) or log F (multiplicative steps in x,
 // exact for the x^2 law near 0), inside a bisection bracket.
 template <typename R>
-__device__ R normal_speed_inverse(R u, R s) {
+__device__ R normal_speed_inverse_adaptive(R u, R s, R x_start) {
   const R sp = (R)kSqrtPiD * s;
   const bool upper = u > (R)0.5;
   const R target = upper ? (R)1 - u : u;  // 1 - u is exact for u = (2k+1) 2^-24
@@ -183,16 +193,7 @@ __device__ R normal_speed_inverse(R u, R s) {
   const R xq = fmin((R)0.05, (R)0.3 / ((R)1 + Fn<R>::fabs(s)));
   const R g_s = sp * Fn<R>::erfc(s) - Fn<R>::exp(-s * s);
   R lo = 0, hi = fmax(s, (R)0) + (R)6.5;
-  const R L = -Fn<R>::log((R)1 - u);
-  R x;
-  if (s >= (R)1.5) x = s + (R)0.70710678118654752 * Fn<R>::ncdfinv(u) + (R)0.5 / s;
-  else if (s >= (R)0) x = (R)0.5 * s + Fn<R>::sqrt((R)0.25 * s * s + L);
-  else x = Fn<R>::sqrt(L) / ((R)1 - s);
-  if (!upper && !(x > lo)) {
-    // small-x asymptote F ~ x^2 e^{-s^2} / Z
-    const R zes = s < (R)0 ? Zs : (s < (R)9 ? Z * Fn<R>::exp(s * s) : (R)1e30);
-    x = Fn<R>::sqrt(u * zes);
-  }
+  R x = x_start;
   if (!(x > lo && x < hi)) x = (R)0.5 * (lo + hi);
 #pragma unroll 1
   for (int it = 0; it < Fn<R>::kIter; ++it) {
@@ -261,20 +262,107 @@ __device__ R normal_speed_inverse(R u, R s) {
   return fmax(x, (R)0);
 }
 
+// Start of the normal-speed solve from the context's table at (s, z = Phi^-1(u));
+// beyond the table's s range: the Gaussian limit s + z / sqrt(2) + 1/(2s)
+// (large s) or the small-x law F ~ x^2 / (Z e^{s^2}) (very negative s).
+__device__ __forceinline__ float normal_speed_start(const float* tab, float s, float z, float u) {
+  const float fs = (s - (float)kVnSLo) / (float)kVnStep;
+  if (!(fs <= (float)(kVnNS - 1))) return s + 0.70710678f * z + 0.5f / s;  // also catches NaN
+  if (!(fs >= 0.0f)) {
+    const float a = -s;
+    const float zs = 1.0f - 1.77245385f * a * erfcxf(a);  // e^{s^2} Z
+    return fmaxf(sqrtf(u * fmaxf(zs, 1e-30f)), 1e-30f);
+  }
+  const int i = min((int)fs, kVnNS - 2);
+  const float a = fminf(fs - (float)i, 1.0f);
+  const float fz = (z - (float)kZLo) / (float)kVnStep;
+  const int j = min(max((int)floorf(fz), 0), kVnNZ - 2);
+  const float b = fminf(fmaxf(fz - (float)j, 0.0f), 1.0f);
+  const float* r0 = tab + i * kVnNZ + j;
+  const float* r1 = r0 + kVnNZ;
+  const float x = (1.0f - a) * ((1.0f - b) * __ldg(r0) + b * __ldg(r0 + 1)) + a * ((1.0f - b) * __ldg(r1) + b * __ldg(r1 + 1));
+  return fmaxf(x, 1e-30f);
+}
+
+// Float: two Newton steps from the table start (error ~1e-4 -> ~1e-8 in the
+// bulk, <= 3e-5 relative at the extreme uniforms), on the survival function
+// above the median and on the CDF below it (selected per lane, no branch on
+// the tail); near x = 0 the CDF comes from 4-point Gauss-Legendre.
+// Double: the table start, then the adaptive loop to double precision.
+template <typename R>
+__device__ R normal_speed_inverse(R u, R s, const float* tab) {
+  const float z = normcdfinvf((float)u);
+  const R x0 = (R)normal_speed_start(tab, (float)s, z, (float)u);
+  if constexpr (sizeof(R) == 8) {
+    return normal_speed_inverse_adaptive<R>(u, s, x0);
+  } else {
+    const float sp = 1.77245385090551602730f * s;
+    const bool upper = u > 0.5f;
+    const float target = upper ? 1.0f - u : u;
+    float Z, Zs, gs = 0.0f;
+    if (s >= 0.0f) {
+      Z = expf(-s * s) + sp * erfcf(-s);
+      Zs = Z;
+      gs = sp * erfcf(s) - expf(-s * s);
+    } else {
+      Zs = 1.0f + sp * erfcxf(-s);
+      Z = Zs;
+    }
+    const float xq = fminf(0.05f, 0.3f / (1.0f + fabsf(s)));
+    float x = x0;
+#pragma unroll 1
+    for (int it = 0; it < 2; ++it) {
+      const float y = x - s;
+      float T, p;
+      if (s >= 0.0f) {
+        const float e = expf(-y * y);
+        p = 2.0f * x * e / Z;
+        const float ec = erfcf(fabsf(y));
+        const float erfc_y = y >= 0.0f ? ec : 2.0f - ec;
+        const float erfc_w = y >= 0.0f ? 2.0f - ec : ec;
+        T = upper ? (e + sp * erfc_y) / Z : ((sp * erfc_w - e) - gs) / Z;
+      } else {
+        const float e = expf(-x * (x - 2.0f * s));
+        p = 2.0f * x * e / Zs;
+        const float qn = e * (1.0f + sp * erfcxf(y));
+        T = upper ? qn / Zs : (Zs - qn) / Zs;
+      }
+      if (!upper && x < xq) {
+        // F near x = 0 by quadrature of p on [0, x] (F ~ x^2 keeps its digits)
+        const float gx[4] = {0.06943184420297371f, 0.33000947820757187f, 0.6699905217924281f, 0.9305681557970262f};
+        const float gw[4] = {0.17392742256872692f, 0.3260725774312731f, 0.3260725774312731f, 0.17392742256872692f};
+        // integrand scaled by e^{s^2} when s < 0 (then divided by Zs = Z e^{s^2})
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float t = x * gx[k];
+          acc += gw[k] * 2.0f * t * expf(s >= 0.0f ? -(t - s) * (t - s) : -t * (t - 2.0f * s));
+        }
+        T = x * acc / (s >= 0.0f ? Z : Zs);
+      }
+      const float f = T - target;
+      const float dx = p > 0.0f ? (upper ? f / p : -f / p) : 0.0f;
+      const float xn = x + dx;
+      x = xn > 0.0f ? xn : 0.5f * x;
+    }
+    return x;
+  }
+}
+
 // Seed particle pid of query q: position on the CV (body frame, m) and
 // velocity (c_mp units).  Stream frame: flow along +z, upstream pole at -z;
 // local frame n (inward), t1 (tangential projection of the flow), t2 = t1 x n;
 // Eq. 14b-c tangential laws by Box-Muller; Eq. 15 rotation to the body frame.
 template <typename R>
-__device__ __forceinline__ void seed_particle(const QueryDev& q, const QC<R>& c, uint64_t pid, R pos[3],
-                                              R vel[3]) {
+__device__ __forceinline__ void seed_particle(const QueryDev& q, const QC<R>& c, const float* vn_table, uint64_t pid,
+                                              R pos[3], R vel[3]) {
   const uint4 w0 = draws(q, pid, 0);
   const uint4 w1 = draws(q, pid, 1);
   const R x = latitude_inverse<R>(uniform<R>(w0.x), q, c);
   const R cphi = Fn<R>::sqrt(((R)1 - x) * ((R)1 + x));
   R st, ct;
   Fn<R>::sincospi((R)2 * uniform<R>(w0.y), &st, &ct);
-  const R vn = normal_speed_inverse<R>(uniform<R>(w0.z), c.S * x);
+  const R vn = normal_speed_inverse<R>(uniform<R>(w0.z), c.S * x, vn_table);
   const R rad = Fn<R>::sqrt(-Fn<R>::log(uniform<R>(w0.w)));
   R sa, ca;
   Fn<R>::sincospi((R)2 * uniform<R>(w1.x), &sa, &ca);
@@ -333,8 +421,11 @@ template <typename R>
 struct Ray {
   R o[3], d[3], inv[3], oi[3];
   R Sx, Sy, Sz;
-  int kx, ky, kz;
+  uint32_t k;  // axis permutation: kx | ky << 2 | kz << 4
   R tlo;
+  __device__ __forceinline__ int kx() const { return k & 3; }
+  __device__ __forceinline__ int ky() const { return (k >> 2) & 3; }
+  __device__ __forceinline__ int kz() const { return (k >> 4) & 3; }
 };
 
 template <typename R>
@@ -353,7 +444,7 @@ __device__ __forceinline__ void make_ray(Ray<R>& r, const R o[3], const R d[3], 
   int kx = kz == 2 ? 0 : kz + 1;
   int ky = kx == 2 ? 0 : kx + 1;
   if (pick(d, kz) < (R)0) { const int t = kx; kx = ky; ky = t; }
-  r.kx = kx; r.ky = ky; r.kz = kz;
+  r.k = (uint32_t)kx | ((uint32_t)ky << 2) | ((uint32_t)kz << 4);
   r.Sz = (R)1 / pick(d, kz);
   r.Sx = pick(d, kx) * r.Sz;
   r.Sy = pick(d, ky) * r.Sz;
@@ -367,10 +458,11 @@ __device__ __forceinline__ void test_triangle(const Ray<R>& r, const R V0[3], co
   R A[3], B[3], C[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) { A[i] = V0[i] - r.o[i]; B[i] = V1[i] - r.o[i]; C[i] = V2[i] - r.o[i]; }
-  const R Akz = pick(A, r.kz), Bkz = pick(B, r.kz), Ckz = pick(C, r.kz);
-  const R Ax = pick(A, r.kx) - r.Sx * Akz, Ay = pick(A, r.ky) - r.Sy * Akz;
-  const R Bx = pick(B, r.kx) - r.Sx * Bkz, By = pick(B, r.ky) - r.Sy * Bkz;
-  const R Cx = pick(C, r.kx) - r.Sx * Ckz, Cy = pick(C, r.ky) - r.Sy * Ckz;
+  const int kx = r.kx(), ky = r.ky(), kz = r.kz();
+  const R Akz = pick(A, kz), Bkz = pick(B, kz), Ckz = pick(C, kz);
+  const R Ax = pick(A, kx) - r.Sx * Akz, Ay = pick(A, ky) - r.Sy * Akz;
+  const R Bx = pick(B, kx) - r.Sx * Bkz, By = pick(B, ky) - r.Sy * Bkz;
+  const R Cx = pick(C, kx) - r.Sx * Ckz, Cy = pick(C, ky) - r.Sy * Ckz;
   R U = edge_fn(Cx, By, Cy, Bx);
   R V = edge_fn(Ax, Cy, Ay, Cx);
   R W = edge_fn(Bx, Ay, By, Ax);
@@ -397,70 +489,84 @@ __device__ __forceinline__ void slab(R lo, R hi, R inv, R oi, R& tn, R& tf) {
   tf = fmax(a, b);
 }
 
+// Resumable traversal of one ray: the lane's position in the tree (current
+// node or leaf, stack) and its best hit so far.  One call of trav_step
+// processes one inner node or one leaf, so a warp can interleave rays that
+// are at different depths and hand a finished lane new work at once.
 template <typename R>
-__device__ uint32_t closest_hit(const MeshDev& m, const float4* __restrict__ s_nodes, uint32_t smem_nodes,
-                                const Ray<R>& r, uint32_t last, R& t_hit, uint32_t& n_nodes, uint32_t& n_tris,
-                                int* err) {
-  uint32_t best = 0xFFFFFFFFu;
-  R tbest = (R)CUDART_INF;
-  if (m.n_nodes == 0) return best;
-  int stack_node[kMaxStack];
-  R stack_t[kMaxStack];
-  int sp = 0;
-  int cur = 0;
-  for (;;) {
-    if (cur >= 0) {
-      ++n_nodes;
-      float4 n0, n1, n2, n3;
-      if ((uint32_t)cur < smem_nodes) {
-        n0 = s_nodes[4 * cur]; n1 = s_nodes[4 * cur + 1]; n2 = s_nodes[4 * cur + 2]; n3 = s_nodes[4 * cur + 3];
-      } else {
-        const float4* g = m.nodes + 4 * (size_t)cur;
-        n0 = __ldg(g); n1 = __ldg(g + 1); n2 = __ldg(g + 2); n3 = __ldg(g + 3);
-      }
-      R a0, b0, a1, b1, a2, b2;
-      slab<R>((R)n0.x, (R)n0.y, r.inv[0], r.oi[0], a0, b0);
-      slab<R>((R)n0.z, (R)n0.w, r.inv[1], r.oi[1], a1, b1);
-      slab<R>((R)n2.x, (R)n2.y, r.inv[2], r.oi[2], a2, b2);
-      const R tmin0 = fmax(fmax(a0, a1), fmax(a2, r.tlo));
-      const R tmax0 = fmin(fmin(b0, b1), fmin(b2, tbest));
-      slab<R>((R)n1.x, (R)n1.y, r.inv[0], r.oi[0], a0, b0);
-      slab<R>((R)n1.z, (R)n1.w, r.inv[1], r.oi[1], a1, b1);
-      slab<R>((R)n2.z, (R)n2.w, r.inv[2], r.oi[2], a2, b2);
-      const R tmin1 = fmax(fmax(a0, a1), fmax(a2, r.tlo));
-      const R tmax1 = fmin(fmin(b0, b1), fmin(b2, tbest));
-      const bool h0 = tmin0 <= tmax0, h1 = tmin1 <= tmax1;
-      int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-      if (h0 && h1) {
-        R tfar = tmin1;
-        if (tmin1 < tmin0) { const int t = c0; c0 = c1; c1 = t; tfar = tmin0; }
-        if (sp >= kMaxStack) { atomicOr(err, 1); return 0xFFFFFFFFu; }
-        stack_node[sp] = c1;
-        stack_t[sp] = tfar;
-        ++sp;
-        cur = c0;
-        continue;
-      }
-      if (h0) { cur = c0; continue; }
-      if (h1) { cur = c1; continue; }
+struct Trav {
+  R tbest;
+  uint32_t best;
+  int cur;  // inner node >= 0, leaf < 0
+  int sp;
+};
+
+template <typename R>
+__device__ __forceinline__ void trav_begin(Trav<R>& t) {
+  t.tbest = (R)CUDART_INF;
+  t.best = 0xFFFFFFFFu;
+  t.cur = 0;
+  t.sp = 0;
+}
+
+// Returns true when the traversal of the ray is finished (stack empty).  A
+// mesh without nodes (no triangles) has nothing to visit: every ray misses.
+template <typename R>
+__device__ __forceinline__ bool trav_step(const MeshDev& m, const float4* __restrict__ s_nodes, uint32_t n_stage,
+                                          const Ray<R>& r, uint32_t last, Trav<R>& t, int* stack_node, R* stack_t,
+                                          uint32_t& n_nodes, uint32_t& n_tris, int* err) {
+  if (m.n_nodes == 0) return true;
+  if (t.cur >= 0) {
+    ++n_nodes;
+    float4 n0, n1, n2, n3;
+    if ((uint32_t)t.cur < n_stage) {
+      n0 = s_nodes[4 * t.cur]; n1 = s_nodes[4 * t.cur + 1]; n2 = s_nodes[4 * t.cur + 2]; n3 = s_nodes[4 * t.cur + 3];
     } else {
-      const uint32_t code = ~(uint32_t)cur;
-      const uint32_t first = code & 0xFFFFFFu, count = code >> 24;
-      for (uint32_t k = first; k < first + count; ++k) {
-        R V0[3], V1[3], V2[3];
-        const uint32_t id = TriLoad<R>::load(m, k, V0, V1, V2);
-        if (id == last) continue;
-        ++n_tris;
-        test_triangle<R>(r, V0, V1, V2, id, tbest, best);
-      }
+      const float4* g = m.nodes + 4 * (size_t)t.cur;
+      n0 = __ldg(g); n1 = __ldg(g + 1); n2 = __ldg(g + 2); n3 = __ldg(g + 3);
     }
-    // pop the next candidate whose entry distance is still below the best hit
-    for (;;) {
-      if (sp == 0) { t_hit = tbest; return best; }
-      --sp;
-      if (stack_t[sp] <= tbest) { cur = stack_node[sp]; break; }
+    R a0, b0, a1, b1, a2, b2;
+    slab<R>((R)n0.x, (R)n0.y, r.inv[0], r.oi[0], a0, b0);
+    slab<R>((R)n0.z, (R)n0.w, r.inv[1], r.oi[1], a1, b1);
+    slab<R>((R)n2.x, (R)n2.y, r.inv[2], r.oi[2], a2, b2);
+    const R tmin0 = fmax(fmax(a0, a1), fmax(a2, r.tlo));
+    const R tmax0 = fmin(fmin(b0, b1), fmin(b2, t.tbest));
+    slab<R>((R)n1.x, (R)n1.y, r.inv[0], r.oi[0], a0, b0);
+    slab<R>((R)n1.z, (R)n1.w, r.inv[1], r.oi[1], a1, b1);
+    slab<R>((R)n2.z, (R)n2.w, r.inv[2], r.oi[2], a2, b2);
+    const R tmin1 = fmax(fmax(a0, a1), fmax(a2, r.tlo));
+    const R tmax1 = fmin(fmin(b0, b1), fmin(b2, t.tbest));
+    const bool h0 = tmin0 <= tmax0, h1 = tmin1 <= tmax1;
+    int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+    if (h0 && h1) {
+      R tfar = tmin1;
+      if (tmin1 < tmin0) { const int x = c0; c0 = c1; c1 = x; tfar = tmin0; }
+      if (t.sp >= kMaxStack) { atomicOr(err, 1); return true; }
+      stack_node[t.sp] = c1;
+      stack_t[t.sp] = tfar;
+      ++t.sp;
+      t.cur = c0;
+      return false;
+    }
+    if (h0) { t.cur = c0; return false; }
+    if (h1) { t.cur = c1; return false; }
+  } else {
+    const uint32_t code = ~(uint32_t)t.cur;
+    const uint32_t first = code & 0xFFFFFFu, count = code >> 24;
+    for (uint32_t k = first; k < first + count; ++k) {
+      R V0[3], V1[3], V2[3];
+      const uint32_t id = TriLoad<R>::load(m, k, V0, V1, V2);
+      if (id == last) continue;
+      ++n_tris;
+      test_triangle<R>(r, V0, V1, V2, id, t.tbest, t.best);
     }
   }
+  // next candidate whose entry distance is still below the best hit
+  while (t.sp > 0) {
+    --t.sp;
+    if (stack_t[t.sp] <= t.tbest) { t.cur = stack_node[t.sp]; return false; }
+  }
+  return true;
 }
 
 // ------------------------------------------------ re-emission (§II.A)
@@ -485,14 +591,14 @@ template <> struct Frame<double> {
 // (normal speed c_W sqrt(-ln u1), tangential c_W sqrt(-ln u2) at angle 2 pi u3
 // in the frame (t1, n x t1)); otherwise specular reflection.
 template <typename R>
-__device__ __forceinline__ void reemit(const QueryDev& q, const QC<R>& c, uint64_t pid, uint32_t bounce,
-                                       const R n[3], const R t1[3], R v[3]) {
+__device__ __forceinline__ void reemit(const QueryDev& q, R cw, uint64_t pid, uint32_t bounce, const R n[3],
+                                       const R t1[3], R v[3]) {
   const uint4 w = draws(q, pid, 2 + bounce);
   const R vdn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
   if (uniform<double>(w.x) < q.eps) {
     const R sgn = vdn < (R)0 ? (R)1 : (R)-1;
-    const R vn = c.cw * Fn<R>::sqrt(-Fn<R>::log(uniform<R>(w.y)));
-    const R vt = c.cw * Fn<R>::sqrt(-Fn<R>::log(uniform<R>(w.z)));
+    const R vn = cw * Fn<R>::sqrt(-Fn<R>::log(uniform<R>(w.y)));
+    const R vt = cw * Fn<R>::sqrt(-Fn<R>::log(uniform<R>(w.z)));
     R s, co;
     Fn<R>::sincospi((R)2 * uniform<R>(w.w), &s, &co);
     const R t2[3] = {n[1] * t1[2] - n[2] * t1[1], n[2] * t1[0] - n[0] * t1[2], n[0] * t1[1] - n[1] * t1[0]};
@@ -507,18 +613,21 @@ __device__ __forceinline__ void reemit(const QueryDev& q, const QC<R>& c, uint64
 __device__ __forceinline__ long long quantize(float x) { return __float2ll_rn(x); }
 __device__ __forceinline__ long long quantize(double x) { return __double2ll_rn(x); }
 
-// Per-lane partial sums for the query the lane is working on.
+// Per-lane partial sums for the query the lane is working on.  They live in
+// shared memory (one slot per thread), which keeps them out of the registers
+// the traversal needs.
 struct LaneAcc {
   long long F[3], T[3];
-  uint32_t hits, hit_particles, truncated, particles, nodes, tris;
   double d2;
+  uint32_t hits, hit_particles, truncated, particles;
   int q;
+  uint32_t pad;
 };
 
 __device__ __forceinline__ void lane_reset(LaneAcc& a, int q) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) { a.F[i] = 0; a.T[i] = 0; }
-  a.hits = a.hit_particles = a.truncated = a.particles = a.nodes = a.tris = 0;
+  a.hits = a.hit_particles = a.truncated = a.particles = 0;
   a.d2 = 0.0;
   a.q = q;
 }
@@ -535,9 +644,13 @@ __device__ __forceinline__ void lane_flush(AccDev* acc, LaneAcc& a) {
   if (a.hit_particles) atomicAdd(&A.hit_particles, (unsigned long long)a.hit_particles);
   if (a.truncated) atomicAdd(&A.truncated, (unsigned long long)a.truncated);
   atomicAdd(&A.particles, (unsigned long long)a.particles);
-  if (a.nodes) atomicAdd(&A.nodes, (unsigned long long)a.nodes);
-  if (a.tris) atomicAdd(&A.tris, (unsigned long long)a.tris);
   if (a.d2 != 0.0) atomicAdd(&A.d2, a.d2);
+}
+
+__device__ __forceinline__ void work_flush(AccDev* acc, int q, uint32_t n_nodes, uint32_t n_tris) {
+  if (q < 0) return;
+  if (n_nodes) atomicAdd(&acc[q].nodes, (unsigned long long)n_nodes);
+  if (n_tris) atomicAdd(&acc[q].tris, (unsigned long long)n_tris);
 }
 
 // Work index g -> item (binary search over item starts).
@@ -550,142 +663,247 @@ __device__ __forceinline__ uint32_t find_item(const ItemDev* items, uint32_t n_i
   return lo;
 }
 
-// --------------------------------------------------------- trace kernel
+// Per-query constants of the traced (not seeded) part, in the path's precision.
+template <typename R> struct HitConst;
+template <> struct HitConst<float> {
+  static __device__ __forceinline__ float cw(const QueryDev& q) { return q.fcw; }
+  static __device__ __forceinline__ float scale(const QueryDev& q) { return q.fscale; }
+  static __device__ __forceinline__ float ref(const QueryDev& q, int i) { return q.fref[i]; }
+  static __device__ __forceinline__ float vhat(const QueryDev& q, int i) { return q.fvhat[i]; }
+};
+template <> struct HitConst<double> {
+  static __device__ __forceinline__ double cw(const QueryDev& q) { return q.cw; }
+  static __device__ __forceinline__ double scale(const QueryDev& q) { return 1.0 / q.quantum; }
+  static __device__ __forceinline__ double ref(const QueryDev& q, int i) { return q.ref[i]; }
+  static __device__ __forceinline__ double vhat(const QueryDev& q, int i) { return q.vhat[i]; }
+};
+
+// A seeded particle waiting in its warp's queue (shared memory).
 template <typename R>
-__global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
-  extern __shared__ float4 s_nodes[];
+struct Seeded {
+  R pos[3], vel[3];
+  uint64_t pid;
+  uint32_t q;
+  uint32_t pad;
+};
+
+// Seeds particle pid of query qi into a queue slot.  Kept out of line: the
+// seeding temporaries then do not stay live across the traversal loop.
+template <typename R>
+__device__ __noinline__ void seed_into(const TraceArgs& a, uint32_t qi, uint64_t pid, Seeded<R>& e) {
+  const QueryDev& q = a.queries[qi];
+  QC<R> c;
+  c.load(q);
+  R pos[3], vel[3];
+  seed_particle<R>(q, c, a.vn_table, pid, pos, vel);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { e.pos[i] = pos[i]; e.vel[i] = vel[i]; }
+  e.pid = pid;
+  e.q = qi;
+  if (a.rec.pos != nullptr) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      a.rec.pos[3 * pid + i] = (double)pos[i];
+      a.rec.vel[3 * pid + i] = (double)vel[i];
+    }
+  }
+}
+
+constexpr uint32_t kQueue = 64;     // queue slots per warp (two seeding batches)
+constexpr uint32_t kRefillAt = 8;   // lanes with finished rays that end a traversal round
+
+// --------------------------------------------------------- trace kernel
+// Persistent kernel.  Each warp keeps a queue of seeded particles in shared
+// memory; when its lanes need particles and the queue runs low, all 32 lanes
+// seed one particle each (so the inverse-CDF solves run at full warp width).
+// Lanes then trace in rounds of resumable traversal steps; a round ends when
+// kRefillAt lanes have finished their rays, and those lanes re-emit (next
+// bounce) or finish their particle and take the next one from the queue.
+// MINB > 0: a register-capped instantiation for 128-thread blocks with at
+// least MINB resident blocks per SM (more warps to hide latency, at the cost
+// of spills inside the out-of-line seeding).
+template <typename R, int MINB>
+__global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : 1) trace_kernel(TraceArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t n_stage = min(a.smem_nodes, a.mesh.n_nodes);
+  float4* s_nodes = reinterpret_cast<float4*>(smem);
   for (uint32_t i = threadIdx.x; i < 4 * n_stage; i += blockDim.x) s_nodes[i] = __ldg(&a.mesh.nodes[i]);
+  Seeded<R>* queue = reinterpret_cast<Seeded<R>*>(smem + (size_t)n_stage * 4 * sizeof(float4)) +
+                     (threadIdx.x >> 5) * kQueue;
+  LaneAcc& acc = reinterpret_cast<LaneAcc*>(smem + (size_t)n_stage * 4 * sizeof(float4) +
+                                            (size_t)(blockDim.x >> 5) * kQueue * sizeof(Seeded<R>))[threadIdx.x];
+  lane_reset(acc, -1);
   __syncthreads();
 
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
-  LaneAcc acc;
-  lane_reset(acc, -1);
 
-  // particle slot
-  bool active = false;
-  uint64_t pid = 0;
-  int qi = -1;
-  uint32_t bounce = 0, last = 0xFFFFFFFFu;
-  R pos[3], vel[3], dvp[3];
-  QC<R> c;
-  const QueryDev* q = nullptr;
-
-  // warp-private pool of work indices
+  // warp-uniform state: queue ring, work pool
+  uint32_t q_head = 0, q_count = 0;
   uint64_t pool_base = 0;
   uint32_t pool_rem = 0;
   bool drained = false;
+  // lane's cached work item (for seeding)
+  uint64_t it_g0 = 1, it_g1 = 0, it_pid0 = 0;
+  uint32_t it_q = 0;
+
+  // lane's particle
+  bool has = false, tdone = true;
+  uint64_t pid = 0;
+  int qi = -1;
+  uint32_t bounce = 0, last = 0xFFFFFFFFu;
+  R dvp[3] = {0, 0, 0};
+  Ray<R> ray;
+  Trav<R> tv;
+  trav_begin(tv);
+  int stack_node[kMaxStack];
+  R stack_t[kMaxStack];
+  uint32_t n_nodes = 0, n_tris = 0;
 
   for (;;) {
-    unsigned need = __ballot_sync(kFull, !active);
-    if (need != 0u && !drained) {
-      uint64_t my_g = ~0ull;
-      while (need != 0u) {
+    // ---- 1. lanes whose ray is finished: re-emit, or finish the particle
+    if (has && tdone) {
+      const QueryDev& q = a.queries[qi];
+      bool finish = true;
+      if (tv.best != 0xFFFFFFFFu) {
+        const uint32_t hit = tv.best;
+        R nrm[3], t1[3], hp[3], v_in[3];
+        Frame<R>::load(a.mesh, hit, nrm, t1);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { hp[i] = ray.o[i] + tv.tbest * ray.d[i]; v_in[i] = ray.d[i]; }
+        R v[3] = {ray.d[0], ray.d[1], ray.d[2]};
+        reemit<R>(q, HitConst<R>::cw(q), pid, bounce, nrm, t1, v);
+        R dv[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { dv[i] = v_in[i] - v[i]; dvp[i] += dv[i]; }
+        const R r0 = hp[0] - HitConst<R>::ref(q, 0), r1 = hp[1] - HitConst<R>::ref(q, 1),
+                r2 = hp[2] - HitConst<R>::ref(q, 2);
+        const R tq[3] = {r1 * dv[2] - r2 * dv[1], r2 * dv[0] - r0 * dv[2], r0 * dv[1] - r1 * dv[0]};
+        const R sc = HitConst<R>::scale(q);
+        long long qf[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          qf[i] = quantize(dv[i] * sc);
+          acc.F[i] += qf[i];
+          acc.T[i] += quantize(tq[i] * sc);
+        }
+        long long* panel = q.panel;
+        if (panel != nullptr) {
+          long long* pp = panel + 3 * (size_t)hit;
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+            if (qf[i]) atomicAdd(reinterpret_cast<unsigned long long*>(pp + i), (unsigned long long)qf[i]);
+        }
+        if (a.rec.tri != nullptr && bounce < a.rec.K) a.rec.tri[(size_t)pid * a.rec.K + bounce] = hit;
+        ++acc.hits;
+        if (bounce == 0) ++acc.hit_particles;
+        ++bounce;
+        last = hit;
+        if (bounce >= q.max_bounces) {
+          ++acc.truncated;
+        } else {
+          const R speed = Fn<R>::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+          make_ray<R>(ray, hp, v, (sizeof(R) == 4 ? (R)1e-6 : (R)1e-9) / speed);
+          trav_begin(tv);
+          tdone = a.mesh.n_nodes == 0;
+          finish = false;
+        }
+      }
+      if (finish) {
+        R d = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) d += dvp[i] * HitConst<R>::vhat(q, i);
+        acc.d2 += (double)d * (double)d;
+        ++acc.particles;
+        if (a.rec.n_hits != nullptr) {
+          a.rec.n_hits[pid] = bounce;
+          a.rec.truncated[pid] = (tv.best != 0xFFFFFFFFu && bounce >= q.max_bounces) ? 1u : 0u;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) a.rec.dv[3 * pid + i] = (double)dvp[i];
+        }
+        has = false;
+      }
+    }
+
+    // ---- 2. idle lanes take particles from the queue; seed a batch when it runs low
+    const unsigned need = __ballot_sync(kFull, !has);
+    if (need != 0u) {
+      const uint32_t n_need = __popc(need);
+      if (q_count < n_need && !drained && q_count + 32u <= kQueue) {
         if (pool_rem == 0) {
           unsigned long long base = 0;
           if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)a.chunk);
           base = __shfl_sync(kFull, base, 0);
-          if (base >= a.total) { drained = true; break; }
-          pool_base = base;
-          const uint64_t left = a.total - base;
-          pool_rem = left < (uint64_t)a.chunk ? (uint32_t)left : a.chunk;
-        }
-        const uint32_t n = __popc(need);
-        const uint32_t take = min(n, pool_rem);
-        const uint32_t rank = __popc(need & lt_mask);
-        if (((need >> lane) & 1u) && rank < take) my_g = pool_base + rank;
-        for (uint32_t k = 0; k < take; ++k) need &= need - 1u;
-        pool_base += take;
-        pool_rem -= take;
-      }
-      if (my_g != ~0ull) {
-        const uint32_t it = find_item(a.items, a.n_items, my_g);
-        const ItemDev item = a.items[it];
-        const int nq = (int)item.query;
-        if (nq != qi) {
-          if (nq != acc.q) { lane_flush(a.acc, acc); lane_reset(acc, nq); }
-          qi = nq;
-          q = &a.queries[qi];
-          c.load(*q);
-        }
-        pid = item.pid_begin + (my_g - item.g_begin);
-        seed_particle<R>(*q, c, pid, pos, vel);
-        if (a.rec.pos != nullptr) {
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            a.rec.pos[3 * pid + i] = (double)pos[i];
-            a.rec.vel[3 * pid + i] = (double)vel[i];
+          if (base >= a.total) {
+            drained = true;
+          } else {
+            pool_base = base;
+            const uint64_t left = a.total - base;
+            pool_rem = left < (uint64_t)a.chunk ? (uint32_t)left : a.chunk;
           }
         }
-        active = true;
+        if (!drained) {
+          const uint32_t nb = min(32u, pool_rem);
+          if (lane < nb) {
+            const uint64_t g = pool_base + lane;
+            if (!(g >= it_g0 && g < it_g1)) {
+              const ItemDev item = a.items[find_item(a.items, a.n_items, g)];
+              it_g0 = item.g_begin;
+              it_g1 = item.g_begin + item.count;
+              it_pid0 = item.pid_begin;
+              it_q = item.query;
+            }
+            seed_into<R>(a, it_q, it_pid0 + (g - it_g0), queue[(q_head + q_count + lane) & (kQueue - 1)]);
+          }
+          pool_base += nb;
+          pool_rem -= nb;
+          q_count += nb;
+        }
+        __syncwarp();
+      }
+      const uint32_t take = min(n_need, q_count);
+      const uint32_t rank = __popc(need & lt_mask);
+      if (((need >> lane) & 1u) && rank < take) {
+        const Seeded<R>& e = queue[(q_head + rank) & (kQueue - 1)];
+        pid = e.pid;
+        const int nq = (int)e.q;
+        if (nq != acc.q) {
+          if (a.count_work) { work_flush(a.acc, acc.q, n_nodes, n_tris); n_nodes = n_tris = 0; }
+          lane_flush(a.acc, acc);
+          lane_reset(acc, nq);
+        }
+        qi = nq;
+        R pos[3] = {e.pos[0], e.pos[1], e.pos[2]}, vel[3] = {e.vel[0], e.vel[1], e.vel[2]};
+        const R speed = Fn<R>::sqrt(vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
+        make_ray<R>(ray, pos, vel, (sizeof(R) == 4 ? (R)1e-6 : (R)1e-9) / speed);
+        trav_begin(tv);
+        tdone = a.mesh.n_nodes == 0;
+        has = true;
         bounce = 0;
         last = 0xFFFFFFFFu;
         dvp[0] = dvp[1] = dvp[2] = (R)0;
       }
+      q_head = (q_head + take) & (kQueue - 1);
+      q_count -= take;
+      __syncwarp();
     }
-    if (!__any_sync(kFull, active)) break;
-    if (!active) continue;
 
-    // one free flight: closest hit along the current velocity
-    Ray<R> ray;
-    const R speed = Fn<R>::sqrt(vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
-    // smallest accepted hit distance: 1e-6 m in float, 1e-9 m in double (t is in m per c_mp unit)
-    const R tlo = (sizeof(R) == 4 ? (R)1e-6 : (R)1e-9) / speed;
-    make_ray<R>(ray, pos, vel, tlo);
-    R t_hit = 0;
-    uint32_t n_nodes = 0, n_tris = 0;
-    const uint32_t hit = closest_hit<R>(a.mesh, s_nodes, n_stage, ray, last, t_hit, n_nodes, n_tris, a.error);
-    if (a.count_work) { acc.nodes += n_nodes; acc.tris += n_tris; }
-    bool done = false;
-    if (hit == 0xFFFFFFFFu) {
-      done = true;
-    } else {
-      R nrm[3], t1[3], hp[3], v_in[3];
-      Frame<R>::load(a.mesh, hit, nrm, t1);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) { hp[i] = pos[i] + t_hit * vel[i]; v_in[i] = vel[i]; }
-      reemit<R>(*q, c, pid, bounce, nrm, t1, vel);
-      R dv[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) { dv[i] = v_in[i] - vel[i]; dvp[i] += dv[i]; }
-      const R r0 = hp[0] - c.ref[0], r1 = hp[1] - c.ref[1], r2 = hp[2] - c.ref[2];
-      const R tq[3] = {r1 * dv[2] - r2 * dv[1], r2 * dv[0] - r0 * dv[2], r0 * dv[1] - r1 * dv[0]};
-      long long qf[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        qf[i] = quantize(dv[i] * c.scale);
-        acc.F[i] += qf[i];
-        acc.T[i] += quantize(tq[i] * c.scale);
-      }
-      if (q->panel != nullptr) {
-        long long* pp = q->panel + 3 * (size_t)hit;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-          if (qf[i]) atomicAdd(reinterpret_cast<unsigned long long*>(pp + i), (unsigned long long)qf[i]);
-      }
-      if (a.rec.tri != nullptr && bounce < a.rec.K) a.rec.tri[(size_t)pid * a.rec.K + bounce] = hit;
-      ++acc.hits;
-      if (bounce == 0) ++acc.hit_particles;
-      ++bounce;
-      last = hit;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) pos[i] = hp[i];
-      if (bounce >= q->max_bounces) { done = true; ++acc.truncated; }
+    // ---- 3. the warp is done when nothing is in flight and nothing is left to seed
+    if (!__any_sync(kFull, has)) {
+      if (drained && q_count == 0) break;
+      continue;
     }
-    if (done) {
-      const R d = dvp[0] * c.vhat[0] + dvp[1] * c.vhat[1] + dvp[2] * c.vhat[2];
-      acc.d2 += (double)d * (double)d;
-      ++acc.particles;
-      if (a.rec.n_hits != nullptr) {
-        a.rec.n_hits[pid] = bounce;
-        a.rec.truncated[pid] = (bounce >= q->max_bounces && hit != 0xFFFFFFFFu) ? 1u : 0u;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) a.rec.dv[3 * pid + i] = (double)dvp[i];
-      }
-      active = false;
+
+    // ---- 4. traversal round
+    for (;;) {
+      if (has && !tdone) tdone = trav_step<R>(a.mesh, s_nodes, n_stage, ray, last, tv, stack_node, stack_t, n_nodes,
+                                              n_tris, a.error);
+      const unsigned fin = __ballot_sync(kFull, has && tdone);
+      const unsigned run = __ballot_sync(kFull, has && !tdone);
+      if (run == 0u || (uint32_t)__popc(fin) >= kRefillAt) break;
     }
   }
+  if (a.count_work) work_flush(a.acc, acc.q, n_nodes, n_tris);
   lane_flush(a.acc, acc);
 }
 
@@ -788,10 +1006,9 @@ __global__ void setup_kernel(QueryDev* qs, const QueryDev* base, const double* d
   const double S = q.S, K1 = q.K1, D = q.Dnorm;
   for (int j = threadIdx.x; j <= kHTable; j += blockDim.x) {
     double x;
-    if (j == 0) x = -1.0;
-    else if (j == kHTable) x = 1.0;
-    else {
-      const double u = (double)j / kHTable;
+    {
+      const double zj = kZLo + (kZHi - kZLo) * j / kHTable;
+      const double u = 0.5 * erfc(-zj * 0.70710678118654752440);  // Phi(z_j)
       double lo = -1.0, hi = 1.0;
       x = 2.0 * u - 1.0;
       for (int it = 0; it < 200; ++it) {
@@ -807,6 +1024,36 @@ __global__ void setup_kernel(QueryDev* qs, const QueryDev* base, const double* d
     }
     q.htab[j] = (float)x;
   }
+}
+
+// Normal-speed start table (FP64, once per context): entry (i, j) is the
+// root of F(x; s_i) = Phi(z_j) by bisection, on the survival function above
+// the median (the same law as Eq. 14a; see normal_speed_inverse).
+__global__ void vn_table_kernel(float* tab) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= kVnNS * kVnNZ) return;
+  const int i = k / kVnNZ, j = k % kVnNZ;
+  const double s = kVnSLo + kVnStep * i;
+  const double z = kZLo + kVnStep * j;
+  const double u = 0.5 * erfc(-z * 0.70710678118654752440);
+  const double sp = kSqrtPiD * s;
+  const double Z = exp(-s * s) + sp * erfc(-s);
+  double lo = 0.0, hi = fmax(s, 0.0) + 12.0;
+  for (int it = 0; it < 200; ++it) {
+    const double x = 0.5 * (lo + hi);
+    if (x <= lo || x >= hi) break;
+    const double y = x - s;
+    bool below;
+    if (u <= 0.5) {
+      const double F = (exp(-s * s) - exp(-y * y) + sp * (erfc(-s) - erfc(y))) / Z;
+      below = F < u;
+    } else {
+      const double Q = (exp(-y * y) + sp * erfc(y)) / Z;
+      below = Q > 1.0 - u;
+    }
+    if (below) lo = x; else hi = x;
+  }
+  tab[k] = (float)(0.5 * (lo + hi));
 }
 
 // -------------------------------------------------------- final reduction
@@ -887,31 +1134,65 @@ cudaError_t launch_setup(QueryDev* d_queries, uint32_t nq, const QueryDev* d_bas
   return cudaGetLastError();
 }
 
-size_t trace_smem_bytes(const LaunchCfg& cfg, uint32_t n_nodes) {
-  return (size_t)std::min(cfg.smem_nodes, n_nodes) * 4 * sizeof(float4);
+cudaError_t launch_vn_table(float* d_table, cudaStream_t stream) {
+  vn_table_kernel<<<(kVnNS * kVnNZ + 127) / 128, 128, 0, stream>>>(d_table);
+  return cudaGetLastError();
 }
 
-int trace_max_blocks_per_sm(uint32_t precision, const LaunchCfg& cfg, uint32_t n_nodes) {
+size_t trace_smem_bytes(const LaunchCfg& cfg, uint32_t n_nodes, uint32_t precision) {
+  const size_t queue = (size_t)(cfg.block / 32) * kQueue *
+                       (precision == TPMC_FP64 ? sizeof(Seeded<double>) : sizeof(Seeded<float>));
+  return (size_t)std::min(cfg.smem_nodes, n_nodes) * 4 * sizeof(float4) + queue + (size_t)cfg.block * sizeof(LaneAcc);
+}
+
+namespace {
+using TraceFn = void (*)(TraceArgs);
+
+// Kernel instantiation for a schedule: the register-capped float variants
+// serve 128-thread blocks at 5 or 6 blocks per SM.
+TraceFn pick_trace(uint32_t precision, uint32_t block, uint32_t blocks_per_sm) {
+  if (precision == TPMC_FP64) return trace_kernel<double, 0>;
+  if (block <= 128 && blocks_per_sm >= 6) return trace_kernel<float, 6>;
+  if (block <= 128 && blocks_per_sm == 5) return trace_kernel<float, 5>;
+  return trace_kernel<float, 0>;
+}
+
+int occupancy(TraceFn f, uint32_t block, size_t smem) {
   int nb = 0;
-  const size_t smem = trace_smem_bytes(cfg, n_nodes);
-  if (precision == TPMC_FP64)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_kernel<double>, cfg.block, smem);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_kernel<float>, cfg.block, smem);
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, (int)block, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   return nb;
+}
+}  // namespace
+
+// Largest resident block count over the instantiations that can run `cfg`.
+int trace_max_blocks_per_sm(uint32_t precision, const LaunchCfg& cfg, uint32_t n_nodes) {
+  const size_t smem = trace_smem_bytes(cfg, n_nodes, precision);
+  if (smem > 227 * 1024) return 0;
+  int best = occupancy(pick_trace(precision, cfg.block, 1), cfg.block, smem);
+  if (precision == TPMC_FP32 && cfg.block <= 128) {
+    for (int minb : {5, 6}) {
+      const int nb = occupancy(pick_trace(precision, cfg.block, (uint32_t)minb), cfg.block, smem);
+      if (nb >= minb) best = std::max(best, nb);
+    }
+  }
+  return best;
 }
 
 cudaError_t launch_trace(const TraceArgs& args, uint32_t precision, const LaunchCfg& cfg, int num_sms,
                          cudaStream_t stream) {
-  const size_t smem = trace_smem_bytes(cfg, args.mesh.n_nodes);
+  const size_t smem = trace_smem_bytes(cfg, args.mesh.n_nodes, precision);
   const uint32_t grid = (uint32_t)num_sms * cfg.blocks_per_sm;
-  if (precision == TPMC_FP64) {
-    cudaFuncSetAttribute(trace_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    trace_kernel<double><<<grid, cfg.block, smem, stream>>>(args);
-  } else {
-    cudaFuncSetAttribute(trace_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    trace_kernel<float><<<grid, cfg.block, smem, stream>>>(args);
-  }
+  const TraceFn f = pick_trace(precision, cfg.block, cfg.blocks_per_sm);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  f<<<grid, cfg.block, smem, stream>>>(args);
   return cudaGetLastError();
 }
 

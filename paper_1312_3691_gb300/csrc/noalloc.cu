@@ -110,6 +110,7 @@ extern "C" tpmc_status tpmc_sweep_noalloc(tpmc_ctx* ctx, tpmc_mesh_id mesh, cons
   a.counter = &A->counter;
   a.error = &A->error;
   a.count_work = c->counters ? 1u : 0u;
+  a.vn_table = c->vn_table;
   const LaunchCfg cfg = c->schedule(m, base->precision, a.total);
   a.chunk = cfg.chunk;
   a.smem_nodes = cfg.smem_nodes;

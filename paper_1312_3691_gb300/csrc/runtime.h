@@ -71,6 +71,7 @@ struct Ctx {
   LaunchCfg last_cfg;
   std::map<uint64_t, LaunchCfg> tuned;
   Scratch s_queries, s_acc, s_items, s_misc, s_base, s_out, s_in;
+  float* vn_table = nullptr;   // normal-speed start table, built once at creation
   void* h_pinned = nullptr;
   int* h_err_word = nullptr;
   ServeState* serve = nullptr;

@@ -186,6 +186,7 @@ void loop(ServeState* s) {
       a.counter = s->d_counters + (group_idx++ % 64);
       a.error = s->d_err;
       a.count_work = c->counters ? 1u : 0u;
+      a.vn_table = c->vn_table;
       a.chunk = cfg.chunk;
       a.smem_nodes = cfg.smem_nodes;
       if (e == cudaSuccess) e = launch_trace(a, kv.first.second, cfg, c->num_sms, s->stream);

@@ -11,10 +11,17 @@
 
 namespace tpmc {
 
-// Knots of the start table for the inverse of the latitude CDF: x_j =
-// H^-1(j / kHTable), j = 0..kHTable (Eq. 11 integrated; the table only seeds
-// Newton's method, the root is solved to float or double precision).
+// Start tables of the inverse-CDF solves (they only start Newton's method;
+// the root is then solved in the path's precision).  Both are laid out in
+// z = Phi^-1(u), the standard normal quantile of the uniform, so that the
+// tails are as finely resolved as the bulk.
+// Latitude (Eq. 11), per query: x_j = H^-1(Phi(z_j)), z_j = kZLo + (kZHi - kZLo) j / kHTable.
 constexpr int kHTable = 128;
+constexpr double kZLo = -5.5, kZHi = 5.5;
+// Normal speed (Eq. 14a), one table per context: x(s_i, z_j) with s_i = kVnSLo + i kVnStep
+// (kVnNS rows) and z_j = kZLo + j kVnStep (kVnNZ columns).
+constexpr double kVnSLo = -8.0, kVnStep = 0.25;
+constexpr int kVnNS = 97, kVnNZ = 45;
 constexpr int kMaxStack = 64;    // BVH traversal stack (the builder keeps depth below)
 constexpr int kMaxRecordK = 64;  // hits recorded per particle in verification runs
 
@@ -104,6 +111,7 @@ struct TraceArgs {
   uint64_t total;             // sum of item counts
   unsigned long long* counter;  // global work counter (zeroed before launch)
   int* error;                 // device error word (stack overflow)
+  const float* vn_table;      // [kVnNS][kVnNZ] normal-speed start table
   RecordsDev rec;
 };
 
@@ -117,6 +125,7 @@ struct LaunchCfg {
 // ------------------------------------------------------------ host launchers
 cudaError_t launch_setup(QueryDev* d_queries, uint32_t nq, const QueryDev* d_base, const double* d_dirs,
                          const double* d_S, ItemDev* d_items, const uint32_t* d_slots, cudaStream_t stream);
+cudaError_t launch_vn_table(float* d_table, cudaStream_t stream);
 cudaError_t launch_trace(const TraceArgs& args, uint32_t precision, const LaunchCfg& cfg, int num_sms,
                          cudaStream_t stream);
 cudaError_t launch_finalize(const QueryDev* d_queries, const AccDev* d_acc, uint32_t nq, const uint32_t* d_slots,
@@ -124,7 +133,7 @@ cudaError_t launch_finalize(const QueryDev* d_queries, const AccDev* d_acc, uint
 cudaError_t launch_panels(const QueryDev* d_query, const long long* d_panel, const float4* frames,
                           const double* frames64, uint32_t n_tri, double* d_pressure, double* d_shear,
                           cudaStream_t stream);
-size_t trace_smem_bytes(const LaunchCfg& cfg, uint32_t n_nodes);
+size_t trace_smem_bytes(const LaunchCfg& cfg, uint32_t n_nodes, uint32_t precision);
 int trace_max_blocks_per_sm(uint32_t precision, const LaunchCfg& cfg, uint32_t n_nodes);
 
 // ---------------------------------------------------------------- BVH (host)
