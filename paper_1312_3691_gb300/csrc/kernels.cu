@@ -489,15 +489,20 @@ __device__ __forceinline__ void slab(R lo, R hi, R inv, R oi, R& tn, R& tf) {
   tf = fmax(a, b);
 }
 
-// Resumable traversal of one ray: the lane's position in the tree (current
-// node or leaf, stack) and its best hit so far.  One call of trav_step
-// processes one inner node or one leaf, so a warp can interleave rays that
-// are at different depths and hand a finished lane new work at once.
+// Resumable traversal of one ray, organised as in Aila & Laine's
+// "while-while" scheme with speculative traversal: a warp steps through inner
+// nodes until every searching lane holds a leaf, then all of them test their
+// leaves together, so node visits and triangle tests run in separate, mostly
+// converged loops.  A lane that found a leaf postpones it and keeps descending
+// while other lanes are still searching.
+constexpr int kDone = (int)0x80000000;  // no valid leaf code: first + count would exceed 2^24
+
 template <typename R>
 struct Trav {
   R tbest;
   uint32_t best;
-  int cur;  // inner node >= 0, leaf < 0
+  int cur;   // inner node >= 0; a leaf found while one is postponed (< 0); kDone when the stack is empty
+  int leaf;  // postponed leaf (< 0), or 0 for none
   int sp;
 };
 
@@ -506,67 +511,93 @@ __device__ __forceinline__ void trav_begin(Trav<R>& t) {
   t.tbest = (R)CUDART_INF;
   t.best = 0xFFFFFFFFu;
   t.cur = 0;
+  t.leaf = 0;
   t.sp = 0;
 }
 
-// Returns true when the traversal of the ray is finished (stack empty).  A
-// mesh without nodes (no triangles) has nothing to visit: every ray misses.
+// Next stacked candidate whose entry distance is still below the best hit.
 template <typename R>
-__device__ __forceinline__ bool trav_step(const MeshDev& m, const float4* __restrict__ s_nodes, uint32_t n_stage,
-                                          const Ray<R>& r, uint32_t last, Trav<R>& t, int* stack_node, R* stack_t,
-                                          uint32_t& n_nodes, uint32_t& n_tris, int* err) {
-  if (m.n_nodes == 0) return true;
-  if (t.cur >= 0) {
-    ++n_nodes;
-    float4 n0, n1, n2, n3;
-    if ((uint32_t)t.cur < n_stage) {
-      n0 = s_nodes[4 * t.cur]; n1 = s_nodes[4 * t.cur + 1]; n2 = s_nodes[4 * t.cur + 2]; n3 = s_nodes[4 * t.cur + 3];
-    } else {
-      const float4* g = m.nodes + 4 * (size_t)t.cur;
-      n0 = __ldg(g); n1 = __ldg(g + 1); n2 = __ldg(g + 2); n3 = __ldg(g + 3);
-    }
-    R a0, b0, a1, b1, a2, b2;
-    slab<R>((R)n0.x, (R)n0.y, r.inv[0], r.oi[0], a0, b0);
-    slab<R>((R)n0.z, (R)n0.w, r.inv[1], r.oi[1], a1, b1);
-    slab<R>((R)n2.x, (R)n2.y, r.inv[2], r.oi[2], a2, b2);
-    const R tmin0 = fmax(fmax(a0, a1), fmax(a2, r.tlo));
-    const R tmax0 = fmin(fmin(b0, b1), fmin(b2, t.tbest));
-    slab<R>((R)n1.x, (R)n1.y, r.inv[0], r.oi[0], a0, b0);
-    slab<R>((R)n1.z, (R)n1.w, r.inv[1], r.oi[1], a1, b1);
-    slab<R>((R)n2.z, (R)n2.w, r.inv[2], r.oi[2], a2, b2);
-    const R tmin1 = fmax(fmax(a0, a1), fmax(a2, r.tlo));
-    const R tmax1 = fmin(fmin(b0, b1), fmin(b2, t.tbest));
-    const bool h0 = tmin0 <= tmax0, h1 = tmin1 <= tmax1;
-    int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
-    if (h0 && h1) {
-      R tfar = tmin1;
-      if (tmin1 < tmin0) { const int x = c0; c0 = c1; c1 = x; tfar = tmin0; }
-      if (t.sp >= kMaxStack) { atomicOr(err, 1); return true; }
-      stack_node[t.sp] = c1;
-      stack_t[t.sp] = tfar;
-      ++t.sp;
-      t.cur = c0;
-      return false;
-    }
-    if (h0) { t.cur = c0; return false; }
-    if (h1) { t.cur = c1; return false; }
-  } else {
-    const uint32_t code = ~(uint32_t)t.cur;
-    const uint32_t first = code & 0xFFFFFFu, count = code >> 24;
-    for (uint32_t k = first; k < first + count; ++k) {
-      R V0[3], V1[3], V2[3];
-      const uint32_t id = TriLoad<R>::load(m, k, V0, V1, V2);
-      if (id == last) continue;
-      ++n_tris;
-      test_triangle<R>(r, V0, V1, V2, id, t.tbest, t.best);
-    }
-  }
-  // next candidate whose entry distance is still below the best hit
+__device__ __forceinline__ int trav_pop(Trav<R>& t, const int* stack_node, const R* stack_t) {
   while (t.sp > 0) {
     --t.sp;
-    if (stack_t[t.sp] <= t.tbest) { t.cur = stack_node[t.sp]; return false; }
+    if (stack_t[t.sp] <= t.tbest) return stack_node[t.sp];
   }
-  return true;
+  return kDone;
+}
+
+// One inner node: test both children, continue with the nearer hit child,
+// stack the farther one; the first leaf reached is postponed.
+template <typename R>
+__device__ __forceinline__ void trav_inner(const MeshDev& m, const float4* __restrict__ s_nodes, uint32_t n_stage,
+                                           const Ray<R>& r, Trav<R>& t, int* stack_node, R* stack_t, uint32_t& n_nodes,
+                                           int* err) {
+  ++n_nodes;
+  float4 n0, n1, n2, n3;
+  if ((uint32_t)t.cur < n_stage) {
+    n0 = s_nodes[4 * t.cur]; n1 = s_nodes[4 * t.cur + 1]; n2 = s_nodes[4 * t.cur + 2]; n3 = s_nodes[4 * t.cur + 3];
+  } else {
+    const float4* g = m.nodes + 4 * (size_t)t.cur;
+    n0 = __ldg(g); n1 = __ldg(g + 1); n2 = __ldg(g + 2); n3 = __ldg(g + 3);
+  }
+  R a0, b0, a1, b1, a2, b2;
+  slab<R>((R)n0.x, (R)n0.y, r.inv[0], r.oi[0], a0, b0);
+  slab<R>((R)n0.z, (R)n0.w, r.inv[1], r.oi[1], a1, b1);
+  slab<R>((R)n2.x, (R)n2.y, r.inv[2], r.oi[2], a2, b2);
+  const R tmin0 = fmax(fmax(a0, a1), fmax(a2, r.tlo));
+  const R tmax0 = fmin(fmin(b0, b1), fmin(b2, t.tbest));
+  slab<R>((R)n1.x, (R)n1.y, r.inv[0], r.oi[0], a0, b0);
+  slab<R>((R)n1.z, (R)n1.w, r.inv[1], r.oi[1], a1, b1);
+  slab<R>((R)n2.z, (R)n2.w, r.inv[2], r.oi[2], a2, b2);
+  const R tmin1 = fmax(fmax(a0, a1), fmax(a2, r.tlo));
+  const R tmax1 = fmin(fmin(b0, b1), fmin(b2, t.tbest));
+  const bool h0 = tmin0 <= tmax0, h1 = tmin1 <= tmax1;
+  int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+  if (h0 && h1) {
+    R tfar = tmin1;
+    if (tmin1 < tmin0) { const int x = c0; c0 = c1; c1 = x; tfar = tmin0; }
+    if (t.sp >= kMaxStack) {
+      atomicOr(err, 1);
+      t.cur = kDone;
+      t.leaf = 0;
+      return;
+    }
+    stack_node[t.sp] = c1;
+    stack_t[t.sp] = tfar;
+    ++t.sp;
+    t.cur = c0;
+  } else if (h0) {
+    t.cur = c0;
+  } else if (h1) {
+    t.cur = c1;
+  } else {
+    t.cur = trav_pop(t, stack_node, stack_t);
+  }
+  if (t.cur < 0 && t.cur != kDone && t.leaf == 0) {
+    t.leaf = t.cur;
+    t.cur = trav_pop(t, stack_node, stack_t);
+  }
+}
+
+// The postponed leaf: test its triangles; then a leaf found meanwhile becomes
+// the postponed one.  Returns true when the ray's traversal is finished.
+template <typename R>
+__device__ __forceinline__ bool trav_leaf(const MeshDev& m, const Ray<R>& r, uint32_t last, Trav<R>& t,
+                                          const int* stack_node, const R* stack_t, uint32_t& n_tris) {
+  const uint32_t code = ~(uint32_t)t.leaf;
+  const uint32_t first = code & 0xFFFFFFu, count = code >> 24;
+  for (uint32_t k = first; k < first + count; ++k) {
+    R V0[3], V1[3], V2[3];
+    const uint32_t id = TriLoad<R>::load(m, k, V0, V1, V2);
+    if (id == last) continue;
+    ++n_tris;
+    test_triangle<R>(r, V0, V1, V2, id, t.tbest, t.best);
+  }
+  t.leaf = 0;
+  if (t.cur < 0 && t.cur != kDone) {
+    t.leaf = t.cur;
+    t.cur = trav_pop(t, stack_node, stack_t);
+  }
+  return t.leaf == 0 && t.cur == kDone;
 }
 
 // ------------------------------------------------ re-emission (§II.A)
@@ -894,10 +925,17 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : 1) tra
       continue;
     }
 
-    // ---- 4. traversal round
+    // ---- 4. traversal round: inner nodes until every searching lane holds a
+    // leaf (lanes with a leaf keep descending meanwhile), then the leaves
     for (;;) {
-      if (has && !tdone) tdone = trav_step<R>(a.mesh, s_nodes, n_stage, ray, last, tv, stack_node, stack_t, n_nodes,
-                                              n_tris, a.error);
+      while (__any_sync(kFull, has && !tdone && tv.cur >= 0 && tv.leaf == 0)) {
+        if (has && !tdone && tv.cur >= 0)
+          trav_inner<R>(a.mesh, s_nodes, n_stage, ray, tv, stack_node, stack_t, n_nodes, a.error);
+      }
+      if (has && !tdone) {
+        if (tv.leaf != 0) tdone = trav_leaf<R>(a.mesh, ray, last, tv, stack_node, stack_t, n_tris);
+        else if (tv.cur == kDone) tdone = true;
+      }
       const unsigned fin = __ballot_sync(kFull, has && tdone);
       const unsigned run = __ballot_sync(kFull, has && !tdone);
       if (run == 0u || (uint32_t)__popc(fin) >= kRefillAt) break;
