@@ -33,6 +33,7 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
+from tpmc_inputs import meshes as M  # noqa: E402
 from tpmc_inputs import workloads as W  # noqa: E402
 
 METRIC = "traced particles/s on 1 GB300 (% roofline); C_D err vs oracle; serve p50/p99 ms"
@@ -233,6 +234,131 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------- other configurations
+def measure_satellite(T, ctx):
+    """Concave synthetic satellite (60,656 triangles), 1e8 particles, <= 64 bounces,
+    Maxwell 0.9 diffuse, per-panel pressure and shear (host API, wall clock)."""
+    case = W.satellite_case(N=100_000_000)
+    mesh = T.tpmc_mesh_load(ctx, case["xyz"], case["tri"])
+    try:
+        p = T.make_params(**case["params"], want_panels=True)
+        T.tpmc_trace(ctx, mesh, T.make_params(**case["params"]), 1_000_000)  # warm-up
+        r = T.tpmc_trace(ctx, mesh, p, case["N"])
+        pres, shear = T.tpmc_panels(ctx, r["query_id"], case["tri"].shape[0])
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    return {"workload": case["name"] + ", 1e8 particles, <=64 bounces, eps 0.9, panels",
+            "particles_per_s": case["N"] / (r["ms"] / 1e3), "ms": r["ms"], "CD": r["CD"], "CD_sigma": r["CD_sigma"],
+            "torque_Nm": r["torque"], "hits_per_particle": r["n_hits"] / r["n_particles"],
+            "truncated": r["n_truncated"], "max_abs_pressure_Pa": float(np.abs(pres).max()),
+            "max_shear_Pa": float(shear.max())}
+
+
+def measure_attitude_sweep(T, ctx, torch, stream, dev):
+    """32 x 32 yaw/pitch grid x S in {5, 7.5, 10} on the satellite, 2^20 particles per
+    item: one persistent launch against 3,072 one-query launches (same N, so equal
+    C_D error)."""
+    case = W.satellite_case(N=1)
+    grid = W.attitude_grid(32, 32)
+    dirs = np.concatenate([grid] * 3)
+    S = np.repeat([5.0, 7.5, 10.0], len(grid))
+    K, N_each = len(S), 1 << 20
+    mesh = T.tpmc_mesh_load(ctx, case["xyz"], case["tri"])
+    try:
+        base = T.make_params(**case["params"], stream_id=1 << 20)
+        dd = torch.tensor(dirs, dtype=torch.float64, device=dev)
+        ds = torch.tensor(S, dtype=torch.float64, device=dev)
+        out = torch.zeros(K * T.RESULT_BYTES, dtype=torch.uint8, device=dev)
+        T.tpmc_set_stream(ctx, stream)
+        T.tpmc_sweep_device(ctx, mesh, base, dd[:64], ds[:64], 64, N_each, out)  # warm-up
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        T.tpmc_sweep_device(ctx, mesh, base, dd, ds, K, N_each, out)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        batched_ms = a.elapsed_time(b)
+        res = T.results_from_bytes(out.cpu().numpy().tobytes(), K)
+        T.tpmc_set_stream(ctx, None)
+        c_mp = (2 * W.K_B * case["params"]["T_inf"] / case["params"]["m"]) ** 0.5
+        t0 = time.perf_counter()
+        same = 0
+        for k in range(K):
+            pk = dict(case["params"])
+            pk["dir"] = tuple(dirs[k])
+            pk["V"] = S[k] * c_mp
+            r = T.tpmc_trace(ctx, mesh, T.make_params(**pk, stream_id=(1 << 20) + k), N_each)
+            same += int(r["sum_dv_q"] == res[k]["sum_dv_q"])
+        plain_s = time.perf_counter() - t0
+        T.tpmc_set_stream(ctx, stream)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    n = K * N_each
+    return {"workload": f"satellite 60,656 tri, 1,024 attitudes x S{{5,7.5,10}}, 2^20 particles each",
+            "batched_particles_per_s": n / (batched_ms / 1e3), "batched_ms": batched_ms,
+            "plain_particles_per_s": n / plain_s, "plain_ms": 1e3 * plain_s,
+            "speedup_vs_plain": plain_s / (batched_ms / 1e3), "items_bit_identical_to_plain": same, "items": K,
+            "median_CD_sigma_rel": float(np.median([r["CD_sigma"] / r["CD"] for r in res]))}
+
+
+def measure_serving(T, ctx, n_queries=200, rate=100.0):
+    """Poisson stream over four resident meshes (icosphere 1,280, cylinder 4,096,
+    satellites 60k and 500k): continuous batching (submit/poll) against a server
+    that runs one query per launch in arrival order, on the same arrival times."""
+    import threading as th
+
+    ms = [M.icosphere(3), M.cylinder(), M.satellite(60_000), M.satellite(500_000)]
+    ids = [T.tpmc_mesh_load(ctx, x, t) for x, t in ms]
+    stream = W.serving_stream(n_queries, rate, seed=3)
+    st = W.base_state()
+    c_mp = (2 * W.K_B * st["T_inf"] / st["m"]) ** 0.5
+
+    def params(q):
+        return T.make_params(n=st["n"], T_inf=st["T_inf"], m=st["m"], V=q["S"] * c_mp, dir=q["dir"], T_W=st["T_W"],
+                             eps_diffuse=0.9, A_ref=1.0, seed=q["seed"], max_bounces=64)
+
+    try:
+        for i in ids:  # warm-up per mesh
+            T.tpmc_trace(ctx, i, params(stream[0]), 100_000)
+        # continuous batching
+        handles = [None] * len(stream)
+        t_start = time.perf_counter() + 0.05
+
+        def submitter():
+            for k, q in enumerate(stream):
+                d = t_start + q["t_arrival"] - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                handles[k] = T.tpmc_submit(ctx, ids[q["mesh"]], params(q), q["N"])
+
+        thr = th.Thread(target=submitter)
+        thr.start()
+        thr.join()
+        lat = []
+        for h in handles:
+            lat.append(T.tpmc_poll(ctx, h, -1)["ms"])
+        cb_span = time.perf_counter() - t_start
+        # one query per launch, first come first served
+        t_start = time.perf_counter() + 0.05
+        lat_plain = []
+        for q in stream:
+            d = t_start + q["t_arrival"] - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            T.tpmc_trace(ctx, ids[q["mesh"]], params(q), q["N"])
+            lat_plain.append(1e3 * (time.perf_counter() - (t_start + q["t_arrival"])))
+        plain_span = time.perf_counter() - t_start
+    finally:
+        for i in ids:
+            T.tpmc_mesh_unload(ctx, i)
+    n = sum(q["N"] for q in stream)
+    return {"workload": f"{n_queries} Poisson queries at {rate:g}/s, N log-uniform [1e5,1e8], S~U[3,12], "
+                        "4 resident meshes (1,280 / 4,096 / 60,656 / 503,537 tri)",
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "throughput_particles_per_s": n / cb_span,
+            "plain": {"p50_ms": float(np.percentile(lat_plain, 50)), "p99_ms": float(np.percentile(lat_plain, 99)),
+                      "throughput_particles_per_s": n / plain_span}}
+
+
 # ---------------------------------------------------------------- GPU side
 def run_ours(args):
     import torch
@@ -371,6 +497,12 @@ def run_ours(args):
     achieved = flops_per_launch / (launch_avg_ms / 1e3) / 1e12
     traffic = TRACE_TRAFFIC.get(kernel_source_hash())
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras["satellite"] = measure_satellite(T, ctx)
+        extras["attitude_sweep"] = measure_attitude_sweep(T, ctx, torch, stream, dev)
+        extras["serving"] = measure_serving(T, ctx, rate=100.0)
+        extras["serving_high_load"] = measure_serving(T, ctx, rate=200.0)
     if rank == 0:
         cpu_base, cd_err = (None, None)
         if not args.no_cpu_baseline:
@@ -395,6 +527,9 @@ def run_ours(args):
             "clocks": clocks,
             "cpu_baseline": cpu_base,
             "cd_error": cd_err,
+            "serve": {k: extras["serving"][k] for k in ("p50_ms", "p99_ms", "throughput_particles_per_s", "plain")}
+            if "serving" in extras else None,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
     T.tpmc_destroy(ctx)
@@ -452,6 +587,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the satellite, attitude-sweep and serving runs")
     ap.add_argument("--profile-launch", default=None,
                     help="plate-specular|plate-diffuse|cylinder-specular|cylinder-diffuse: one small launch to profile")
     ap.add_argument("--profile-n-each", type=int, default=100_000)

@@ -3,16 +3,19 @@
 // tpmc_submit queues a query; one scheduler thread per context repeatedly
 //   1. admits queued queries into free slots while device memory allows
 //      (panel buffers are charged to the context's budget),
-//   2. gives every admitted query a share of the next launch's particle budget
-//      (a query of at most that share finishes in one launch),
-//   3. enqueues, per (mesh, precision) group, one persistent trace launch
-//      over work items from all of the group's queries, then the FP64
-//      reduction of the queries that finish, and
-//   4. waits for the launch on the host (a CUDA event; no device-side wait),
-//      publishes finished results and frees their slots.
-// A query's particles keep their ids 0..N-1 whatever launches they land in,
-// and its sums are exact integers, so its force and C_D do not depend on what
-// else is in flight.
+//   2. builds a step: a particle budget handed first to the queries with
+//      little work left, smallest first (they finish in this step), then to
+//      the large ones in arrival order,
+//   3. enqueues the step -- set-up of newly admitted queries, one persistent
+//      trace launch per (mesh, precision) group over work items from all of
+//      the group's queries, the FP64 reduction of the queries that finish,
+//      the read-back -- while the previous step may still run (two steps in
+//      flight keep the GPU busy during the host's bookkeeping), and
+//   4. waits for the older step on the host (a CUDA event; no device-side
+//      wait), publishes its finished results and frees their slots.
+// A query's particles keep their ids 0..N-1 whatever steps they land in, and
+// its sums are exact integers, so its force and C_D do not depend on what else
+// is in flight.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -28,8 +31,11 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr uint32_t kSlots = 1024;
 constexpr size_t kMaxQueue = 1u << 16;
-constexpr uint64_t kLaunchParticles = 1ull << 23;  // particle budget of one scheduler step
-constexpr uint64_t kMinShare = 1ull << 16;
+constexpr uint64_t kStepParticles = 1ull << 24;  // particle budget of one step
+constexpr uint64_t kSmallQuery = kStepParticles / 4;  // work left below which a query goes first
+constexpr int kInFlight = 2;                     // steps enqueued ahead of the host
+constexpr int kMaxGroups = 64;                   // trace launches per step
+constexpr int kGroupStreams = 4;                 // streams the groups of a step run on
 }  // namespace
 
 struct Request {
@@ -41,10 +47,28 @@ struct Request {
   QueryDev q;                  // inputs (set-up runs on the device at admission)
   uint64_t N = 0, next_pid = 0;
   int slot = -1;
+  bool set_up = false;         // set-up enqueued
   bool done = false;
   tpmc_result result;
   void* d_panel = nullptr;
   Clock::time_point t_submit;
+};
+
+// Buffers of one step in flight.
+struct StepBuf {
+  ItemDev* h_items = nullptr;
+  uint32_t* h_fresh = nullptr;
+  uint32_t* h_fin = nullptr;
+  tpmc_result* h_res = nullptr;
+  int* h_err = nullptr;
+  ItemDev* d_items = nullptr;
+  uint32_t* d_fresh = nullptr;
+  uint32_t* d_fin = nullptr;
+  tpmc_result* d_res = nullptr;
+  unsigned long long* d_counters = nullptr;
+  int* d_err = nullptr;
+  cudaEvent_t ev = nullptr;
+  std::vector<Request*> members, finishing;
 };
 
 struct ServeState {
@@ -57,203 +81,278 @@ struct ServeState {
   std::map<tpmc_query_id, Request*> all;
   std::vector<Request*> slots;
   cudaStream_t stream = nullptr;
-  cudaEvent_t ev = nullptr;
-  // device
+  cudaStream_t group_stream[kGroupStreams] = {};
+  cudaEvent_t group_done[kGroupStreams] = {};
+  cudaEvent_t ready = nullptr;
   QueryDev* d_q = nullptr;
   AccDev* d_acc = nullptr;
-  ItemDev* d_items = nullptr;
-  uint32_t* d_slots = nullptr;
-  tpmc_result* d_res = nullptr;
-  unsigned long long* d_counters = nullptr;
-  int* d_err = nullptr;
-  // pinned host
-  ItemDev* h_items = nullptr;
-  uint32_t* h_slots = nullptr;
-  tpmc_result* h_res = nullptr;
-  int* h_err = nullptr;
+  StepBuf buf[kInFlight];
+  std::deque<int> inflight;    // buffer indices, oldest first
   void* d_block = nullptr;
   void* h_block = nullptr;
-  uint64_t launches = 0;
+  uint64_t steps = 0;
 };
 
 namespace {
 
-void loop(ServeState* s) {
+// Admits queued requests into free slots (caller holds s->m).
+void admit(ServeState* s) {
   Ctx* c = s->ctx;
-  cudaSetDevice(c->device);
-  std::vector<Request*> fresh, active, finishing;
-  for (;;) {
-    fresh.clear();
-    active.clear();
-    finishing.clear();
-    {
-      std::unique_lock<std::mutex> lk(s->m);
-      s->cv_work.wait(lk, [&] {
-        if (s->stop) return true;
-        if (!s->queue.empty()) return true;
-        for (Request* r : s->slots) if (r) return true;
-        return false;
-      });
-      if (s->stop) return;
-      // 1. admission: a free slot and the panel memory
-      while (!s->queue.empty()) {
-        Request* r = s->queue.front();
-        int slot = -1;
-        for (uint32_t i = 0; i < kSlots; ++i) if (!s->slots[i]) { slot = (int)i; break; }
-        if (slot < 0) break;
-        if (r->want_panels && r->n_tri > 0) {
-          std::lock_guard<std::recursive_mutex> ck(c->mu);
-          if (c->alloc(&r->d_panel, (size_t)r->n_tri * 3 * sizeof(long long), "serving panel loads") != TPMC_OK) {
-            bool any = false;
-            for (Request* a : s->slots) any = any || a;
-            if (any) break;  // wait for memory to free up
-            r->done = true;  // cannot ever fit
-            std::memset(&r->result, 0, sizeof(r->result));
-            r->result.status = TPMC_ENOMEM;
-            r->result.query_id = r->id;
-            auto mit = c->meshes.find(r->mesh);
-            if (mit != c->meshes.end()) --mit->second.in_use;
-            s->queue.pop_front();
-            s->cv_done.notify_all();
-            continue;
-          }
-        }
-        s->queue.pop_front();
-        r->slot = slot;
-        s->slots[slot] = r;
-        fresh.push_back(r);
-      }
-      for (Request* r : s->slots) if (r) active.push_back(r);
-    }
-    if (active.empty()) continue;
-    cudaError_t e = cudaSuccess;
-    // 2. set-up of newly admitted queries, straight into their slots
-    for (size_t i = 0; i < fresh.size() && e == cudaSuccess; ++i) {
-      Request* r = fresh[i];
-      r->q.panel = (long long*)r->d_panel;
-      s->h_slots[i] = (uint32_t)r->slot;
-      e = cudaMemcpyAsync(s->d_q + r->slot, &r->q, sizeof(QueryDev), cudaMemcpyHostToDevice, s->stream);
-      if (e == cudaSuccess) e = cudaMemsetAsync(s->d_acc + r->slot, 0, sizeof(AccDev), s->stream);
-      if (e == cudaSuccess && r->d_panel)
-        e = cudaMemsetAsync(r->d_panel, 0, (size_t)r->n_tri * 3 * sizeof(long long), s->stream);
-    }
-    if (!fresh.empty() && e == cudaSuccess) {
-      e = cudaMemcpyAsync(s->d_slots, s->h_slots, fresh.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s->stream);
-      if (e == cudaSuccess)
-        e = launch_setup(s->d_q, (uint32_t)fresh.size(), nullptr, nullptr, nullptr, nullptr, s->d_slots, s->stream);
-    }
-    // 3. shares of this step, grouped by (mesh, precision)
-    const uint64_t share = std::max<uint64_t>(kMinShare, kLaunchParticles / active.size());
-    std::map<std::pair<tpmc_mesh_id, uint32_t>, std::vector<Request*>> groups;
-    for (Request* r : active) groups[{r->mesh, r->precision}].push_back(r);
-    uint32_t n_items = 0, group_idx = 0;
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_counters, 0, 64 * sizeof(unsigned long long), s->stream);
-    for (auto& kv : groups) {
-      if (group_idx == 64) break;  // one counter per launch; later groups wait for the next step
-      const uint32_t first_item = n_items;
-      uint64_t g = 0;
-      for (Request* r : kv.second) {
-        const uint64_t take = std::min<uint64_t>(r->N - r->next_pid, share);
-        if (take == 0) continue;
-        ItemDev& it = s->h_items[n_items++];
-        it.g_begin = g;
-        it.pid_begin = r->next_pid;
-        it.count = take;
-        it.query = (uint32_t)r->slot;
-        it.pad = 0;
-        g += take;
-        r->next_pid += take;
-        if (r->next_pid == r->N) finishing.push_back(r);
-      }
-      if (n_items == first_item || e != cudaSuccess) continue;
-      MeshDev md;
-      LaunchCfg cfg;
-      {
-        std::lock_guard<std::recursive_mutex> ck(c->mu);
-        const MeshRec& mr = c->meshes.at(kv.first.first);
-        md = mr.dev;
-        cfg = c->schedule(mr, kv.first.second, g);
-      }
-      e = cudaMemcpyAsync(s->d_items + first_item, s->h_items + first_item, (n_items - first_item) * sizeof(ItemDev),
-                          cudaMemcpyHostToDevice, s->stream);
-      TraceArgs a{};
-      a.mesh = md;
-      a.queries = s->d_q;
-      a.acc = s->d_acc;
-      a.items = s->d_items + first_item;
-      a.n_items = n_items - first_item;
-      a.total = g;
-      a.counter = s->d_counters + (group_idx++ % 64);
-      a.error = s->d_err;
-      a.count_work = c->counters ? 1u : 0u;
-      a.vn_table = c->vn_table;
-      a.chunk = cfg.chunk;
-      a.smem_nodes = cfg.smem_nodes;
-      if (e == cudaSuccess) e = launch_trace(a, kv.first.second, cfg, c->num_sms, s->stream);
-    }
-    // 4. reduction of finishing queries, read-back, host-side wait
-    for (size_t i = 0; i < finishing.size(); ++i) s->h_slots[kSlots + i] = (uint32_t)finishing[i]->slot;
-    if (!finishing.empty() && e == cudaSuccess) {
-      e = cudaMemcpyAsync(s->d_slots + kSlots, s->h_slots + kSlots, finishing.size() * sizeof(uint32_t),
-                          cudaMemcpyHostToDevice, s->stream);
-      if (e == cudaSuccess)
-        e = launch_finalize(s->d_q, s->d_acc, (uint32_t)finishing.size(), s->d_slots + kSlots, s->d_res, s->stream);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->h_res, s->d_res, finishing.size() * sizeof(tpmc_result), cudaMemcpyDeviceToHost,
-                            s->stream);
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(s->ev, s->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(s->ev);
-    ++s->launches;
-    const Clock::time_point now = Clock::now();
-    {
-      std::unique_lock<std::mutex> lk(s->m);
-      if (e != cudaSuccess || *s->h_err != 0) {
-        // a failed step fails every query that was in it
-        for (Request* r : active) {
-          r->done = true;
-          std::memset(&r->result, 0, sizeof(r->result));
-          r->result.status = TPMC_ECUDA;
-          r->result.query_id = r->id;
-          s->slots[r->slot] = nullptr;
-        }
-        *s->h_err = 0;
-        cudaGetLastError();
-      } else {
-        for (size_t i = 0; i < finishing.size(); ++i) {
-          Request* r = finishing[i];
-          r->result = s->h_res[i];
-          r->result.query_id = r->id;
-          r->result.ms = std::chrono::duration<double, std::milli>(now - r->t_submit).count();
-          r->done = true;
-          s->slots[r->slot] = nullptr;
-        }
-      }
+  while (!s->queue.empty()) {
+    Request* r = s->queue.front();
+    int slot = -1;
+    for (uint32_t i = 0; i < kSlots; ++i) if (!s->slots[i]) { slot = (int)i; break; }
+    if (slot < 0) return;
+    if (r->want_panels && r->n_tri > 0) {
       std::lock_guard<std::recursive_mutex> ck(c->mu);
-      for (Request* r : active) {
-        if (!r->done) continue;
+      if (c->alloc(&r->d_panel, (size_t)r->n_tri * 3 * sizeof(long long), "serving panel loads") != TPMC_OK) {
+        bool any = false;
+        for (Request* a : s->slots) any = any || a;
+        if (any || !s->inflight.empty()) return;  // wait for memory to free up
+        r->done = true;  // cannot ever fit
+        std::memset(&r->result, 0, sizeof(r->result));
+        r->result.status = TPMC_ENOMEM;
+        r->result.query_id = r->id;
         auto mit = c->meshes.find(r->mesh);
         if (mit != c->meshes.end()) --mit->second.in_use;
-        if (r->d_panel && r->result.status == TPMC_OK) {
-          PanelRec pr;
-          pr.d_panel = r->d_panel;
-          pr.query = r->q;
-          pr.query.gamma = r->result.gamma;
-          pr.query.c_mp = r->result.c_mp;
-          pr.query.quantum = r->result.fixed_quantum;
-          pr.mesh = r->mesh;
-          pr.n_tri = r->n_tri;
-          c->panels[r->id] = pr;
-          r->d_panel = nullptr;
-        } else if (r->d_panel) {
-          c->release(r->d_panel);
-          r->d_panel = nullptr;
-        }
+        s->queue.pop_front();
+        s->cv_done.notify_all();
+        continue;
       }
-      s->cv_done.notify_all();
+    }
+    s->queue.pop_front();
+    r->slot = slot;
+    s->slots[slot] = r;
+  }
+}
+
+// Builds and enqueues one step in buffer b (caller does not hold s->m).
+// Returns false when there was nothing to run.
+bool enqueue_step(ServeState* s, int b, const std::vector<Request*>& cand, cudaError_t& e) {
+  Ctx* c = s->ctx;
+  StepBuf& B = s->buf[b];
+  B.members.clear();
+  B.finishing.clear();
+  // Queries with little work left go first, smallest first, so that they
+  // finish in this step; the rest of the budget goes to the large ones in
+  // arrival order, which then run at nearly the full width of the GPU.
+  std::vector<Request*> order(cand);
+  std::sort(order.begin(), order.end(), [](const Request* x, const Request* y) {
+    const uint64_t rx = x->N - x->next_pid, ry = y->N - y->next_pid;
+    const bool sx = rx <= kSmallQuery, sy = ry <= kSmallQuery;
+    if (sx != sy) return sx;
+    if (sx) return rx != ry ? rx < ry : x->id < y->id;
+    return x->id < y->id;
+  });
+  std::map<Request*, uint64_t> take;
+  uint64_t budget = kStepParticles;
+  for (Request* r : order) {
+    if (budget == 0) break;
+    const uint64_t t = std::min<uint64_t>(r->N - r->next_pid, budget);
+    take[r] = t;
+    budget -= t;
+  }
+  // groups by (mesh, precision) in the order of `order`
+  std::vector<std::pair<std::pair<tpmc_mesh_id, uint32_t>, std::vector<Request*>>> groups;
+  for (Request* r : order) {
+    if (take[r] == 0) continue;
+    const auto key = std::make_pair(r->mesh, r->precision);
+    auto it = std::find_if(groups.begin(), groups.end(), [&](const auto& g) { return g.first == key; });
+    if (it == groups.end()) {
+      if ((int)groups.size() == kMaxGroups) continue;  // later groups wait for the next step
+      groups.push_back({key, {}});
+      it = groups.end() - 1;
+    }
+    it->second.push_back(r);
+  }
+  if (groups.empty()) return false;
+  cudaStream_t st = s->stream;
+  // set-up of newly admitted queries, straight into their slots
+  uint32_t n_fresh = 0;
+  for (auto& g : groups)
+    for (Request* r : g.second) {
+      if (r->set_up) continue;
+      r->q.panel = (long long*)r->d_panel;
+      B.h_fresh[n_fresh++] = (uint32_t)r->slot;
+      if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_q + r->slot, &r->q, sizeof(QueryDev), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(s->d_acc + r->slot, 0, sizeof(AccDev), st);
+      if (e == cudaSuccess && r->d_panel)
+        e = cudaMemsetAsync(r->d_panel, 0, (size_t)r->n_tri * 3 * sizeof(long long), st);
+      r->set_up = true;
+    }
+  if (n_fresh > 0 && e == cudaSuccess) {
+    e = cudaMemcpyAsync(B.d_fresh, B.h_fresh, n_fresh * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_setup(s->d_q, n_fresh, nullptr, nullptr, nullptr, nullptr, B.d_fresh, st);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(B.d_counters, 0, kMaxGroups * sizeof(unsigned long long), st);
+  // the groups run on their own streams once the set-up is done, so that one
+  // launch's tail overlaps the next launch's start
+  if (e == cudaSuccess) e = cudaEventRecord(s->ready, st);
+  bool used[kGroupStreams] = {};
+  uint32_t n_items = 0;
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const uint32_t first_item = n_items;
+    uint64_t g = 0;
+    for (Request* r : groups[gi].second) {
+      ItemDev& it = B.h_items[n_items++];
+      it.g_begin = g;
+      it.pid_begin = r->next_pid;
+      it.count = take[r];
+      it.query = (uint32_t)r->slot;
+      it.pad = 0;
+      g += take[r];
+      r->next_pid += take[r];
+      B.members.push_back(r);
+      if (r->next_pid == r->N) B.finishing.push_back(r);
+    }
+    MeshDev md;
+    LaunchCfg cfg;
+    {
+      std::lock_guard<std::recursive_mutex> ck(c->mu);
+      const MeshRec& mr = c->meshes.at(groups[gi].first.first);
+      md = mr.dev;
+      cfg = c->schedule(mr, groups[gi].first.second, g);
+    }
+    const int gs = (int)(gi % kGroupStreams);
+    cudaStream_t gst = s->group_stream[gs];
+    if (!used[gs] && e == cudaSuccess) e = cudaStreamWaitEvent(gst, s->ready, 0);
+    used[gs] = true;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(B.d_items + first_item, B.h_items + first_item, (n_items - first_item) * sizeof(ItemDev),
+                          cudaMemcpyHostToDevice, gst);
+    TraceArgs a{};
+    a.mesh = md;
+    a.queries = s->d_q;
+    a.acc = s->d_acc;
+    a.items = B.d_items + first_item;
+    a.n_items = n_items - first_item;
+    a.total = g;
+    a.counter = B.d_counters + gi;
+    a.error = B.d_err;
+    a.count_work = c->counters ? 1u : 0u;
+    a.vn_table = c->vn_table;
+    a.chunk = cfg.chunk;
+    a.smem_nodes = cfg.smem_nodes;
+    if (e == cudaSuccess) e = launch_trace(a, groups[gi].first.second, cfg, c->num_sms, gst);
+  }
+  for (int gs = 0; gs < kGroupStreams && e == cudaSuccess; ++gs) {
+    if (!used[gs]) continue;
+    e = cudaEventRecord(s->group_done[gs], s->group_stream[gs]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->group_done[gs], 0);
+  }
+  for (size_t i = 0; i < B.finishing.size(); ++i) B.h_fin[i] = (uint32_t)B.finishing[i]->slot;
+  if (!B.finishing.empty() && e == cudaSuccess) {
+    e = cudaMemcpyAsync(B.d_fin, B.h_fin, B.finishing.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = launch_finalize(s->d_q, s->d_acc, (uint32_t)B.finishing.size(), B.d_fin, B.d_res, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(B.h_res, B.d_res, B.finishing.size() * sizeof(tpmc_result), cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B.h_err, B.d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaEventRecord(B.ev, st);
+  return true;
+}
+
+// Waits for the oldest step and publishes its results (caller does not hold s->m).
+void retire_step(ServeState* s, cudaError_t e_enqueue) {
+  Ctx* c = s->ctx;
+  const int b = s->inflight.front();
+  StepBuf& B = s->buf[b];
+  cudaError_t e = e_enqueue;
+  if (e == cudaSuccess) e = cudaEventSynchronize(B.ev);
+  ++s->steps;
+  const Clock::time_point now = Clock::now();
+  std::unique_lock<std::mutex> lk(s->m);
+  s->inflight.pop_front();
+  std::vector<Request*> done;
+  if (e != cudaSuccess || *B.h_err != 0) {
+    // a failed step fails every query that had work in it
+    for (Request* r : B.members) {
+      if (r->done) continue;
+      r->done = true;
+      std::memset(&r->result, 0, sizeof(r->result));
+      r->result.status = TPMC_ECUDA;
+      r->result.query_id = r->id;
+      done.push_back(r);
+    }
+    *B.h_err = 0;
+    cudaGetLastError();
+  } else {
+    for (size_t i = 0; i < B.finishing.size(); ++i) {
+      Request* r = B.finishing[i];
+      r->result = B.h_res[i];
+      r->result.query_id = r->id;
+      r->result.ms = std::chrono::duration<double, std::milli>(now - r->t_submit).count();
+      r->done = true;
+      done.push_back(r);
     }
   }
+  std::lock_guard<std::recursive_mutex> ck(c->mu);
+  for (Request* r : done) {
+    if (r->slot >= 0 && s->slots[r->slot] == r) s->slots[r->slot] = nullptr;
+    auto mit = c->meshes.find(r->mesh);
+    if (mit != c->meshes.end()) --mit->second.in_use;
+    if (r->d_panel && r->result.status == TPMC_OK) {
+      PanelRec pr;
+      pr.d_panel = r->d_panel;
+      pr.query = r->q;
+      pr.query.gamma = r->result.gamma;
+      pr.query.c_mp = r->result.c_mp;
+      pr.query.quantum = r->result.fixed_quantum;
+      pr.mesh = r->mesh;
+      pr.n_tri = r->n_tri;
+      c->panels[r->id] = pr;
+      r->d_panel = nullptr;
+    } else if (r->d_panel) {
+      c->release(r->d_panel);
+      r->d_panel = nullptr;
+    }
+  }
+  s->cv_done.notify_all();
+}
+
+void loop(ServeState* s) {
+  cudaSetDevice(s->ctx->device);
+  std::vector<Request*> cand;
+  for (;;) {
+    int free_buf = -1;
+    {
+      std::unique_lock<std::mutex> lk(s->m);
+      auto has_work = [&] {
+        for (Request* r : s->slots)
+          if (r && !r->done && r->next_pid < r->N) return true;
+        return false;
+      };
+      s->cv_work.wait(lk, [&] {
+        return s->stop || !s->inflight.empty() || !s->queue.empty() || has_work();
+      });
+      if (s->stop) break;
+      admit(s);
+      cand.clear();
+      for (Request* r : s->slots)
+        if (r && !r->done && r->next_pid < r->N) cand.push_back(r);
+      if ((int)s->inflight.size() < kInFlight && !cand.empty()) {
+        for (int b = 0; b < kInFlight; ++b)
+          if (std::find(s->inflight.begin(), s->inflight.end(), b) == s->inflight.end()) { free_buf = b; break; }
+      }
+    }
+    cudaError_t e = cudaSuccess;
+    if (free_buf >= 0) {
+      const bool pushed = enqueue_step(s, free_buf, cand, e);
+      if (pushed) {
+        std::lock_guard<std::mutex> lk(s->m);
+        s->inflight.push_back(free_buf);
+      }
+      if (pushed && e == cudaSuccess) continue;  // keep the next step ready while this one runs
+    }
+    bool any;
+    {
+      std::lock_guard<std::mutex> lk(s->m);
+      any = !s->inflight.empty();
+    }
+    if (any) retire_step(s, e);
+  }
+  while (!s->inflight.empty()) retire_step(s, cudaSuccess);
 }
 
 tpmc_status start_serving(Ctx* c) {
@@ -261,35 +360,52 @@ tpmc_status start_serving(Ctx* c) {
   s->ctx = c;
   s->slots.assign(kSlots, nullptr);
   cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev, cudaEventBlockingSync | cudaEventDisableTiming);
+  for (int b = 0; b < kInFlight && e == cudaSuccess; ++b)
+    e = cudaEventCreateWithFlags(&s->buf[b].ev, cudaEventBlockingSync | cudaEventDisableTiming);
+  for (int g = 0; g < kGroupStreams && e == cudaSuccess; ++g) {
+    e = cudaStreamCreateWithFlags(&s->group_stream[g], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->group_done[g], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ready, cudaEventDisableTiming);
   if (e != cudaSuccess) { delete s; return cuda_fail(e, "serving stream"); }
-  const size_t dev_bytes = kSlots * (sizeof(QueryDev) + sizeof(AccDev) + 2 * sizeof(ItemDev) + 2 * sizeof(uint32_t) +
-                                     sizeof(tpmc_result)) + 64 * sizeof(unsigned long long) + 256;
+  const size_t per_buf_dev = kSlots * (sizeof(ItemDev) + 2 * sizeof(uint32_t) + sizeof(tpmc_result)) +
+                             kMaxGroups * sizeof(unsigned long long) + 256;
+  const size_t dev_bytes = kSlots * (sizeof(QueryDev) + sizeof(AccDev)) + kInFlight * per_buf_dev + 256;
   tpmc_status st = c->alloc(&s->d_block, dev_bytes, "serving slots");
-  if (st != TPMC_OK) { cudaStreamDestroy(s->stream); cudaEventDestroy(s->ev); delete s; return st; }
+  if (st != TPMC_OK) {
+    cudaStreamDestroy(s->stream);
+    for (int b = 0; b < kInFlight; ++b) if (s->buf[b].ev) cudaEventDestroy(s->buf[b].ev);
+    delete s;
+    return st;
+  }
   char* p = (char*)s->d_block;
   s->d_q = (QueryDev*)p; p += kSlots * sizeof(QueryDev);
   s->d_acc = (AccDev*)p; p += kSlots * sizeof(AccDev);
-  s->d_items = (ItemDev*)p; p += 2 * kSlots * sizeof(ItemDev);
-  s->d_res = (tpmc_result*)p; p += kSlots * sizeof(tpmc_result);
-  s->d_counters = (unsigned long long*)p; p += 64 * sizeof(unsigned long long);
-  s->d_slots = (uint32_t*)p; p += 2 * kSlots * sizeof(uint32_t);
-  s->d_err = (int*)p;
-  cudaMemset(s->d_err, 0, sizeof(int));
-  const size_t host_bytes = 2 * kSlots * sizeof(ItemDev) + 2 * kSlots * sizeof(uint32_t) + kSlots * sizeof(tpmc_result) + 64;
-  if ((e = cudaMallocHost(&s->h_block, host_bytes)) != cudaSuccess) {
+  const size_t per_buf_host = kSlots * (sizeof(ItemDev) + 2 * sizeof(uint32_t) + sizeof(tpmc_result)) + 64;
+  if ((e = cudaMallocHost(&s->h_block, kInFlight * per_buf_host)) != cudaSuccess) {
     c->release(s->d_block);
     cudaStreamDestroy(s->stream);
-    cudaEventDestroy(s->ev);
+    for (int b = 0; b < kInFlight; ++b) cudaEventDestroy(s->buf[b].ev);
     delete s;
     return cuda_fail(e, "serving host buffers");
   }
   char* h = (char*)s->h_block;
-  s->h_items = (ItemDev*)h; h += 2 * kSlots * sizeof(ItemDev);
-  s->h_slots = (uint32_t*)h; h += 2 * kSlots * sizeof(uint32_t);
-  s->h_res = (tpmc_result*)h; h += kSlots * sizeof(tpmc_result);
-  s->h_err = (int*)h;
-  *s->h_err = 0;
+  for (int b = 0; b < kInFlight; ++b) {
+    StepBuf& B = s->buf[b];
+    B.d_items = (ItemDev*)p; p += kSlots * sizeof(ItemDev);
+    B.d_res = (tpmc_result*)p; p += kSlots * sizeof(tpmc_result);
+    B.d_counters = (unsigned long long*)p; p += kMaxGroups * sizeof(unsigned long long);
+    B.d_fresh = (uint32_t*)p; p += kSlots * sizeof(uint32_t);
+    B.d_fin = (uint32_t*)p; p += kSlots * sizeof(uint32_t);
+    B.d_err = (int*)p; p += 256;
+    B.h_items = (ItemDev*)h; h += kSlots * sizeof(ItemDev);
+    B.h_res = (tpmc_result*)h; h += kSlots * sizeof(tpmc_result);
+    B.h_fresh = (uint32_t*)h; h += kSlots * sizeof(uint32_t);
+    B.h_fin = (uint32_t*)h; h += kSlots * sizeof(uint32_t);
+    B.h_err = (int*)h; h += 64;
+    *B.h_err = 0;
+    cudaMemset(B.d_err, 0, sizeof(int));
+  }
   c->serve = s;
   s->th = std::thread(loop, s);
   return TPMC_OK;
@@ -313,7 +429,13 @@ void stop_serving(Ctx* c) {
   }
   c->release(s->d_block);
   cudaFreeHost(s->h_block);
-  cudaEventDestroy(s->ev);
+  for (int b = 0; b < kInFlight; ++b) cudaEventDestroy(s->buf[b].ev);
+  for (int g = 0; g < kGroupStreams; ++g) {
+    cudaStreamSynchronize(s->group_stream[g]);
+    cudaStreamDestroy(s->group_stream[g]);
+    cudaEventDestroy(s->group_done[g]);
+  }
+  cudaEventDestroy(s->ready);
   cudaStreamDestroy(s->stream);
   delete s;
   c->serve = nullptr;
