@@ -56,6 +56,23 @@ def kernel_source_hash() -> str:
         return hashlib.sha256(f.read()).hexdigest()
 
 
+def rank_stream_base(rank: int, group: int) -> int:
+    """Philox stream id of a sweep group on a rank: ranks trace independent
+    particle streams of the same workload (weak scaling, no data exchange)."""
+    return rank * 4096 + group * 128
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's time (the job's time) when several ranks run."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def groups():
     """The four sweep groups of one step: (shape, eps, xyz, tri, base params, dirs[96], S[96])."""
     out = []
@@ -397,7 +414,7 @@ def run_ours(args):
     d_in = []
     for gi, g in enumerate(gs):
         # ranks trace independent streams of the same workload (weak scaling)
-        base = T.make_params(**g["base"], stream_id=rank * 4096 + gi * 128)
+        base = T.make_params(**g["base"], stream_id=rank_stream_base(rank, gi))
         d_in.append((mesh_ids[g["shape"]], base,
                      torch.tensor(g["dirs"], dtype=torch.float64, device=dev),
                      torch.tensor(g["S"], dtype=torch.float64, device=dev),
@@ -450,12 +467,8 @@ def run_ours(args):
         step_ms.append(sum(ms))
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
-    t_step = sum(step_ms) / len(step_ms)
+    t_step = max_over_ranks(sum(step_ms) / len(step_ms), dist, dev)
     particles_step = work["particles"]
-    if dist is not None:
-        t = torch.tensor([t_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
     value = world * particles_step / (t_step / 1e3)
 
     # results of the last timed step
@@ -482,11 +495,7 @@ def run_ours(args):
         for i in ids.values():
             T.tpmc_mesh_unload(ctx, i)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_t = statistics.mean(e2e_ms)
-    if dist is not None:
-        t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
+    e2e_t = max_over_ranks(statistics.mean(e2e_ms), dist, dev)
     e2e_value = world * particles_step / (e2e_t / 1e3)
 
     peaks = measured_peaks()

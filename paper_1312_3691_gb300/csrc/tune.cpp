@@ -79,7 +79,6 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
   c->manual = old_manual;
   if (st != TPMC_OK) return st;
   if ((st = c->check_error_word()) != TPMC_OK) return st;
-  best_cfg.chunk = 0 == best_cfg.chunk ? 0 : best_cfg.chunk;
   c->tuned[tune_key(m.dev.n_tri, params->precision)] = best_cfg;
   if (best) {
     best->block = best_cfg.block;
