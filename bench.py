@@ -556,21 +556,28 @@ def run_profile_launch(args):
     from paper_1312_3691_gb300.build import build
 
     build()
-    shape, gsi = args.profile_launch.split("-")
-    g = [x for x in groups() if x["shape"] == shape and x["eps"] == (1.0 if gsi == "diffuse" else 0.0)][0]
+    if args.profile_launch == "satellite-sweep":
+        case = W.satellite_case(N=1)
+        grid = W.attitude_grid(8, 12)
+        g = {"xyz": case["xyz"], "tri": case["tri"], "base": case["params"], "dirs": grid,
+             "S": np.full(len(grid), 7.0), "cases": list(range(len(grid)))}
+    else:
+        shape, gsi = args.profile_launch.split("-")
+        g = [x for x in groups() if x["shape"] == shape and x["eps"] == (1.0 if gsi == "diffuse" else 0.0)][0]
     ctx = T.tpmc_create(0)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     T.tpmc_set_stream(ctx, stream)
+    if args.launch:
+        vals = [int(x) for x in args.launch.split(",")] + [0, 0]
+        T.tpmc_set_launch(ctx, block=vals[0], blocks_per_sm=vals[1], chunk=vals[2], smem_nodes=vals[3],
+                          refill_at=vals[4], bvh_leaf=vals[5])
     mesh = T.tpmc_mesh_load(ctx, g["xyz"], g["tri"])
     K = len(g["cases"])
     dd = torch.tensor(g["dirs"], dtype=torch.float64, device="cuda")
     ds = torch.tensor(g["S"], dtype=torch.float64, device="cuda")
     out = torch.zeros(K * T.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     base = T.make_params(**g["base"])
-    if args.launch:
-        b, bps, ch, sn = (int(x) for x in args.launch.split(","))
-        T.tpmc_set_launch(ctx, block=b, blocks_per_sm=bps, chunk=ch, smem_nodes=sn)
     times = []
     for _ in range(2):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -598,9 +605,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the satellite, attitude-sweep and serving runs")
     ap.add_argument("--profile-launch", default=None,
-                    help="plate-specular|plate-diffuse|cylinder-specular|cylinder-diffuse: one small launch to profile")
+                    help="plate-specular|plate-diffuse|cylinder-specular|cylinder-diffuse|satellite-sweep: one small launch")
     ap.add_argument("--profile-n-each", type=int, default=100_000)
-    ap.add_argument("--launch", default=None, help="block,blocks_per_sm,chunk,smem_nodes for --profile-launch")
+    ap.add_argument("--launch", default=None,
+                    help="block,blocks_per_sm,chunk,smem_nodes[,refill_at,bvh_leaf] for --profile-launch")
     args = ap.parse_args()
     if args.profile_launch:
         return run_profile_launch(args)

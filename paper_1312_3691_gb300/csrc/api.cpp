@@ -129,6 +129,7 @@ LaunchCfg Ctx::schedule(const MeshRec& m, uint32_t precision, uint64_t total) {
     cfg.chunk = 0;
   }
   cfg.smem_nodes = std::min<uint32_t>(cfg.smem_nodes, m.dev.n_nodes);
+  if (cfg.refill_at == 0 || cfg.refill_at > 32) cfg.refill_at = 16;
   const int maxb = trace_max_blocks_per_sm(precision, cfg, m.dev.n_nodes);
   if (cfg.blocks_per_sm == 0 || (int)cfg.blocks_per_sm > maxb) cfg.blocks_per_sm = std::max(1, maxb);
   if (cfg.chunk == 0) {
@@ -188,6 +189,7 @@ tpmc_status Ctx::run(const MeshRec& m, const QueryDev* h_queries, uint32_t nq, c
   const LaunchCfg cfg = schedule(m, precision, total);
   a.chunk = cfg.chunk;
   a.smem_nodes = cfg.smem_nodes;
+  a.refill_at = cfg.refill_at;
   last_cfg = cfg;
   if (total > 0 && (e = launch_trace(a, precision, cfg, num_sms, stream)) != cudaSuccess) return cuda_fail(e, "trace kernel");
   if ((e = launch_finalize(d_queries, d_acc, nq, nullptr, d_out, stream)) != cudaSuccess)
@@ -294,7 +296,7 @@ tpmc_status tpmc_mesh_load(tpmc_ctx* ctx, const double* xyz, uint32_t n_vert, co
   cudaSetDevice(c->device);
   BvhBuild b;
   const char* err = nullptr;
-  if (!build_bvh(xyz, n_vert, tri, n_tri, 4, &b, &err)) {
+  if (!build_bvh(xyz, n_vert, tri, n_tri, c->bvh_leaf, &b, &err)) {
     b.release();
     return fail(TPMC_EINVAL, err);
   }
@@ -582,11 +584,15 @@ tpmc_status tpmc_set_launch(tpmc_ctx* ctx, const tpmc_launch* cfg) {
   if (!cfg) { c->manual_launch = false; return TPMC_OK; }
   if (cfg->block == 0 || cfg->block % 32 != 0 || cfg->block > 256) return fail(TPMC_EINVAL, "block must be 32..256, multiple of 32");
   if (cfg->chunk != 0 && (cfg->chunk % 32 != 0)) return fail(TPMC_EINVAL, "chunk must be a multiple of 32");
+  if (cfg->refill_at > 32) return fail(TPMC_EINVAL, "refill_at must be in [0, 32]");
+  if (cfg->bvh_leaf > 127) return fail(TPMC_EINVAL, "bvh_leaf must be in [0, 127]");
   c->manual_launch = true;
   c->manual.block = cfg->block;
   c->manual.blocks_per_sm = cfg->blocks_per_sm;
   c->manual.chunk = cfg->chunk;
   c->manual.smem_nodes = cfg->smem_nodes;
+  c->manual.refill_at = cfg->refill_at;
+  c->bvh_leaf = cfg->bvh_leaf ? cfg->bvh_leaf : 4;
   return TPMC_OK;
 }
 
@@ -601,6 +607,8 @@ tpmc_status tpmc_get_launch(tpmc_ctx* ctx, tpmc_mesh_id mesh, uint32_t precision
   out->blocks_per_sm = cfg.blocks_per_sm;
   out->chunk = cfg.chunk;
   out->smem_nodes = cfg.smem_nodes;
+  out->refill_at = cfg.refill_at;
+  out->bvh_leaf = c->bvh_leaf;
   return TPMC_OK;
 }
 

@@ -741,14 +741,13 @@ __device__ __noinline__ void seed_into(const TraceArgs& a, uint32_t qi, uint64_t
 }
 
 constexpr uint32_t kQueue = 64;     // queue slots per warp (two seeding batches)
-constexpr uint32_t kRefillAt = 8;   // lanes with finished rays that end a traversal round
 
 // --------------------------------------------------------- trace kernel
 // Persistent kernel.  Each warp keeps a queue of seeded particles in shared
 // memory; when its lanes need particles and the queue runs low, all 32 lanes
 // seed one particle each (so the inverse-CDF solves run at full warp width).
 // Lanes then trace in rounds of resumable traversal steps; a round ends when
-// kRefillAt lanes have finished their rays, and those lanes re-emit (next
+// refill_at lanes have finished their rays, and those lanes re-emit (next
 // bounce) or finish their particle and take the next one from the queue.
 // MINB > 0: a register-capped instantiation for 128-thread blocks with at
 // least MINB resident blocks per SM (more warps to hide latency, at the cost
@@ -938,7 +937,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : 1) tra
       }
       const unsigned fin = __ballot_sync(kFull, has && tdone);
       const unsigned run = __ballot_sync(kFull, has && !tdone);
-      if (run == 0u || (uint32_t)__popc(fin) >= kRefillAt) break;
+      if (run == 0u || (uint32_t)__popc(fin) >= a.refill_at) break;
     }
   }
   if (a.count_work) work_flush(a.acc, acc.q, n_nodes, n_tris);

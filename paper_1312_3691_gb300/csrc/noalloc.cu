@@ -114,6 +114,7 @@ extern "C" tpmc_status tpmc_sweep_noalloc(tpmc_ctx* ctx, tpmc_mesh_id mesh, cons
   const LaunchCfg cfg = c->schedule(m, base->precision, a.total);
   a.chunk = cfg.chunk;
   a.smem_nodes = cfg.smem_nodes;
+  a.refill_at = cfg.refill_at;
   if ((e = launch_trace(a, base->precision, cfg, c->num_sms, s)) != cudaSuccess) return cuda_fail(e, "trace kernel");
   if ((e = launch_finalize(A->queries, A->acc, K, nullptr, A->results, s)) != cudaSuccess)
     return cuda_fail(e, "finalize kernel");

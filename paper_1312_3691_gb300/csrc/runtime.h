@@ -67,6 +67,7 @@ struct Ctx {
   tpmc_query_id next_query = 1;
   bool counters = false;
   bool manual_launch = false;
+  uint32_t bvh_leaf = 4;       // largest leaf of the BVHs built by later mesh loads
   LaunchCfg manual;
   LaunchCfg last_cfg;
   std::map<uint64_t, LaunchCfg> tuned;

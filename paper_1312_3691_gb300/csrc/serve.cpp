@@ -233,6 +233,7 @@ bool enqueue_step(ServeState* s, int b, const std::vector<Request*>& cand, cudaE
     a.vn_table = c->vn_table;
     a.chunk = cfg.chunk;
     a.smem_nodes = cfg.smem_nodes;
+    a.refill_at = cfg.refill_at;
     if (e == cudaSuccess) e = launch_trace(a, groups[gi].first.second, cfg, c->num_sms, gst);
   }
   for (int gs = 0; gs < kGroupStreams && e == cudaSuccess; ++gs) {

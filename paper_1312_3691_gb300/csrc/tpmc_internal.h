@@ -108,6 +108,7 @@ struct TraceArgs {
   uint32_t chunk;             // ids a warp takes per fetch
   uint32_t smem_nodes;        // nodes staged in shared memory
   uint32_t count_work;        // 1: count node visits and triangle tests
+  uint32_t refill_at;         // finished lanes that end a traversal round
   uint64_t total;             // sum of item counts
   unsigned long long* counter;  // global work counter (zeroed before launch)
   int* error;                 // device error word (stack overflow)
@@ -119,7 +120,8 @@ struct LaunchCfg {
   uint32_t block = 128;
   uint32_t blocks_per_sm = 4;
   uint32_t chunk = 0;
-  uint32_t smem_nodes = 512;
+  uint32_t smem_nodes = 0;
+  uint32_t refill_at = 16;
 };
 
 // ------------------------------------------------------------ host launchers

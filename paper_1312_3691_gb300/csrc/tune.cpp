@@ -35,17 +35,17 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
   std::vector<LaunchCfg> cands;
   const uint32_t nn = m.dev.n_nodes;
   for (uint32_t block : {64u, 128u, 256u})
-    for (uint32_t sm_nodes : {0u, 256u, 1024u}) {
-      if (sm_nodes > 0 && sm_nodes >= 4 * std::max(nn, 1u) && sm_nodes != 256u) continue;
+    for (uint32_t sm_nodes : {0u, 256u}) {
       for (uint32_t occ_div : {1u, 2u})
-        for (uint32_t chunk : {0u, 256u}) {
+        for (uint32_t refill : {4u, 8u, 16u}) {
           LaunchCfg cfg;
           cfg.block = block;
           cfg.smem_nodes = std::min(sm_nodes, nn);
+          cfg.refill_at = refill;
           const int maxb = trace_max_blocks_per_sm(params->precision, cfg, nn);
           if (maxb < 1) continue;
           cfg.blocks_per_sm = std::max(1u, (uint32_t)maxb / occ_div);
-          cfg.chunk = chunk;
+          cfg.chunk = 0;
           cands.push_back(cfg);
         }
     }
@@ -85,6 +85,8 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
     best->blocks_per_sm = best_cfg.blocks_per_sm;
     best->chunk = best_cfg.chunk;
     best->smem_nodes = best_cfg.smem_nodes;
+    best->refill_at = best_cfg.refill_at;
+    best->bvh_leaf = c->bvh_leaf;
   }
   return TPMC_OK;
 }
