@@ -17,7 +17,10 @@ Parity status per function (the pins live in ``tests/test_oracle_*.py``):
 * re-emission ........................... pinned (half-range Maxwellian moments, KS)
 * sphere / plate / cylinder C_D (Eq. 3-4)  pinned (quadrature, textbook cross-flow form)
 * full run on convex meshes ............. pinned (panel-sum expectation within 3 sigma)
-* full run on concave meshes ............ parity unpinned (no closed form exists)
+* full run on concave meshes ............ pinned (Pratt's hemisphere constant, Eq. 5, re-derived by a
+                                          view-factor quadrature; exact specular chord construction)
+* rectangular-CV seeding (§I, §III.A) ... pinned (flux-weighted faces reproduce Eq. 4 at every incidence;
+                                          face shares against the flat-plate flux; KS of both face laws)
 """
 from __future__ import annotations
 
@@ -56,7 +59,11 @@ class Params(ctypes.Structure):
         ("r_cv", ctypes.c_double), ("center", ctypes.c_double * 3),
         ("max_bounces", ctypes.c_uint32), ("stream", ctypes.c_uint32), ("seed", ctypes.c_uint64),
         ("t_min_len", ctypes.c_double), ("intersect", ctypes.c_int32), ("threads", ctypes.c_int32),
+        ("cv_kind", ctypes.c_int32), ("pad", ctypes.c_int32),
+        ("box_lo", ctypes.c_double * 3), ("box_hi", ctypes.c_double * 3),
     ]
+
+CV_SPHERE, CV_BOX_FLUX, CV_BOX_MAXWELL = 0, 1, 2
 
 
 class Result(ctypes.Structure):
@@ -107,7 +114,8 @@ def lib():
             getattr(L, name).restype = _D
             getattr(L, name).argtypes = [_D]
         for name in ["orc_g_phi", "orc_h_x", "orc_position_cdf", "orc_position_inverse", "orc_normal_speed_pdf",
-                     "orc_normal_speed_cdf", "orc_normal_speed_inverse", "orc_sphere_cd_paper"]:
+                     "orc_normal_speed_cdf", "orc_normal_speed_inverse", "orc_sphere_cd_paper",
+                     "orc_truncated_normal_cdf", "orc_truncated_normal_inverse"]:
             getattr(L, name).restype = _D
             getattr(L, name).argtypes = [_D, _D]
         for name in ["orc_plate_cd_paper", "orc_plate_cd_derived"]:
@@ -183,6 +191,8 @@ normal_speed_norm = _scalar("orc_normal_speed_norm")
 normal_speed_pdf = _scalar("orc_normal_speed_pdf")
 normal_speed_cdf = _scalar("orc_normal_speed_cdf")
 normal_speed_inverse = _scalar("orc_normal_speed_inverse")
+truncated_normal_cdf = _scalar("orc_truncated_normal_cdf")
+truncated_normal_inverse = _scalar("orc_truncated_normal_inverse")
 flux_G = _scalar("orc_flux_G")
 flux_P = _scalar("orc_flux_P")
 sphere_cd_paper = _scalar("orc_sphere_cd_paper")
@@ -254,8 +264,9 @@ class Mesh:
         return int(i), tuv
 
 
-def make_params(*, n, T_inf, m, V, dir, T_W, eps_diffuse, A_ref, ref_point=(0, 0, 0), r_cv, center=(0, 0, 0),
-                max_bounces=64, stream=0, seed=0, t_min_len=1e-9, intersect=0, threads=0) -> Params:
+def make_params(*, n, T_inf, m, V, dir, T_W, eps_diffuse, A_ref, ref_point=(0, 0, 0), r_cv=0.0, center=(0, 0, 0),
+                max_bounces=64, stream=0, seed=0, t_min_len=1e-9, intersect=0, threads=0, cv_kind=CV_SPHERE,
+                box_lo=(0, 0, 0), box_hi=(0, 0, 0)) -> Params:
     p = Params()
     p.n, p.T_inf, p.m, p.V = float(n), float(T_inf), float(m), float(V)
     p.dir[:] = [float(x) for x in dir]
@@ -265,6 +276,9 @@ def make_params(*, n, T_inf, m, V, dir, T_W, eps_diffuse, A_ref, ref_point=(0, 0
     p.center[:] = [float(x) for x in center]
     p.max_bounces, p.stream, p.seed = int(max_bounces), int(stream), int(seed)
     p.t_min_len, p.intersect, p.threads = float(t_min_len), int(intersect), int(threads)
+    p.cv_kind = int(cv_kind)
+    p.box_lo[:] = [float(x) for x in box_lo]
+    p.box_hi[:] = [float(x) for x in box_hi]
     return p
 
 

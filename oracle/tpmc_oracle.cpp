@@ -20,15 +20,19 @@
 //   Eq. 14a-c velocity component densities (§III.A.2)
 //   Eq. 15  Rodrigues rotation to body coordinates (§III.A.3)
 //   §II.A   closest-hit ray tracing, diffuse re-emission, momentum sum
+//   §I, §III.A rectangular control volume with uniform positions on its six
+//           faces and per-face counts from the flat-plate flux (the ANGARA
+//           scheme the paper replaces), with two velocity laws per face
 //
 // Readings where the paper is silent or ambiguous (inverse-CDF sampling, the
 // frame orientation, the re-emission law, the RNG layout, tie and edge rules)
 // are stated where they are used.
 //
 // Parity status: every function here is pinned by a test in tests/ against a
-// closed form, a quadrature, an independent sampler or brute force, except
-// the multiple-reflection result on concave meshes, which has no closed form
-// (parity unpinned beyond the same-stream comparison and the sub-checks).
+// closed form, a quadrature, an independent sampler or brute force.  The
+// multiple-reflection path is pinned on a concave hemispherical shell by
+// Pratt's hyperthermal constant (§II.B.3, Eq. 5), re-derived by a view-factor
+// quadrature, and by an exact chord construction for specular walls.
 
 #include <algorithm>
 #include <cmath>
@@ -190,6 +194,25 @@ double normal_speed_inverse(double u, double s) {
   const double hi = std::max(s, 0.0) + 12.0;  // 1 - F(hi) is far below the smallest uniform, 2^-24
   if (u <= 0.5) return bisect_cdf([s](double x) { return normal_speed_cdf(x, s); }, u, 0.0, hi);
   return bisect_cdf([s](double x) { return -normal_speed_survival(x, s); }, -(1.0 - u), 0.0, hi);
+}
+
+// Normal speed of the rectangular-CV seeder's second velocity law: the
+// free-stream Maxwellian of Eq. 2 restricted to velocities that enter the face,
+// i.e. x = v_n / c_mp > 0 with density exp(-(x - s)^2) / (sqrt(pi)/2 erfc(-s)),
+// WITHOUT the flux factor x that Eq. 14a carries.
+//   survival Q(x) = erfc(x - s) / erfc(-s),  CDF F(x) = 1 - Q(x).
+double truncated_normal_cdf(double x, double s) {
+  if (x <= 0.0) return 0.0;
+  return (std::erfc(-s) - std::erfc(x - s)) / std::erfc(-s);
+}
+double truncated_normal_survival(double x, double s) {
+  if (x <= 0.0) return 1.0;
+  return std::erfc(x - s) / std::erfc(-s);
+}
+double truncated_normal_inverse(double u, double s) {
+  const double hi = std::max(s, 0.0) + 12.0;
+  if (u <= 0.5) return bisect_cdf([s](double x) { return truncated_normal_cdf(x, s); }, u, 0.0, hi);
+  return bisect_cdf([s](double x) { return -truncated_normal_survival(x, s); }, -(1.0 - u), 0.0, hi);
 }
 
 // Per-area fluxes onto a surface element whose inward-normal speed ratio is s
@@ -429,6 +452,9 @@ typedef struct {
   double t_min_len;     // smallest accepted hit distance in metres (e.g. 1e-9)
   int32_t intersect;    // 0 auto, 1 brute force, 2 median-split BVH
   int32_t threads;      // 0 = all hardware threads
+  int32_t cv_kind;      // 0 sphere (Eq. 11, 14a-c); 1 box, flux-weighted faces; 2 box, free-stream Maxwellian faces
+  int32_t pad;
+  double box_lo[3], box_hi[3];  // box control volume (cv_kind 1, 2), body frame, metres
 } orc_params;
 
 typedef struct {
@@ -464,6 +490,8 @@ double orc_normal_speed_norm(double s) { return normal_speed_norm(s); }
 double orc_normal_speed_pdf(double x, double s) { return normal_speed_pdf(x, s); }
 double orc_normal_speed_cdf(double x, double s) { return normal_speed_cdf(x, s); }
 double orc_normal_speed_inverse(double u, double s) { return normal_speed_inverse(u, s); }
+double orc_truncated_normal_cdf(double x, double s) { return truncated_normal_cdf(x, s); }
+double orc_truncated_normal_inverse(double u, double s) { return truncated_normal_inverse(u, s); }
 double orc_flux_G(double s) { return flux_G(s); }
 double orc_flux_P(double s) { return flux_P(s); }
 
@@ -621,7 +649,8 @@ int64_t orc_closest_hit(const void* h, const double* o, const double* d, int64_t
 int orc_trace(const void* mesh_handle, const orc_params* p, uint64_t N_total, uint64_t pid_begin, uint64_t count,
               orc_result* res, double* panel_dv, const orc_records* rec) {
   const Mesh& m = *(const Mesh*)mesh_handle;
-  if (!(p->n > 0 && p->T_inf > 0 && p->m > 0 && p->V > 0 && p->T_W > 0 && p->r_cv > 0)) return -1;
+  if (!(p->n > 0 && p->T_inf > 0 && p->m > 0 && p->V > 0 && p->T_W > 0)) return -1;
+  if (p->cv_kind == 0 && !(p->r_cv > 0)) return -1;
   if (!(p->eps_diffuse >= 0 && p->eps_diffuse <= 1) || p->max_bounces < 1 || N_total == 0) return -1;
   if (count == 0 || pid_begin + count > N_total) return -1;
   const V3 Vraw = load3(p->dir);
@@ -633,8 +662,40 @@ int orc_trace(const void* mesh_handle, const orc_params* p, uint64_t N_total, ui
   const double cW = std::sqrt(2.0 * kBoltzmann * p->T_W / p->m);
   const double S = p->V / c;
   const double cw = cW / c;
-  const double gamma = gamma_coefficient(S) * c * p->n * p->r_cv * p->r_cv;  // molecules per second
-  const double weight = gamma / (double)N_total;                              // molecules/s per particle
+  if (p->cv_kind < 0 || p->cv_kind > 2) return -1;
+  const bool box = p->cv_kind != 0;
+  // Rectangular control volume (§I, §III.A): faces f = 2 a + k are x_a = hi_a
+  // (k = 0, inward normal -e_a) and x_a = lo_a (k = 1, inward normal +e_a).
+  // Face f receives the flat-plate number flux A_f n c G(s_f) of the free
+  // stream, s_f = S (Vhat . inward normal), and the particle ids
+  // [floor(N C_f), floor(N C_{f+1})), C_f the cumulative share of the total.
+  struct Face { int axis; double coord; V3 n_in; double s, area; uint64_t begin, end; };
+  Face faces[6];
+  double box_flux = 0.0;  // sum of A_f G(s_f), m^2
+  if (box) {
+    for (int a = 0; a < 3; ++a)
+      if (!(p->box_hi[a] > p->box_lo[a])) return -1;
+    for (int f = 0; f < 6; ++f) {
+      Face& F = faces[f];
+      F.axis = f / 2;
+      const int a1 = (F.axis + 1) % 3, a2 = (F.axis + 2) % 3;
+      const double sign = (f % 2 == 0) ? -1.0 : 1.0;
+      F.coord = (f % 2 == 0) ? p->box_hi[F.axis] : p->box_lo[F.axis];
+      F.n_in = V3{F.axis == 0 ? sign : 0.0, F.axis == 1 ? sign : 0.0, F.axis == 2 ? sign : 0.0};
+      F.s = S * dot(Vhat, F.n_in);
+      F.area = (p->box_hi[a1] - p->box_lo[a1]) * (p->box_hi[a2] - p->box_lo[a2]);
+      box_flux += F.area * flux_G(F.s);
+    }
+    double cum = 0.0;
+    for (int f = 0; f < 6; ++f) {
+      faces[f].begin = (uint64_t)std::floor((double)N_total * cum);
+      cum += faces[f].area * flux_G(faces[f].s) / box_flux;
+      faces[f].end = f == 5 ? N_total : (uint64_t)std::floor((double)N_total * cum);
+    }
+  }
+  const double gamma = box ? box_flux * c * p->n
+                           : gamma_coefficient(S) * c * p->n * p->r_cv * p->r_cv;  // molecules per second
+  const double weight = gamma / (double)N_total;                                   // molecules/s per particle
   const double q_inf = 0.5 * p->n * p->m * p->V * p->V;
   const V3 center = load3(p->center), ref = load3(p->ref_point);
 
@@ -664,6 +725,29 @@ int orc_trace(const void* mesh_handle, const orc_params* p, uint64_t N_total, ui
       double u0[4], u1[4];
       draw_block(p->seed, p->stream, pid, 0, u0);
       draw_block(p->seed, p->stream, pid, 1, u1);
+      V3 pos, v;
+      if (box) {
+        // Rectangular CV: the face owning this id; a uniform point on it;
+        // the inward normal speed from the face's law; tangential components
+        // of the free stream plus thermal parts (Box-Muller, as on the sphere).
+        int f = 0;
+        while (f < 5 && pid >= faces[f].end) ++f;
+        const Face& F = faces[f];
+        const int a1 = (F.axis + 1) % 3, a2 = (F.axis + 2) % 3;
+        double pc[3];
+        pc[F.axis] = F.coord;
+        pc[a1] = p->box_lo[a1] + u0[0] * (p->box_hi[a1] - p->box_lo[a1]);
+        pc[a2] = p->box_lo[a2] + u0[1] * (p->box_hi[a2] - p->box_lo[a2]);
+        pos = V3{pc[0], pc[1], pc[2]};
+        const double vn = p->cv_kind == 1 ? normal_speed_inverse(u0[2], F.s) : truncated_normal_inverse(u0[2], F.s);
+        const double rad = std::sqrt(-std::log(u0[3]));
+        const double vh[3] = {Vhat.x, Vhat.y, Vhat.z};
+        double vc[3];
+        vc[F.axis] = 0.0;
+        vc[a1] = S * vh[a1] + rad * std::cos(2.0 * kPi * u1[0]);
+        vc[a2] = S * vh[a2] + rad * std::sin(2.0 * kPi * u1[0]);
+        v = vn * F.n_in + V3{vc[0], vc[1], vc[2]};
+      } else {
       // a3: position on the control sphere (Eq. 11 by inverse transform,
       // theta uniform); stream frame has the flow along +z, so the upstream
       // pole phi = pi/2 sits at -z.
@@ -672,7 +756,7 @@ int orc_trace(const void* mesh_handle, const orc_params* p, uint64_t N_total, ui
       const double theta = 2.0 * kPi * u0[1];
       const V3 out_s{cphi * std::cos(theta), cphi * std::sin(theta), -x};
       const V3 out_b = rodrigues(Vhat, out_s);  // a5 (Eq. 15)
-      V3 pos = center + p->r_cv * out_b;
+      pos = center + p->r_cv * out_b;
       // a4: local frame n (inward), t1 (tangential projection of the flow),
       // t2 = t1 x n; velocity components from Eq. 14a-c; then the transpose
       // of the local frame matrix carries them to body coordinates.
@@ -685,7 +769,8 @@ int orc_trace(const void* mesh_handle, const orc_params* p, uint64_t N_total, ui
       const double rad = std::sqrt(-std::log(u0[3]));
       const double vt1 = S * cphi + rad * std::cos(2.0 * kPi * u1[0]);
       const double vt2 = rad * std::sin(2.0 * kPi * u1[0]);
-      V3 v = vn * nl + vt1 * t1 + vt2 * t2;
+      v = vn * nl + vt1 * t1 + vt2 * t2;
+      }
       if (rec) {
         if (rec->pos) store3(rec->pos + 3 * k, pos);
         if (rec->vel) store3(rec->vel + 3 * k, v);

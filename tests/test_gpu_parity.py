@@ -134,6 +134,37 @@ def test_fp32_concave_satellite_matches_oracle(T, orc, ctx):
         assert abs(res["torque"][k] - ores["torque"][k]) <= 1e-4 * scale + 3 * res["CD_sigma"] / max(res["CD"], 1e-30) * scale
 
 
+@pytest.mark.parametrize("precision,eps", [("fp32", 1.0), ("fp64", 1.0), ("fp32", 0.0)])
+def test_concave_hemisphere_matches_oracle(T, orc, ctx, precision, eps):
+    """Pratt's hyperthermal cavity: every entering particle re-hits the shell
+    (on average twice when diffuse, ~2.8 times when specular)."""
+    case = W.hemisphere_case(N=60_013)
+    p = dict(case["params"], eps_diffuse=eps)
+    prec = T.TPMC_FP32 if precision == "fp32" else T.TPMC_FP64
+    res, rec, ores, orec = _run_pair(T, orc, ctx, case["xyz"], case["tri"], p, case["N"], prec)
+    ident = _assert_paths(rec, orec)
+    assert (rec["n_hits"] >= 3).sum() > 0.1 * res["n_hit_particles"]
+    if precision == "fp64":
+        np.testing.assert_allclose(rec["dv"][ident], orec["dv"][ident], rtol=0, atol=1e-8 * case["params"]["V"])
+    assert cd_close(res["CD"], ores["CD"], ores["CD_sigma"])
+    assert res["n_truncated"] == ores["n_truncated"] == 0
+
+
+def test_concave_hemisphere_full_size_reaches_pratts_limit(T, orc, ctx):
+    """1e7 particles in FP32: eps_eff = (C_D - 2) S_W / sqrt(pi) reaches Pratt's
+    eps_D(90 deg) = 1.05349 within 4 standard errors plus 1e-3 for the faceting."""
+    case = W.hemisphere_case(N=10_000_000)
+    mesh = T.tpmc_mesh_load(ctx, case["xyz"], case["tri"])
+    try:
+        res = T.tpmc_trace(ctx, mesh, T.make_params(**case["params"]), case["N"])
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    k = case["S_W"] / math.sqrt(math.pi)
+    eps = (res["CD"] - 2.0 - 1.0 / case["S"] ** 2) * k
+    assert abs(eps - 1.05349) < 4.0 * res["CD_sigma"] * k + 1e-3, (eps, res["CD_sigma"] * k)
+    assert abs(res["n_hits"] / res["n_hit_particles"] - 2.0) < 3e-3  # 5.4e-4 standard error
+
+
 def test_panels_match_oracle(T, orc, ctx):
     xyz, tri = M.icosphere(2)
     params = dict(**W.base_state(S=4.0), dir=(0, 1.0, 0.2), eps_diffuse=0.7, A_ref=math.pi, r_cv=1.4, seed=9,

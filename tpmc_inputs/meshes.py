@@ -178,6 +178,29 @@ def satellite(target_triangles: int = 60_000):
     return _finish(np.concatenate(xyz), np.concatenate(tri))
 
 
+def hemisphere_shell(radius: float = 1.0, n_lat: int = 32, n_lon: int = 96):
+    """Open hemispherical shell z >= 0 (rim on z = 0, pole at +z), two-sided.
+
+    Seen from z < 0 it is a concave cavity facing -z; a flow along +z enters
+    it.  n_lon * (2 n_lat - 1) triangles (6,048 for the defaults).
+    """
+    xyz = [(0.0, 0.0, radius)]
+    for i in range(1, n_lat + 1):
+        th = 0.5 * np.pi * i / n_lat
+        for j in range(n_lon):
+            ph = 2.0 * np.pi * j / n_lon
+            xyz.append((radius * np.sin(th) * np.cos(ph), radius * np.sin(th) * np.sin(ph), radius * np.cos(th)))
+    idx = lambda i, j: 1 + (i - 1) * n_lon + (j % n_lon)
+    tri = []
+    for j in range(n_lon):
+        tri.append((0, idx(1, j), idx(1, j + 1)))
+    for i in range(1, n_lat):
+        for j in range(n_lon):
+            a, b, c, d = idx(i, j), idx(i + 1, j), idx(i + 1, j + 1), idx(i, j + 1)
+            tri += [(a, b, c), (a, c, d)]
+    return _finish(xyz, tri)
+
+
 def bounding_sphere(xyz):
     """Centre of the axis-aligned bounding box and the largest vertex distance from it."""
     xyz = np.asarray(xyz, dtype=np.float64)

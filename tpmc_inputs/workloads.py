@@ -90,6 +90,29 @@ def satellite_case(N=100_000_000, target_triangles=60_000, seed=7):
                 precision="fp32")
 
 
+def hemisphere_case(N=1_000_000, n_lat=32, n_lon=96, S=40.0, S_W=math.sqrt(2.5), seed=5):
+    """Concave hemispherical shell (6,048 triangles) facing an axial flow.
+
+    The flow (+z) enters the open side; full diffuse accommodation.  A large
+    S (40, T_inf = 1 K) makes the free stream hyperthermal (the incoming part
+    of C_D is 2 + 1/S^2), and the wall temperature is set from S_W (640 K for
+    the default S_W = 1.58) so that the re-emission term of C_D is large
+    against the statistical error.  A_ref is
+    the area of the faceted opening (a regular n_lon-gon inscribed in the
+    unit circle).
+    """
+    xyz, tri = meshes.hemisphere_shell(1.0, n_lat, n_lon)
+    T_inf = 1.0
+    V = stream_speed(S, T_inf)
+    T_W = M_OXYGEN * (V / S_W) ** 2 / (2.0 * K_B)
+    A_ref = 0.5 * n_lon * math.sin(2.0 * math.pi / n_lon)
+    return dict(name=f"hemisphere-{tri.shape[0]}-S{S:g}-SW{S_W:.3g}", xyz=xyz, tri=tri, N=N, S=S, S_W=S_W,
+                params=dict(n=1.0e15, T_inf=T_inf, m=M_OXYGEN, V=V, T_W=T_W, dir=(0.0, 0.0, 1.0), eps_diffuse=1.0,
+                            A_ref=A_ref, ref_point=(0, 0, 0), r_cv=1.2, center=(0, 0, 0), max_bounces=200,
+                            seed=seed),
+                precision="fp32")
+
+
 def attitude_grid(n_yaw=32, n_pitch=32):
     """Yaw, pitch over a 32 x 32 grid of [-90, 90) deg; flow into the body along -(cos p cos y, cos p sin y, sin p)."""
     dirs = []
