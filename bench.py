@@ -290,6 +290,89 @@ def measure_hemisphere(T, ctx):
             "eps_D_pratt": 1.05349, "hits_per_hit_particle": r["n_hits"] / max(r["n_hit_particles"], 1)}
 
 
+def measure_box_cv(T, ctx):
+    """Sphere (1,280-triangle icosphere), S 5, diffuse, 1e7 particles per case, as the
+    stream turns from a box face normal to a box diagonal: C_D of the flux-weighted
+    box and of the Maxwell box relative to the spherical CV's C_D (the consistent
+    seeding), with the combined standard error (host API, wall clock)."""
+    xyz, tri = M.icosphere(3)
+    N = 10_000_000
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    rows, ms, n = [], 0.0, 0
+    try:
+        for alpha in (0.0, 15.0, 30.0, 45.0):
+            a = math.radians(alpha)
+            base = dict(**W.base_state(S=5.0), dir=(math.sin(a), 0.0, math.cos(a)), eps_diffuse=1.0, A_ref=math.pi,
+                        seed=77, max_bounces=8)
+            res = {}
+            for name, extra in (("sphere", dict(r_cv=1.2)),
+                                ("box_flux", dict(cv_kind=1, box_lo=(-1.2,) * 3, box_hi=(1.2,) * 3)),
+                                ("box_maxwell", dict(cv_kind=2, box_lo=(-1.2,) * 3, box_hi=(1.2,) * 3))):
+                res[name] = T.tpmc_trace(ctx, mesh, T.make_params(**base, **extra), N)
+                ms += res[name]["ms"]
+                n += N
+            sph = res["sphere"]
+            row = {"alpha_deg": alpha, "CD_sphere_cv": sph["CD"]}
+            for name in ("box_flux", "box_maxwell"):
+                r = res[name]
+                row[name + "_vs_sphere_pct"] = 100.0 * (r["CD"] / sph["CD"] - 1.0)
+                row[name + "_sigma_pct"] = 100.0 * math.hypot(r["CD_sigma"], sph["CD_sigma"]) / sph["CD"]
+            rows.append(row)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    return {"workload": "icosphere 1,280 tri, S 5, T_W/T_inf 0.3, diffuse, 1e7 particles per case; "
+                        "CV: sphere r 1.2 m or box half-width 1.2 m",
+            "particles_per_s": n / (ms / 1e3), "rows": rows}
+
+
+def measure_moment_sweep(T, ctx, torch, stream, dev):
+    """Restoring moment about the quarter chord (§III.D.1) on the synthetic
+    satellite at the Table 1 conditions: alpha in [-90, 90] step 10 x 8 roll
+    angles = 152 attitudes x 2^22 particles in one persistent launch; the
+    pitching-moment coefficient C_m = -M.e_p / (q_inf c) (pitch-up positive, area-
+    scaled, A_ref = 1 m^2) for the horizontal (beta 0) and vertical (beta 90) rolls."""
+    case = W.satellite_moment_case(N=1)
+    alphas = [-90.0 + 10.0 * i for i in range(19)]
+    betas = [45.0 * j for j in range(8)]
+    V, E, grid = W.alpha_beta_dirs(alphas, betas)
+    K, N_each = len(grid), 1 << 22
+    mesh = T.tpmc_mesh_load(ctx, case["xyz"], case["tri"])
+    try:
+        base = T.make_params(**case["params"], stream_id=1 << 21)
+        dd = torch.tensor(V, dtype=torch.float64, device=dev)
+        out = torch.zeros(K * T.RESULT_BYTES, dtype=torch.uint8, device=dev)
+        T.tpmc_set_stream(ctx, stream)
+        T.tpmc_sweep_device(ctx, mesh, base, dd[:8], None, 8, 1 << 16, out)  # warm-up
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        T.tpmc_sweep_device(ctx, mesh, base, dd, None, K, N_each, out)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b)
+        res = T.results_from_bytes(out.cpu().numpy().tobytes(), K)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    cm = {}
+    for r, e, (al, be) in zip(res, E, grid):
+        cm[(al, be)] = -float(np.dot(r["CM"], e))
+    # trim angle per roll angle: where C_m crosses zero going up in alpha (linear interpolation)
+    trim = {}
+    for be in betas:
+        vals = [cm[(al, be)] for al in alphas]
+        for k in range(len(alphas) - 1):
+            if vals[k] >= 0.0 > vals[k + 1]:
+                trim[f"{be:g}"] = round(alphas[k] + 10.0 * vals[k] / (vals[k] - vals[k + 1]), 2)
+                break
+    stable = all(cm[(al, be)] * al < 0.0 for (al, be) in grid if abs(al) >= 30.0)
+    return {"workload": f"{case['name']}, chord 2 m, ref c/4, {K} attitudes x 2^22 particles, diffuse",
+            "particles_per_s": K * N_each / (ms / 1e3), "ms": ms,
+            "alpha_deg": alphas,
+            "Cm_horizontal_m2": [round(cm[(al, 0.0)], 4) for al in alphas],
+            "Cm_vertical_m2": [round(cm[(al, 90.0)], 4) for al in alphas],
+            "trim_alpha_deg_by_beta": trim, "restoring_for_all_abs_alpha_ge_30": stable,
+            "max_CD_sigma_rel": max(r["CD_sigma"] / r["CD"] for r in res)}
+
+
 def measure_attitude_sweep(T, ctx, torch, stream, dev):
     """32 x 32 yaw/pitch grid x S in {5, 7.5, 10} on the satellite, 2^20 particles per
     item: one persistent launch against 3,072 one-query launches (same N, so equal
@@ -529,6 +612,8 @@ def run_ours(args):
     if rank == 0 and not args.no_extras:
         extras["satellite"] = measure_satellite(T, ctx)
         extras["concave_hemisphere"] = measure_hemisphere(T, ctx)
+        extras["box_cv"] = measure_box_cv(T, ctx)
+        extras["moment_sweep"] = measure_moment_sweep(T, ctx, torch, stream, dev)
         extras["attitude_sweep"] = measure_attitude_sweep(T, ctx, torch, stream, dev)
         extras["serving"] = measure_serving(T, ctx, rate=100.0)
         extras["serving_high_load"] = measure_serving(T, ctx, rate=200.0)

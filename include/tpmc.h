@@ -57,6 +57,28 @@ typedef uint64_t tpmc_query_id;
  * the final force/C_D reduction.  FP64: everything in double. */
 enum { TPMC_FP32 = 0, TPMC_FP64 = 1 };
 
+/* Control volume on which test particles are seeded (tpmc_params.cv_kind).
+ *   TPMC_CV_SPHERE       the paper's consistent seeding on a sphere (§III.A:
+ *                        Eq. 10 flux, Eq. 11 latitude, Eq. 14a-c velocity,
+ *                        Eq. 15 rotation).  The default.
+ *   TPMC_CV_BOX_FLUX     rectangular CV (§I, §III.A; the ANGARA scheme):
+ *                        uniform points on the six faces, face f taking the
+ *                        particle ids [floor(N C_f), floor(N C_{f+1})), C_f
+ *                        the cumulative share of the flat-plate number flux
+ *                        A_f n c G(s_f); inward normal speed from the
+ *                        flux-weighted law of Eq. 14a at s_f = S Vhat.n_in.
+ *                        Kinetically consistent: same expectation as the sphere.
+ *   TPMC_CV_BOX_MAXWELL  the same faces and counts, but the inward normal speed
+ *                        drawn from the free-stream Maxwellian restricted to
+ *                        entering velocities (no flux factor): the
+ *                        inconsistent seeding whose incidence-dependent bias
+ *                        the paper reports.
+ * Faces are ordered +x, -x, +y, -y, +z, -z (x_a = box_hi[a], then box_lo[a]).
+ * Both box kinds use the same Philox draws as the sphere: block 0 holds the
+ * two face coordinates, the normal speed and the tangential radius, block 1
+ * the tangential angle. */
+enum { TPMC_CV_SPHERE = 0, TPMC_CV_BOX_FLUX = 1, TPMC_CV_BOX_MAXWELL = 2 };
+
 /* One free-molecular query (§II.A; §III.C; Table 1 of the paper). */
 typedef struct {
   double n;             /* free-stream number density, 1/m^3 (> 0)                      */
@@ -75,18 +97,29 @@ typedef struct {
   uint64_t seed;        /* Philox key                                                   */
   uint32_t stream_id;   /* Philox counter word 2 (distinguishes runs sharing a seed)   */
   uint32_t want_panels; /* 1: keep per-triangle loads for tpmc_panels                   */
+  uint32_t cv_kind;     /* TPMC_CV_SPHERE (0, default), TPMC_CV_BOX_FLUX, TPMC_CV_BOX_MAXWELL */
+  uint32_t pad_cv;      /* must be 0                                                    */
+  double box_lo[3];     /* box CV corners, body frame, m (box kinds only): the mesh must */
+  double box_hi[3];     /* lie strictly inside; r_cv and center are then ignored         */
+  double l_ref;         /* moment reference length, m, for CM (<= 0: 1 m), e.g. the chord c
+                           of §III.D.1 with ref_point at c/4                               */
 } tpmc_params;
 
 /* Result of one query.  force/torque in N and N m; CD = force . Vhat / (q_inf A_ref). */
 typedef struct {
   double force[3], torque[3];
   double CD, CD_sigma;          /* C_D and its Monte Carlo standard error               */
+  double CF[3];                 /* force / (q_inf A_ref), body axes                     */
+  double CM[3];                 /* torque about ref_point / (q_inf A_ref l_ref), body axes;
+                                   with A_ref = 1 m^2, CM is the area-scaled moment
+                                   coefficient M / (q_inf c) of §III.D.1               */
   double S, S_W;                /* speed ratios V/c_mp and V/c_W                        */
-  double gamma;                 /* molecules per second entering the CV (Eq. 10)        */
+  double gamma;                 /* molecules per second entering the CV (Eq. 10 for the
+                                   sphere; sum of the faces' flat-plate fluxes for a box) */
   double weight;                /* molecules per second per simulated particle (Gamma/N) */
   double q_inf;                 /* dynamic pressure n m V^2 / 2, Pa                     */
   double c_mp;                  /* most probable thermal speed, m/s                     */
-  double r_cv, center[3];       /* control volume used                                  */
+  double r_cv, center[3];       /* control volume used (box: r_cv = 0, centre of the box) */
   double fixed_quantum;         /* value of one unit of the int64 sums (c_mp units)     */
   int64_t sum_dv_q[3];          /* sum over hits of (v_in - v_out), fixed point         */
   int64_t sum_rdv_q[3];         /* sum over hits of (r_hit - ref) x (v_in - v_out)      */

@@ -60,7 +60,7 @@ class Params(ctypes.Structure):
         ("max_bounces", ctypes.c_uint32), ("stream", ctypes.c_uint32), ("seed", ctypes.c_uint64),
         ("t_min_len", ctypes.c_double), ("intersect", ctypes.c_int32), ("threads", ctypes.c_int32),
         ("cv_kind", ctypes.c_int32), ("pad", ctypes.c_int32),
-        ("box_lo", ctypes.c_double * 3), ("box_hi", ctypes.c_double * 3),
+        ("box_lo", ctypes.c_double * 3), ("box_hi", ctypes.c_double * 3), ("l_ref", ctypes.c_double),
     ]
 
 CV_SPHERE, CV_BOX_FLUX, CV_BOX_MAXWELL = 0, 1, 2
@@ -76,6 +76,7 @@ class Result(ctypes.Structure):
         ("sum_d", ctypes.c_double), ("sum_d2", ctypes.c_double),
         ("n_particles", ctypes.c_uint64), ("n_hits", ctypes.c_uint64),
         ("n_hit_particles", ctypes.c_uint64), ("n_truncated", ctypes.c_uint64),
+        ("CF", ctypes.c_double * 3), ("CM", ctypes.c_double * 3),
     ]
 
     def as_dict(self) -> dict:
@@ -266,7 +267,7 @@ class Mesh:
 
 def make_params(*, n, T_inf, m, V, dir, T_W, eps_diffuse, A_ref, ref_point=(0, 0, 0), r_cv=0.0, center=(0, 0, 0),
                 max_bounces=64, stream=0, seed=0, t_min_len=1e-9, intersect=0, threads=0, cv_kind=CV_SPHERE,
-                box_lo=(0, 0, 0), box_hi=(0, 0, 0)) -> Params:
+                box_lo=(0, 0, 0), box_hi=(0, 0, 0), l_ref=0.0) -> Params:
     p = Params()
     p.n, p.T_inf, p.m, p.V = float(n), float(T_inf), float(m), float(V)
     p.dir[:] = [float(x) for x in dir]
@@ -279,6 +280,7 @@ def make_params(*, n, T_inf, m, V, dir, T_W, eps_diffuse, A_ref, ref_point=(0, 0
     p.cv_kind = int(cv_kind)
     p.box_lo[:] = [float(x) for x in box_lo]
     p.box_hi[:] = [float(x) for x in box_hi]
+    p.l_ref = float(l_ref)
     return p
 
 

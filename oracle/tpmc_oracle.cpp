@@ -455,6 +455,7 @@ typedef struct {
   int32_t cv_kind;      // 0 sphere (Eq. 11, 14a-c); 1 box, flux-weighted faces; 2 box, free-stream Maxwellian faces
   int32_t pad;
   double box_lo[3], box_hi[3];  // box control volume (cv_kind 1, 2), body frame, metres
+  double l_ref;                 // moment reference length (<= 0: 1 m)
 } orc_params;
 
 typedef struct {
@@ -462,6 +463,7 @@ typedef struct {
   double CD, CD_sigma, gamma, weight, S, S_W, q_inf, c_mp;
   double sum_dv[3], sum_rdv[3], sum_d, sum_d2;
   uint64_t n_particles, n_hits, n_hit_particles, n_truncated;
+  double CF[3], CM[3];  // force / (q_inf A_ref); torque / (q_inf A_ref l_ref) (§III.D.1)
 } orc_result;
 
 // Per-particle records (each pointer may be null; K = hits kept per particle).
@@ -861,6 +863,11 @@ int orc_trace(const void* mesh_handle, const orc_params* p, uint64_t N_total, ui
   const double scale = gamma / (double)count * p->m * c;
   for (int a = 0; a < 3; ++a) { res->force[a] = scale * sdv[a]; res->torque[a] = scale * srdv[a]; }
   res->CD = (res->force[0] * Vhat.x + res->force[1] * Vhat.y + res->force[2] * Vhat.z) / (q_inf * p->A_ref);
+  const double l_ref = p->l_ref > 0.0 ? p->l_ref : 1.0;
+  for (int a = 0; a < 3; ++a) {
+    res->CF[a] = res->force[a] / (q_inf * p->A_ref);
+    res->CM[a] = res->torque[a] / (q_inf * p->A_ref * l_ref);
+  }
   // Standard error of the mean of the per-particle drag contributions.
   const double nc = (double)count;
   const double mean = sd / nc;

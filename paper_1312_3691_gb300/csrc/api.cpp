@@ -80,6 +80,12 @@ tpmc_status validate_params(const tpmc_params* p) {
   if (!std::isfinite(p->r_cv)) return fail(TPMC_EINVAL, "r_cv must be finite");
   if (p->max_bounces < 1) return fail(TPMC_EINVAL, "max_bounces must be >= 1");
   if (p->precision != TPMC_FP32 && p->precision != TPMC_FP64) return fail(TPMC_EINVAL, "unknown precision");
+  if (p->cv_kind > TPMC_CV_BOX_MAXWELL) return fail(TPMC_EINVAL, "unknown cv_kind");
+  if (!std::isfinite(p->l_ref)) return fail(TPMC_EINVAL, "l_ref must be finite");
+  if (p->cv_kind != TPMC_CV_SPHERE)
+    for (int i = 0; i < 3; ++i)
+      if (!(std::isfinite(p->box_lo[i]) && std::isfinite(p->box_hi[i]) && p->box_hi[i] > p->box_lo[i]))
+        return fail(TPMC_EINVAL, "box CV: box_lo and box_hi must be finite with box_hi > box_lo");
   return TPMC_OK;
 }
 
@@ -88,7 +94,23 @@ tpmc_status fill_query(const MeshRec& m, const tpmc_params* p, uint64_t N, Query
   q->n = p->n; q->T_inf = p->T_inf; q->m = p->m; q->V = p->V;
   for (int i = 0; i < 3; ++i) { q->dir[i] = p->dir[i]; q->ref[i] = p->ref_point[i]; }
   q->T_W = p->T_W; q->eps = p->eps_diffuse; q->A_ref = p->A_ref;
-  if (p->r_cv <= 0.0) {
+  q->l_ref = p->l_ref > 0.0 ? p->l_ref : 1.0;
+  q->cv_kind = p->cv_kind;
+  if (p->cv_kind != TPMC_CV_SPHERE) {
+    // box CV: the body must lie strictly inside the box
+    for (int i = 0; i < 3; ++i) {
+      q->box_lo[i] = p->box_lo[i];
+      q->box_hi[i] = p->box_hi[i];
+      q->center[i] = 0.5 * (p->box_lo[i] + p->box_hi[i]);
+    }
+    q->r_cv = 0.0;
+    for (uint64_t k = 0; k < m.h_tri.size(); ++k) {
+      const double* v = &m.h_xyz[3 * (size_t)m.h_tri[k]];
+      for (int i = 0; i < 3; ++i)
+        if (!(v[i] > q->box_lo[i] && v[i] < q->box_hi[i]))
+          return fail(TPMC_EINVAL, "the mesh is not strictly inside the box control volume");
+    }
+  } else if (p->r_cv <= 0.0) {
     for (int i = 0; i < 3; ++i) q->center[i] = m.center[i];
     q->r_cv = m.radius > 0.0 ? 1.05 * m.radius : 1.0;
   } else {

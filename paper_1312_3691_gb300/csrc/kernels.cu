@@ -63,6 +63,7 @@ template <> struct Fn<float> {
   static __device__ __forceinline__ float erfc(float x) { return erfcf(x); }
   static __device__ __forceinline__ float erfcx(float x) { return erfcxf(x); }
   static __device__ __forceinline__ float ncdfinv(float x) { return normcdfinvf(x); }
+  static __device__ __forceinline__ float erfcinv(float x) { return erfcinvf(x); }
   static __device__ __forceinline__ void sincospi(float x, float* s, float* c) { sincospif(x, s, c); }
   static __device__ __forceinline__ float fabs(float x) { return fabsf(x); }
 };
@@ -73,6 +74,7 @@ template <> struct Fn<double> {
   static __device__ __forceinline__ double erfc(double x) { return ::erfc(x); }
   static __device__ __forceinline__ double erfcx(double x) { return ::erfcx(x); }
   static __device__ __forceinline__ double ncdfinv(double x) { return ::normcdfinv(x); }
+  static __device__ __forceinline__ double erfcinv(double x) { return ::erfcinv(x); }
   static __device__ __forceinline__ void sincospi(double x, double* s, double* c) { ::sincospi(x, s, c); }
   static __device__ __forceinline__ double fabs(double x) { return ::fabs(x); }
   static constexpr double kTolLat = 1e-14;
@@ -353,11 +355,75 @@ __device__ R normal_speed_inverse(R u, R s, const float* tab) {
 // velocity (c_mp units).  Stream frame: flow along +z, upstream pole at -z;
 // local frame n (inward), t1 (tangential projection of the flow), t2 = t1 x n;
 // Eq. 14b-c tangential laws by Box-Muller; Eq. 15 rotation to the body frame.
+// Box-CV constants in the path's precision.
+template <typename R> struct BoxC;
+template <> struct BoxC<float> {
+  static __device__ __forceinline__ float s(const QueryDev& q, int f) { return q.fface_s[f]; }
+  static __device__ __forceinline__ float lo(const QueryDev& q, int i) { return q.fbox_lo[i]; }
+  static __device__ __forceinline__ float ext(const QueryDev& q, int i) { return q.fbox_ext[i]; }
+  static __device__ __forceinline__ float hi(const QueryDev& q, int i) { return q.fbox_lo[i] + q.fbox_ext[i]; }
+};
+template <> struct BoxC<double> {
+  static __device__ __forceinline__ double s(const QueryDev& q, int f) { return q.face_s[f]; }
+  static __device__ __forceinline__ double lo(const QueryDev& q, int i) { return q.box_lo[i]; }
+  static __device__ __forceinline__ double ext(const QueryDev& q, int i) { return q.box_hi[i] - q.box_lo[i]; }
+  static __device__ __forceinline__ double hi(const QueryDev& q, int i) { return q.box_hi[i]; }
+};
+
+// Inward normal speed of the Maxwell box faces: the free-stream Maxwellian
+// restricted to x = v_n / c_mp > 0 (density exp(-(x - s)^2), no flux factor),
+// whose survival function erfc(x - s) / erfc(-s) = 1 - u inverts in closed
+// form.  1 - u is exact for these uniforms.  A face whose erfc(-s) underflows
+// carries no particle ids (its flux share is below 1e-35); the guard only
+// keeps a non-finite value out of the ray set-up.
+template <typename R>
+__device__ __forceinline__ R truncated_normal_inverse(R u, R s) {
+  R x = s + Fn<R>::erfcinv(((R)1 - u) * Fn<R>::erfc(-s));
+  if (!(x > (R)0) || !(x < (R)1e30)) x = (R)1e-30;
+  return x;
+}
+
+// Rectangular-CV seeding (§I, §III.A): the face owning id pid, a uniform
+// point on it, the inward normal speed from the face's law, and the
+// tangential components of the drifting Maxwellian (free-stream drift plus the
+// same Box-Muller pair as on the sphere).
+template <typename R>
+__device__ __forceinline__ void seed_box(const QueryDev& q, const QC<R>& c, const float* vn_table, uint64_t pid,
+                                         const uint4& w0, const uint4& w1, R pos[3], R vel[3]) {
+  int f = 0;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) f += pid >= q.face_end[k] ? 1 : 0;
+  // face axis ax; its first tangential axis (ax + 1) mod 3 takes w0.x, the second w0.y
+  const int ax = f >> 1, a1 = ax == 2 ? 0 : ax + 1;
+  const bool hi_face = (f & 1) == 0;
+  const R s_f = BoxC<R>::s(q, f);
+  const R vn = q.cv_kind == TPMC_CV_BOX_FLUX ? normal_speed_inverse<R>(uniform<R>(w0.z), s_f, vn_table)
+                                             : truncated_normal_inverse<R>(uniform<R>(w0.z), s_f);
+  const R rad = Fn<R>::sqrt(-Fn<R>::log(uniform<R>(w0.w)));
+  R sa, ca;
+  Fn<R>::sincospi((R)2 * uniform<R>(w1.x), &sa, &ca);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (i == ax) {
+      pos[i] = hi_face ? BoxC<R>::hi(q, i) : BoxC<R>::lo(q, i);
+      vel[i] = hi_face ? -vn : vn;
+    } else {
+      const bool first = i == a1;
+      pos[i] = BoxC<R>::lo(q, i) + uniform<R>(first ? w0.x : w0.y) * BoxC<R>::ext(q, i);
+      vel[i] = c.S * c.vhat[i] + rad * (first ? ca : sa);
+    }
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ void seed_particle(const QueryDev& q, const QC<R>& c, const float* vn_table, uint64_t pid,
                                               R pos[3], R vel[3]) {
   const uint4 w0 = draws(q, pid, 0);
   const uint4 w1 = draws(q, pid, 1);
+  if (q.cv_kind != TPMC_CV_SPHERE) {
+    seed_box<R>(q, c, vn_table, pid, w0, w1, pos, vel);
+    return;
+  }
   const R x = latitude_inverse<R>(uniform<R>(w0.x), q, c);
   const R cphi = Fn<R>::sqrt(((R)1 - x) * ((R)1 + x));
   R st, ct;
@@ -1012,6 +1078,31 @@ __global__ void setup_kernel(QueryDev* qs, const QueryDev* base, const double* d
       q.Dnorm = eS + kSqrtPiD * (1.0 + 2.0 * S * S) * erS / (2.0 * S);
       q.K1 = kSqrtPiD / (4.0 * S) * (2.0 * S * S + 1.0) * erfc(S) - 0.5 * eS;
       q.gamma = (kSqrtPiD * eS + (CUDART_PI / (2.0 * S) + CUDART_PI * S) * erS) * c * q.n * q.r_cv * q.r_cv;
+      if (q.cv_kind != TPMC_CV_SPHERE) {
+        // Rectangular CV (§I, §III.A): face f receives the flat-plate number
+        // flux A_f n c G(s_f), G(s) = (e^{-s^2} + sqrt(pi) s erfc(-s)) / (2 sqrt(pi)),
+        // and the particle ids up to floor(N C_{f+1}), C the cumulative share.
+        double flux[6], total = 0.0;
+        for (int f = 0; f < 6; ++f) {
+          const int ax = f / 2, a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
+          const double s_f = S * (f % 2 == 0 ? -vh[ax] : vh[ax]);
+          const double area = (q.box_hi[a1] - q.box_lo[a1]) * (q.box_hi[a2] - q.box_lo[a2]);
+          flux[f] = area * ((exp(-s_f * s_f) + kSqrtPiD * s_f * erfc(-s_f)) / (2.0 * kSqrtPiD));
+          total += flux[f];
+          q.face_s[f] = s_f;
+          q.fface_s[f] = (float)s_f;
+        }
+        double cum = 0.0;
+        for (int f = 0; f < 6; ++f) {
+          cum += flux[f] / total;
+          q.face_end[f] = f == 5 ? q.N : (uint64_t)floor((double)q.N * cum);
+        }
+        for (int i = 0; i < 3; ++i) {
+          q.fbox_lo[i] = (float)q.box_lo[i];
+          q.fbox_ext[i] = (float)(q.box_hi[i] - q.box_lo[i]);
+        }
+        q.gamma = total * c * q.n;
+      }
       q.q_inf = 0.5 * q.n * q.m * q.V * q.V;
       // fixed point: worst case |v| <= max(S + 8, 8 c_W/c), so every int64 sum fits for
       // N * max_bounces hits of |dv| <= 2 |v|max and lever arms <= rmax.
@@ -1039,7 +1130,7 @@ __global__ void setup_kernel(QueryDev* qs, const QueryDev* base, const double* d
     s_ok = st == TPMC_OK;
   }
   __syncthreads();
-  if (!s_ok) return;
+  if (!s_ok || q.cv_kind != TPMC_CV_SPHERE) return;  // the latitude table serves the sphere only
   const double S = q.S, K1 = q.K1, D = q.Dnorm;
   for (int j = threadIdx.x; j <= kHTable; j += blockDim.x) {
     double x;
@@ -1118,6 +1209,11 @@ __global__ void finalize_kernel(const QueryDev* qs, const AccDev* acc, uint32_t 
     const double scale = Np > 0 ? q.gamma / Np * q.m * q.c_mp : 0.0;
     for (int k = 0; k < 3; ++k) { r.force[k] = scale * sdv[k]; r.torque[k] = scale * srdv[k]; }
     r.CD = (r.force[0] * q.vhat[0] + r.force[1] * q.vhat[1] + r.force[2] * q.vhat[2]) / (q.q_inf * q.A_ref);
+    // force and moment coefficient vectors (the moment about ref over q_inf A_ref l_ref, §III.D.1)
+    for (int k = 0; k < 3; ++k) {
+      r.CF[k] = r.force[k] / (q.q_inf * q.A_ref);
+      r.CM[k] = r.torque[k] / (q.q_inf * q.A_ref * q.l_ref);
+    }
     const double mean = Np > 0 ? (sdv[0] * q.vhat[0] + sdv[1] * q.vhat[1] + sdv[2] * q.vhat[2]) / Np : 0.0;
     const double var = Np > 1 ? fmax(0.0, (A.d2 - Np * mean * mean) / (Np - 1.0)) : 0.0;
     r.CD_sigma = Np > 0 ? q.gamma * q.m * q.c_mp / (q.q_inf * q.A_ref) * sqrt(var / Np) : 0.0;

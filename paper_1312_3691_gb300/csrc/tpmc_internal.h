@@ -52,13 +52,14 @@ struct MeshDev {
 // FP64 set-up kernel (flux normalisation, rotation, start table).
 struct QueryDev {
   // inputs
-  double n, T_inf, m, V, dir[3], T_W, eps, A_ref, ref[3], r_cv, center[3];
+  double n, T_inf, m, V, dir[3], T_W, eps, A_ref, ref[3], r_cv, center[3], l_ref;
   double rmax;            // bound on |hit point - ref| (mesh extent seen from ref)
   uint64_t N;             // particles of this query (ids 0..N-1)
   uint64_t seed;
   uint32_t stream_id, max_bounces;
   uint32_t precision;
-  uint32_t pad0;
+  uint32_t cv_kind;       // TPMC_CV_*
+  double box_lo[3], box_hi[3];
   long long* panel;       // [n_tri][3] fixed-point per-triangle sums, or null
   // derived by the set-up kernel
   double S, cw, c_mp, gamma, q_inf, Dnorm, K1, vhat[3], R[9];
@@ -68,6 +69,12 @@ struct QueryDev {
   float fS, fcw, fr_cv, fsqrtpi_4S, fK1, fD_inv, fscale;
   float fR[9], fvhat[3], fcenter[3], fref[3];
   float htab[kHTable + 1];
+  // box CV (cv_kind != sphere): face f = 2a + k is x_a = hi_a (k = 0) or lo_a
+  // (k = 1) and owns particle ids [face_end[f-1], face_end[f]); s_f is its
+  // inward-normal speed ratio
+  uint64_t face_end[6];
+  double face_s[6];
+  float fface_s[6], fbox_lo[3], fbox_ext[3];
 };
 
 // Work item: particles [pid_begin, pid_begin + count) of query `query`,

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libtpmc.so")
 
 TPMC_OK, TPMC_EINVAL, TPMC_ENOMEM, TPMC_EBUSY, TPMC_ETIMEOUT, TPMC_ECUDA, TPMC_ENOTFOUND = range(7)
 TPMC_FP32, TPMC_FP64 = 0, 1
+TPMC_CV_SPHERE, TPMC_CV_BOX_FLUX, TPMC_CV_BOX_MAXWELL = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EBUSY", 4: "ETIMEOUT", 5: "ECUDA", 6: "ENOTFOUND"}
 
 _D3 = ctypes.c_double * 3
@@ -30,12 +31,15 @@ class tpmc_params(ctypes.Structure):
         ("ref_point", _D3), ("r_cv", ctypes.c_double), ("center", _D3),
         ("max_bounces", ctypes.c_uint32), ("precision", ctypes.c_uint32), ("seed", ctypes.c_uint64),
         ("stream_id", ctypes.c_uint32), ("want_panels", ctypes.c_uint32),
+        ("cv_kind", ctypes.c_uint32), ("pad_cv", ctypes.c_uint32), ("box_lo", _D3), ("box_hi", _D3),
+        ("l_ref", ctypes.c_double),
     ]
 
 
 class tpmc_result(ctypes.Structure):
     _fields_ = [
         ("force", _D3), ("torque", _D3), ("CD", ctypes.c_double), ("CD_sigma", ctypes.c_double),
+        ("CF", _D3), ("CM", _D3),
         ("S", ctypes.c_double), ("S_W", ctypes.c_double), ("gamma", ctypes.c_double), ("weight", ctypes.c_double),
         ("q_inf", ctypes.c_double), ("c_mp", ctypes.c_double), ("r_cv", ctypes.c_double), ("center", _D3),
         ("fixed_quantum", ctypes.c_double), ("sum_dv_q", ctypes.c_int64 * 3), ("sum_rdv_q", ctypes.c_int64 * 3),
@@ -201,7 +205,8 @@ def tpmc_mesh_info(ctx, mesh: int) -> dict:
 
 def make_params(*, n, T_inf, m, V, dir, T_W, eps_diffuse, A_ref, ref_point=(0, 0, 0), r_cv=0.0,
                 center=(0, 0, 0), max_bounces=64, precision=TPMC_FP32, seed=0, stream_id=0,
-                want_panels=False) -> tpmc_params:
+                want_panels=False, cv_kind=TPMC_CV_SPHERE, box_lo=(0, 0, 0), box_hi=(0, 0, 0),
+                l_ref=0.0) -> tpmc_params:
     p = tpmc_params()
     p.n, p.T_inf, p.m, p.V = float(n), float(T_inf), float(m), float(V)
     p.dir[:] = [float(x) for x in dir]
@@ -211,6 +216,10 @@ def make_params(*, n, T_inf, m, V, dir, T_W, eps_diffuse, A_ref, ref_point=(0, 0
     p.center[:] = [float(x) for x in center]
     p.max_bounces, p.precision, p.seed = int(max_bounces), int(precision), int(seed)
     p.stream_id, p.want_panels = int(stream_id), int(bool(want_panels))
+    p.cv_kind = int(cv_kind)
+    p.box_lo[:] = [float(x) for x in box_lo]
+    p.box_hi[:] = [float(x) for x in box_hi]
+    p.l_ref = float(l_ref)
     return p
 
 

@@ -3,7 +3,10 @@ import numpy as np
 
 # A hit within this distance (metres) of a triangle edge, or at a grazing
 # angle, may legitimately land on the neighbouring triangle in float32; the
-# particle's path is compared only up to such a hit.
+# particle's path is compared only up to such a hit.  The float32 position
+# error grows with every bounce, and along a ray meeting the surface at
+# incidence cosine cos it becomes an error of (error / cos) in the hit point,
+# so hit b (0-based) counts as near an edge when edge * cos < EDGE_M (1 + b).
 EDGE_M = 1e-5
 GRAZING_COS = 1e-4
 
@@ -23,7 +26,8 @@ def compare_paths(gpu_rec: dict, orc_rec: dict, K: int):
     identical = (nh_g == nh_o) & (tg == to).all(axis=1)
     explained = np.zeros(n, dtype=bool)
     bad = np.nonzero(~identical)[0]
-    near = (orc_rec["edge"] < EDGE_M) | (orc_rec["cosi"] < GRAZING_COS)
+    bounce = np.arange(orc_rec["edge"].shape[1])[None, :]
+    near = (orc_rec["edge"] * orc_rec["cosi"] < EDGE_M * (1 + bounce)) | (orc_rec["cosi"] < GRAZING_COS)
     for i in bad:
         # first bounce where the paths differ
         lim = int(min(max(nh_g[i], nh_o[i]), K))

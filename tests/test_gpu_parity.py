@@ -319,6 +319,144 @@ def test_sweep_equals_separate_queries(T, ctx):
         T.tpmc_mesh_unload(ctx, mesh)
 
 
+# --------------------------------------------- rectangular control volume
+def _box_case(T, alpha_deg, kind, N, S=5.0):
+    a = math.radians(alpha_deg)
+    xyz, tri = M.icosphere(3)
+    params = dict(**W.base_state(S=S), dir=(math.sin(a), 0.0, math.cos(a)), eps_diffuse=1.0, A_ref=math.pi,
+                  seed=77, max_bounces=8, box_lo=(-1.2, -1.2, -1.2), box_hi=(1.2, 1.2, 1.2))
+    cv = {"flux": 1, "maxwell": 2}[kind]
+    return xyz, tri, params, cv
+
+
+@pytest.mark.parametrize("precision,kind,alpha_deg", [
+    ("fp32", "flux", 30.0), ("fp32", "maxwell", 45.0), ("fp64", "flux", 0.0), ("fp64", "maxwell", 30.0),
+])
+def test_box_cv_matches_oracle(T, orc, ctx, precision, kind, alpha_deg):
+    """Rectangular-CV seeding (both face laws) on the same Philox streams: face
+    ids, seeded states and paths agree with the oracle."""
+    N = 50_021
+    xyz, tri, params, cv = _box_case(T, alpha_deg, kind, N)
+    prec = T.TPMC_FP32 if precision == "fp32" else T.TPMC_FP64
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    try:
+        res, rec = T.tpmc_trace_records(ctx, mesh, T.make_params(**params, precision=prec, cv_kind=cv), N, K=K)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    ores, _, orec = orc.trace(orc.Mesh(xyz, tri), orc.make_params(**params, cv_kind=cv), N, records=True, K=K)
+    _assert_paths(rec, orec)
+    tol_pos, tol_vel = (2e-5, 2e-4) if precision == "fp32" else (1e-12, 1e-9)
+    np.testing.assert_allclose(rec["pos"], orec["pos"], rtol=0, atol=tol_pos)
+    np.testing.assert_allclose(rec["vel"], orec["vel"], rtol=0, atol=tol_vel)
+    assert cd_close(res["CD"], ores["CD"], ores["CD_sigma"])
+    assert abs(res["gamma"] - ores["gamma"]) <= 1e-12 * ores["gamma"]
+    assert res["r_cv"] == 0.0
+
+
+def test_box_cv_full_size_bias(T, orc, ctx):
+    """1e7 particles per case on the sphere: the flux-weighted box reproduces the
+    exact drag at 0 and 45 degrees; the Maxwell box is low by an amount that
+    changes with the incidence angle."""
+    N = 10_000_000
+    out = {}
+    for kind in ("flux", "maxwell"):
+        for alpha in (0.0, 45.0):
+            xyz, tri, params, cv = _box_case(T, alpha, kind, N)
+            mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+            try:
+                r = T.tpmc_trace(ctx, mesh, T.make_params(**params, cv_kind=cv), N)
+            finally:
+                T.tpmc_mesh_unload(ctx, mesh)
+            F = orc.panel_sum(xyz, tri, params["dir"], 5.0, 1.0, math.sqrt(0.3))
+            ref = F @ np.asarray(params["dir"]) / (0.5 * 25.0 * math.pi)
+            out[kind, alpha] = ((r["CD"] - ref) / ref, r["CD_sigma"] / ref)
+    for alpha in (0.0, 45.0):
+        e, sig = out["flux", alpha]
+        assert abs(e) <= 1e-4 + 3.5 * sig, (alpha, e, sig)
+        e, sig = out["maxwell", alpha]
+        assert e < -10.0 * sig, (alpha, e, sig)
+    (e0, s0), (e45, s45) = out["maxwell", 0.0], out["maxwell", 45.0]
+    assert abs(e45 - e0) > 5.0 * math.hypot(s0, s45), out
+
+
+def test_box_cv_sweep_equals_separate_queries(T, ctx):
+    """The set-up kernel rebuilds the face shares for every swept direction and S."""
+    xyz, tri, params, cv = _box_case(T, 0.0, "maxwell", 1)
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    try:
+        dirs = W.attitude_grid(2, 3)
+        S = np.array([2.0, 5.0, 9.0] * 2)
+        base = T.make_params(**params, cv_kind=cv, stream_id=300)
+        sw = T.tpmc_sweep(ctx, mesh, base, dirs, S, 30_000)
+        for k in range(len(S)):
+            pk = dict(params)
+            pk["dir"] = tuple(dirs[k])
+            pk["V"] = S[k] * math.sqrt(2 * W.K_B * pk["T_inf"] / pk["m"])
+            r = T.tpmc_trace(ctx, mesh, T.make_params(**pk, cv_kind=cv, stream_id=300 + k), 30_000)
+            assert sw[k]["sum_dv_q"] == r["sum_dv_q"], k
+            assert abs(sw[k]["gamma"] - r["gamma"]) <= 1e-13 * r["gamma"]
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+
+
+def test_box_cv_rejects_a_box_that_cuts_the_mesh(T, ctx):
+    xyz, tri, params, cv = _box_case(T, 0.0, "flux", 1)
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    try:
+        for lo, hi in [((-0.9, -1.2, -1.2), (1.2, 1.2, 1.2)), ((-1.2, -1.2, -1.2), (1.2, -1.3, 1.2))]:
+            p = dict(params, box_lo=lo, box_hi=hi)
+            with pytest.raises(T.TpmcError):
+                T.tpmc_trace(ctx, mesh, T.make_params(**p, cv_kind=cv), 1000)
+        with pytest.raises(T.TpmcError):
+            T.tpmc_trace(ctx, mesh, T.make_params(**params, cv_kind=7), 1000)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+
+
+# ------------------------------------------ moments about the quarter chord
+def test_moment_sweep_matches_oracle(T, orc, ctx):
+    """Restoring-moment sweep (§III.D.1) on the synthetic satellite at the Table 1
+    conditions: per attitude, the swept CM and CF agree with oracle runs on the
+    same Philox streams, and CM is the torque over q_inf A_ref l_ref."""
+    case = W.satellite_moment_case(N=1)
+    V, E, grid = W.alpha_beta_dirs([-60.0, 0.0, 30.0, 90.0], [0.0, 90.0])
+    N_each = 40_000
+    mesh = T.tpmc_mesh_load(ctx, case["xyz"], case["tri"])
+    try:
+        base = T.make_params(**case["params"], stream_id=500)
+        sw = T.tpmc_sweep(ctx, mesh, base, V, None, N_each)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    om = orc.Mesh(case["xyz"], case["tri"])
+    cm_scale = max(np.linalg.norm(r["CM"]) for r in sw)
+    for k, r in enumerate(sw):
+        o, _, _ = orc.trace(om, orc.make_params(**dict(case["params"], dir=tuple(V[k]), stream=500 + k)), N_each)
+        np.testing.assert_allclose(r["CM"], np.asarray(r["torque"]) / (r["q_inf"] * 1.0 * 2.0), rtol=1e-12)
+        # identical particles except the rare near-edge paths: agreement far inside the statistical error
+        assert np.all(np.abs(np.asarray(r["CM"]) - o["CM"]) <= 2e-3 * cm_scale), (grid[k], r["CM"], o["CM"])
+        assert cd_close(r["CD"], o["CD"], o["CD_sigma"])
+        assert abs(r["CD"] - np.dot(r["CF"], V[k])) <= 1e-12 * abs(r["CD"])
+
+
+def test_restoring_moment_full_size(T, ctx):
+    """2^22 particles per attitude: the moment about c/4 turns the roll axis back
+    toward the flow (restoring) for every |alpha| >= 15 deg in both the horizontal
+    (beta = 0) and vertical (beta = 90) roll positions, and grows from 15 to 60 deg."""
+    case = W.satellite_moment_case(N=1)
+    alphas = [-90.0, -60.0, -30.0, -15.0, 15.0, 30.0, 60.0, 90.0]
+    V, E, grid = W.alpha_beta_dirs(alphas, [0.0, 90.0])
+    mesh = T.tpmc_mesh_load(ctx, case["xyz"], case["tri"])
+    try:
+        sw = T.tpmc_sweep(ctx, mesh, T.make_params(**case["params"], stream_id=900), V, None, 1 << 22)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    restoring = {g: math.copysign(1.0, g[0]) * float(np.dot(r["CM"], e)) for r, e, g in zip(sw, E, grid)}
+    for (a, b), m in restoring.items():
+        assert m > 0.0, ((a, b), m)
+    for b in (0.0, 90.0):
+        assert restoring[(15.0, b)] < restoring[(30.0, b)] < restoring[(60.0, b)]
+
+
 def test_sweep_device_entry_point(T, ctx):
     import torch
 

@@ -113,6 +113,44 @@ def hemisphere_case(N=1_000_000, n_lat=32, n_lon=96, S=40.0, S_W=math.sqrt(2.5),
                 precision="fp32")
 
 
+def table1_state():
+    """Flight conditions of §III.D.1, Table 1 (225 km circular orbit): T_inf 809.2 K,
+    T_W 300 K, V 7770 m/s, rho 9.06e-14 kg/m^3, read as atomic oxygen (n = rho / m)."""
+    return dict(n=9.06e-14 / M_OXYGEN, T_inf=809.2, m=M_OXYGEN, V=7770.0, T_W=300.0)
+
+
+def alpha_beta_dirs(alphas_deg, betas_deg):
+    """Attitudes of the restoring-moment sweep (§III.D.1) about the roll axis +z.
+
+    The flow arrives from d = (sin a cos b, sin a sin b, cos a): a is the angle of
+    incidence from the roll axis (a = 0: head-on onto the +z end), b the roll
+    angle.  Returns (Vhat, e_p, grid) with Vhat = -d the flow direction, e_p =
+    (-sin b, cos b, 0) the pitch axis (a positive moment about e_p turns +z
+    toward d, decreasing |a| for a > 0), and grid the (a, b) pairs, a fastest.
+    """
+    grid = [(a, b) for b in betas_deg for a in alphas_deg]
+    V, E = [], []
+    for a, b in grid:
+        ar, br = math.radians(a), math.radians(b)
+        V.append((-math.sin(ar) * math.cos(br), -math.sin(ar) * math.sin(br), -math.cos(ar)))
+        E.append((-math.sin(br), math.cos(br), 0.0))
+    return np.array(V), np.array(E), grid
+
+
+def satellite_moment_case(N=100_000, target_triangles=60_000, seed=11):
+    """Synthetic satellite at the Table 1 conditions, moments about the quarter
+    chord: chord c = 2 m (bus length along the roll axis z), reference point
+    c/4 behind the +z end (z = 0.5 m), A_ref = 1 m^2 so that CM = M / (q_inf c)
+    is the paper's area-scaled pitching-moment coefficient.  Diffuse walls."""
+    xyz, tri = meshes.satellite(target_triangles)
+    c, rb = meshes.bounding_sphere(xyz)
+    return dict(name=f"satellite-{tri.shape[0]}-table1", xyz=xyz, tri=tri, N=N, chord=2.0,
+                params=dict(**table1_state(), dir=(0.0, 0.0, -1.0), eps_diffuse=1.0, A_ref=1.0,
+                            ref_point=(0.0, 0.0, 0.5), l_ref=2.0, r_cv=1.05 * rb, center=tuple(c),
+                            max_bounces=64, seed=seed),
+                precision="fp32")
+
+
 def attitude_grid(n_yaw=32, n_pitch=32):
     """Yaw, pitch over a 32 x 32 grid of [-90, 90) deg; flow into the body along -(cos p cos y, cos p sin y, sin p)."""
     dirs = []
