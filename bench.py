@@ -48,7 +48,9 @@ FLOPS_PER_PARTICLE = 300     # seeding: two inverse-CDF solves, Box-Muller, rota
 FLOPS_PER_HIT = 60           # re-emission, momentum difference, torque, quantisation
 # DRAM bytes per trace launch from an ncu capture, valid only for the kernel
 # source it was taken on (keyed by the SHA-256 of kernels.cu).
-TRACE_TRAFFIC = {}
+# Mean over the four bench groups of dram__bytes_read.sum + dram__bytes_write.sum
+# for one full-size launch (9.6e8 particles).
+TRACE_TRAFFIC = {"73c0a81d5c53edc0ebf35332dda29bf85040ae4b97caa6b12a07d489d7789730": 23_535_936}
 
 
 def kernel_source_hash() -> str:
