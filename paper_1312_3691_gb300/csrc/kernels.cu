@@ -286,8 +286,9 @@ __device__ __forceinline__ float normal_speed_start(const float* tab, float s, f
   return fmaxf(x, 1e-30f);
 }
 
-// Float: two Newton steps from the table start (error ~1e-4 -> ~1e-8 in the
-// bulk, <= 3e-5 relative at the extreme uniforms), on the survival function
+// Float: one Newton step from the bilinear table start (start error ~3e-5;
+// after the step ~6e-8 relative in the median, 2e-5 at the 99th percentile,
+// <= 1.5e-4 at the extreme uniforms u ~ 2^-24), on the survival function
 // above the median and on the CDF below it (selected per lane, no branch on
 // the tail); near x = 0 the CDF comes from 4-point Gauss-Legendre.
 // Double: the table start, then the adaptive loop to double precision.
@@ -312,8 +313,7 @@ __device__ R normal_speed_inverse(R u, R s, const float* tab) {
     }
     const float xq = fminf(0.05f, 0.3f / (1.0f + fabsf(s)));
     float x = x0;
-#pragma unroll 1
-    for (int it = 0; it < 2; ++it) {
+    {
       const float y = x - s;
       float T, p;
       if (s >= 0.0f) {

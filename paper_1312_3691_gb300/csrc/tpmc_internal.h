@@ -19,9 +19,9 @@ namespace tpmc {
 constexpr int kHTable = 128;
 constexpr double kZLo = -5.5, kZHi = 5.5;
 // Normal speed (Eq. 14a), one table per context: x(s_i, z_j) with s_i = kVnSLo + i kVnStep
-// (kVnNS rows) and z_j = kZLo + j kVnStep (kVnNZ columns).
-constexpr double kVnSLo = -8.0, kVnStep = 0.25;
-constexpr int kVnNS = 97, kVnNZ = 45;
+// (kVnNS rows, s in [-8, 16]) and z_j = kZLo + j kVnStep (kVnNZ columns); 69 KB.
+constexpr double kVnSLo = -8.0, kVnStep = 0.125;
+constexpr int kVnNS = 193, kVnNZ = 89;
 constexpr int kMaxStack = 64;    // BVH traversal stack (the builder keeps depth below)
 constexpr int kMaxRecordK = 64;  // hits recorded per particle in verification runs
 
