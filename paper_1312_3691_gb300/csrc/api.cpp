@@ -145,7 +145,11 @@ LaunchCfg Ctx::schedule(const MeshRec& m, uint32_t precision, uint64_t total) {
   if (manual_launch) cfg = manual;
   else if (it != tuned.end()) cfg = it->second;
   else {
-    cfg.block = 128;
+    // Untuned default, from same-box sweeps on GB300: on a tree of a few
+    // nodes the time goes to seeding, which prefers registers (256 threads,
+    // no register cap); on larger trees the traversal's dependent loads prefer
+    // more resident warps (128 threads at the highest occupancy, 8 blocks).
+    cfg.block = m.dev.n_nodes <= 8 ? 256 : 128;
     cfg.smem_nodes = 0;  // the hot top of the tree stays in L1; shared-memory staging costs bank conflicts
     cfg.blocks_per_sm = 0;
     cfg.chunk = 0;

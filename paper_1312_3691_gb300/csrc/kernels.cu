@@ -1282,10 +1282,12 @@ namespace {
 using TraceFn = void (*)(TraceArgs);
 
 // Kernel instantiation for a schedule: the register-capped float variants
-// serve 128-thread blocks at 5 or 6 blocks per SM.
+// serve 128-thread blocks at 5 to 8 blocks per SM.
 TraceFn pick_trace(uint32_t precision, uint32_t block, uint32_t blocks_per_sm) {
   if (precision == TPMC_FP64) return trace_kernel<double, 0>;
-  if (block <= 128 && blocks_per_sm >= 6) return trace_kernel<float, 6>;
+  if (block <= 128 && blocks_per_sm >= 8) return trace_kernel<float, 8>;
+  if (block <= 128 && blocks_per_sm == 7) return trace_kernel<float, 7>;
+  if (block <= 128 && blocks_per_sm == 6) return trace_kernel<float, 6>;
   if (block <= 128 && blocks_per_sm == 5) return trace_kernel<float, 5>;
   return trace_kernel<float, 0>;
 }
@@ -1310,7 +1312,7 @@ int trace_max_blocks_per_sm(uint32_t precision, const LaunchCfg& cfg, uint32_t n
   if (smem > 227 * 1024) return 0;
   int best = occupancy(pick_trace(precision, cfg.block, 1), cfg.block, smem);
   if (precision == TPMC_FP32 && cfg.block <= 128) {
-    for (int minb : {5, 6}) {
+    for (int minb : {5, 6, 7, 8}) {
       const int nb = occupancy(pick_trace(precision, cfg.block, (uint32_t)minb), cfg.block, smem);
       if (nb >= minb) best = std::max(best, nb);
     }

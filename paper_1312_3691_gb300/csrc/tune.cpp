@@ -1,7 +1,7 @@
 // Autotuner of the trace kernel's launch schedule.
 //
 // Candidates: threads per block, shared-memory BVH nodes, resident blocks per
-// SM and the warp fetch size.  Each is timed with CUDA events on a short run of
+// SM (the highest occupancy, 6 and 4) and the traversal-round refill threshold.  Each is timed with CUDA events on a short run of
 // the caller's query; the fastest is kept for the mesh's size class (powers of
 // 4 of the triangle count) and precision, and later launches on meshes of that
 // class use it.
@@ -36,15 +36,15 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
   const uint32_t nn = m.dev.n_nodes;
   for (uint32_t block : {64u, 128u, 256u})
     for (uint32_t sm_nodes : {0u, 256u}) {
-      for (uint32_t occ_div : {1u, 2u})
+      for (uint32_t occ : {0u, 6u, 4u})  // 0: the highest occupancy
         for (uint32_t refill : {4u, 8u, 16u}) {
           LaunchCfg cfg;
           cfg.block = block;
           cfg.smem_nodes = std::min(sm_nodes, nn);
           cfg.refill_at = refill;
           const int maxb = trace_max_blocks_per_sm(params->precision, cfg, nn);
-          if (maxb < 1) continue;
-          cfg.blocks_per_sm = std::max(1u, (uint32_t)maxb / occ_div);
+          if (maxb < 1 || (occ != 0 && occ >= (uint32_t)maxb)) continue;
+          cfg.blocks_per_sm = occ == 0 ? (uint32_t)maxb : occ;
           cfg.chunk = 0;
           cands.push_back(cfg);
         }
