@@ -19,6 +19,9 @@ Parity status per function (the pins live in ``tests/test_oracle_*.py``):
 * full run on convex meshes ............. pinned (panel-sum expectation within 3 sigma)
 * full run on concave meshes ............ pinned (Pratt's hemisphere constant, Eq. 5, re-derived by a
                                           view-factor quadrature; exact specular chord construction)
+* Cercignani-Lampis-Lord (extension) .... pinned (alpha = 1 is the diffuse law, 0 specular; normal-energy and
+                                          tangential-momentum accommodation exactly alpha_n, sigma_t;
+                                          reciprocity: a wall-temperature flux comes back unchanged)
 * rectangular-CV seeding (§I, §III.A) ... pinned (flux-weighted faces reproduce Eq. 4 at every incidence;
                                           face shares against the flat-plate flux; KS of both face laws)
 """
@@ -61,7 +64,11 @@ class Params(ctypes.Structure):
         ("t_min_len", ctypes.c_double), ("intersect", ctypes.c_int32), ("threads", ctypes.c_int32),
         ("cv_kind", ctypes.c_int32), ("pad", ctypes.c_int32),
         ("box_lo", ctypes.c_double * 3), ("box_hi", ctypes.c_double * 3), ("l_ref", ctypes.c_double),
+        ("gsi_model", ctypes.c_int32), ("pad2", ctypes.c_int32), ("alpha_n", ctypes.c_double),
+        ("sigma_t", ctypes.c_double),
     ]
+
+GSI_MAXWELL, GSI_CLL = 0, 1
 
 CV_SPHERE, CV_BOX_FLUX, CV_BOX_MAXWELL = 0, 1, 2
 
@@ -134,6 +141,8 @@ def lib():
         L.orc_rodrigues.argtypes = [_PD, _PD, _PD]
         L.orc_gsi.restype = None
         L.orc_gsi.argtypes = [_PD, _PD, _PD, _PD, _D, _D, _PD]
+        L.orc_cll.restype = None
+        L.orc_cll.argtypes = [_PD, _PD, _PD, _PD, _D, _D, _D, _PD]
         L.orc_panel_sum.restype = None
         L.orc_panel_sum.argtypes = [_PD, _PU32, ctypes.c_uint32, ctypes.c_int, _PD, _D, _D, _D, _PD]
         L.orc_mesh_create.restype = ctypes.c_void_p
@@ -229,6 +238,14 @@ def gsi(v, nrm, t1, u, eps, cw) -> np.ndarray:
     return out
 
 
+def cll(v, nrm, t1, u, alpha_n, alpha_t, cw) -> np.ndarray:
+    out = np.zeros(3)
+    uu = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(4))
+    lib().orc_cll(_pd(_vec3(v)), _pd(_vec3(nrm)), _pd(_vec3(t1)), _pd(uu), float(alpha_n), float(alpha_t), float(cw),
+                  _pd(out))
+    return out
+
+
 def panel_sum(xyz, tri, Vhat, S, eps, cw, two_sided=False) -> np.ndarray:
     X = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64))
     T = np.ascontiguousarray(np.asarray(tri, dtype=np.uint32))
@@ -267,7 +284,8 @@ class Mesh:
 
 def make_params(*, n, T_inf, m, V, dir, T_W, eps_diffuse, A_ref, ref_point=(0, 0, 0), r_cv=0.0, center=(0, 0, 0),
                 max_bounces=64, stream=0, seed=0, t_min_len=1e-9, intersect=0, threads=0, cv_kind=CV_SPHERE,
-                box_lo=(0, 0, 0), box_hi=(0, 0, 0), l_ref=0.0) -> Params:
+                box_lo=(0, 0, 0), box_hi=(0, 0, 0), l_ref=0.0, gsi_model=GSI_MAXWELL, alpha_n=1.0,
+                sigma_t=1.0) -> Params:
     p = Params()
     p.n, p.T_inf, p.m, p.V = float(n), float(T_inf), float(m), float(V)
     p.dir[:] = [float(x) for x in dir]
@@ -281,6 +299,7 @@ def make_params(*, n, T_inf, m, V, dir, T_W, eps_diffuse, A_ref, ref_point=(0, 0
     p.box_lo[:] = [float(x) for x in box_lo]
     p.box_hi[:] = [float(x) for x in box_hi]
     p.l_ref = float(l_ref)
+    p.gsi_model, p.alpha_n, p.sigma_t = int(gsi_model), float(alpha_n), float(sigma_t)
     return p
 
 

@@ -20,6 +20,8 @@
 //   Eq. 14a-c velocity component densities (§III.A.2)
 //   Eq. 15  Rodrigues rotation to body coordinates (§III.A.3)
 //   §II.A   closest-hit ray tracing, diffuse re-emission, momentum sum
+//   (ext.)  Cercignani-Lampis-Lord surface model, an alternative to §II.A's
+//           Maxwell mix (no passage of the paper uses it)
 //   §I, §III.A rectangular control volume with uniform positions on its six
 //           faces and per-face counts from the flat-plate flux (the ANGARA
 //           scheme the paper replaces), with two velocity laws per face
@@ -433,6 +435,32 @@ V3 gsi(V3 v, V3 nrm, V3 t1, const double u[4], double eps, double cw) {
   return v - (2.0 * dot(v, nrm)) * nrm;
 }
 
+// Cercignani-Lampis-Lord surface model (Lord's sampling of the CL kernel; an
+// alternative to the Maxwell mix, not used in the paper).  In units of the
+// wall's thermal speed c_W, with the hit-side normal n (pointing back into
+// the gas), the incident normal speed v_n > 0 and tangential velocity v_t:
+//   normal:     r = sqrt(-alpha_n ln u0), theta = 2 pi u1,
+//               v_n' = sqrt(r^2 + (1 - alpha_n) v_n^2 + 2 r sqrt(1 - alpha_n) v_n cos theta)
+//   tangential: rho = sqrt(-alpha_t ln u2), phi = 2 pi u3,
+//               v_t' = sqrt(1 - alpha_t) v_t + rho (cos phi t1 + sin phi t2),
+// alpha_n the normal-energy accommodation, alpha_t = sigma_t (2 - sigma_t)
+// with sigma_t the tangential-momentum accommodation.  alpha_n = alpha_t = 1
+// is the diffuse law above; 0 is specular reflection.
+V3 cll(V3 v, V3 nrm, V3 t1, const double u[4], double alpha_n, double alpha_t, double cw) {
+  const V3 n_out = dot(v, nrm) < 0.0 ? nrm : (-1.0) * nrm;
+  const V3 t2 = cross(nrm, t1);
+  const double vn = -dot(v, n_out) / cw;
+  const V3 vt = (1.0 / cw) * (v + (cw * vn) * n_out);
+  const double r = std::sqrt(-alpha_n * std::log(u[0]));
+  const double theta = 2.0 * kPi * u[1];
+  const double b = std::sqrt(1.0 - alpha_n) * vn;
+  const double vn_out = std::sqrt(std::max(0.0, r * r + b * b + 2.0 * r * b * std::cos(theta)));
+  const double rho = std::sqrt(-alpha_t * std::log(u[2]));
+  const double phi = 2.0 * kPi * u[3];
+  const V3 vt_out = std::sqrt(1.0 - alpha_t) * vt + (rho * std::cos(phi)) * t1 + (rho * std::sin(phi)) * t2;
+  return cw * (vn_out * n_out + vt_out);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -456,6 +484,9 @@ typedef struct {
   int32_t pad;
   double box_lo[3], box_hi[3];  // box control volume (cv_kind 1, 2), body frame, metres
   double l_ref;                 // moment reference length (<= 0: 1 m)
+  int32_t gsi_model;            // 0 Maxwell mix (eps_diffuse), 1 Cercignani-Lampis-Lord (alpha_n, sigma_t)
+  int32_t pad2;
+  double alpha_n, sigma_t;
 } orc_params;
 
 typedef struct {
@@ -499,6 +530,11 @@ double orc_flux_P(double s) { return flux_P(s); }
 
 void orc_surface_force(const double* nrm, const double* Vhat, double S, double eps, double cw, double* out) {
   store3(out, surface_force(unit(load3(nrm)), unit(load3(Vhat)), S, eps, cw));
+}
+
+void orc_cll(const double* v, const double* nrm, const double* t1, const double* u, double alpha_n, double alpha_t,
+             double cw, double* out) {
+  store3(out, cll(load3(v), unit(load3(nrm)), unit(load3(t1)), u, alpha_n, alpha_t, cw));
 }
 
 void orc_rodrigues(const double* Vhat, const double* x, double* out) {
@@ -665,6 +701,9 @@ int orc_trace(const void* mesh_handle, const orc_params* p, uint64_t N_total, ui
   const double S = p->V / c;
   const double cw = cW / c;
   if (p->cv_kind < 0 || p->cv_kind > 2) return -1;
+  if (p->gsi_model < 0 || p->gsi_model > 1) return -1;
+  if (p->gsi_model == 1 && !(p->alpha_n >= 0 && p->alpha_n <= 1 && p->sigma_t >= 0 && p->sigma_t <= 1)) return -1;
+  const double alpha_t = p->sigma_t * (2.0 - p->sigma_t);
   const bool box = p->cv_kind != 0;
   // Rectangular control volume (§I, §III.A): faces f = 2 a + k are x_a = hi_a
   // (k = 0, inward normal -e_a) and x_a = lo_a (k = 1, inward normal +e_a).
@@ -790,7 +829,8 @@ int orc_trace(const void* mesh_handle, const orc_params* p, uint64_t N_total, ui
         const V3 hp = pos + hit.t * v;
         double ub[4];
         draw_block(p->seed, p->stream, pid, 2 + b, ub);
-        const V3 v_out = gsi(v, m.nrm[i], m.t1[i], ub, p->eps_diffuse, cw);
+        const V3 v_out = p->gsi_model == 1 ? cll(v, m.nrm[i], m.t1[i], ub, p->alpha_n, alpha_t, cw)
+                                           : gsi(v, m.nrm[i], m.t1[i], ub, p->eps_diffuse, cw);
         const V3 dvh = v - v_out;
         dv_p = dv_p + dvh;
         rdv_p = rdv_p + cross(hp - ref, dvh);
