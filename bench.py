@@ -357,14 +357,15 @@ def measure_moment_sweep(T, ctx, torch, stream, dev):
     cm = {}
     for r, e, (al, be) in zip(res, E, grid):
         cm[(al, be)] = -float(np.dot(r["CM"], e))
-    # trim angle per roll angle: where C_m crosses zero going up in alpha (linear interpolation)
+    # trim angle per roll angle: the stable zero of C_m (falling through zero as alpha
+    # grows) nearest alpha = 0, by linear interpolation
     trim = {}
     for be in betas:
         vals = [cm[(al, be)] for al in alphas]
-        for k in range(len(alphas) - 1):
-            if vals[k] >= 0.0 > vals[k + 1]:
-                trim[f"{be:g}"] = round(alphas[k] + 10.0 * vals[k] / (vals[k] - vals[k + 1]), 2)
-                break
+        zeros = [alphas[k] + 10.0 * vals[k] / (vals[k] - vals[k + 1])
+                 for k in range(len(alphas) - 1) if vals[k] >= 0.0 > vals[k + 1]]
+        if zeros:
+            trim[f"{be:g}"] = round(min(zeros, key=abs), 2)
     stable = all(cm[(al, be)] * al < 0.0 for (al, be) in grid if abs(al) >= 30.0)
     return {"workload": f"{case['name']}, chord 2 m, ref c/4, {K} attitudes x 2^22 particles, diffuse",
             "particles_per_s": K * N_each / (ms / 1e3), "ms": ms,

@@ -79,6 +79,19 @@ enum { TPMC_FP32 = 0, TPMC_FP64 = 1 };
  * the tangential angle. */
 enum { TPMC_CV_SPHERE = 0, TPMC_CV_BOX_FLUX = 1, TPMC_CV_BOX_MAXWELL = 2 };
 
+/* Gas-surface interaction (tpmc_params.gsi_model).
+ *   TPMC_GSI_MAXWELL  the paper's model (§II.A): a fraction eps_diffuse of the
+ *                     hits re-emitted diffusely from the flux-weighted
+ *                     half-range Maxwellian at T_W, the rest specularly.  The
+ *                     default.
+ *   TPMC_GSI_CLL      Cercignani-Lampis-Lord (Lord's sampling of the CL
+ *                     kernel; not in the paper): normal-energy accommodation
+ *                     alpha_n and tangential-momentum accommodation sigma_t,
+ *                     both in [0, 1].  1, 1 is the diffuse law; 0, 0 is
+ *                     specular reflection.  Uses the same Philox block per
+ *                     bounce as the Maxwell model. */
+enum { TPMC_GSI_MAXWELL = 0, TPMC_GSI_CLL = 1 };
+
 /* One free-molecular query (§II.A; §III.C; Table 1 of the paper). */
 typedef struct {
   double n;             /* free-stream number density, 1/m^3 (> 0)                      */
@@ -103,6 +116,10 @@ typedef struct {
   double box_hi[3];     /* lie strictly inside; r_cv and center are then ignored         */
   double l_ref;         /* moment reference length, m, for CM (<= 0: 1 m), e.g. the chord c
                            of §III.D.1 with ref_point at c/4                               */
+  uint32_t gsi_model;   /* TPMC_GSI_MAXWELL (0, default) or TPMC_GSI_CLL                 */
+  uint32_t pad_gsi;     /* must be 0                                                    */
+  double alpha_n;       /* CLL normal-energy accommodation, [0, 1]                      */
+  double sigma_t;       /* CLL tangential-momentum accommodation, [0, 1]                */
 } tpmc_params;
 
 /* Result of one query.  force/torque in N and N m; CD = force . Vhat / (q_inf A_ref). */

@@ -82,6 +82,10 @@ tpmc_status validate_params(const tpmc_params* p) {
   if (p->precision != TPMC_FP32 && p->precision != TPMC_FP64) return fail(TPMC_EINVAL, "unknown precision");
   if (p->cv_kind > TPMC_CV_BOX_MAXWELL) return fail(TPMC_EINVAL, "unknown cv_kind");
   if (!std::isfinite(p->l_ref)) return fail(TPMC_EINVAL, "l_ref must be finite");
+  if (p->gsi_model > TPMC_GSI_CLL) return fail(TPMC_EINVAL, "unknown gsi_model");
+  if (p->gsi_model == TPMC_GSI_CLL &&
+      !(p->alpha_n >= 0.0 && p->alpha_n <= 1.0 && p->sigma_t >= 0.0 && p->sigma_t <= 1.0))
+    return fail(TPMC_EINVAL, "CLL: alpha_n and sigma_t must be in [0, 1]");
   if (p->cv_kind != TPMC_CV_SPHERE)
     for (int i = 0; i < 3; ++i)
       if (!(std::isfinite(p->box_lo[i]) && std::isfinite(p->box_hi[i]) && p->box_hi[i] > p->box_lo[i]))
@@ -96,6 +100,12 @@ tpmc_status fill_query(const MeshRec& m, const tpmc_params* p, uint64_t N, Query
   q->T_W = p->T_W; q->eps = p->eps_diffuse; q->A_ref = p->A_ref;
   q->l_ref = p->l_ref > 0.0 ? p->l_ref : 1.0;
   q->cv_kind = p->cv_kind;
+  q->gsi_model = p->gsi_model;
+  if (p->gsi_model == TPMC_GSI_CLL) {
+    const double at = p->sigma_t * (2.0 - p->sigma_t);
+    const double c[4] = {p->alpha_n, std::sqrt(1.0 - p->alpha_n), at, std::sqrt(std::max(0.0, 1.0 - at))};
+    for (int i = 0; i < 4; ++i) { q->cll[i] = c[i]; q->fcll[i] = (float)c[i]; }
+  }
   if (p->cv_kind != TPMC_CV_SPHERE) {
     // box CV: the body must lie strictly inside the box
     for (int i = 0; i < 3; ++i) {
@@ -138,9 +148,9 @@ tpmc_status fill_query(const MeshRec& m, const tpmc_params* p, uint64_t N, Query
   return TPMC_OK;
 }
 
-LaunchCfg Ctx::schedule(const MeshRec& m, uint32_t precision, uint64_t total) {
+LaunchCfg Ctx::schedule(const MeshRec& m, uint32_t variant, uint64_t total) {
   LaunchCfg cfg;
-  const uint64_t key = tune_key(m.dev.n_tri, precision);
+  const uint64_t key = tune_key(m.dev.n_tri, variant);
   auto it = tuned.find(key);
   if (manual_launch) cfg = manual;
   else if (it != tuned.end()) cfg = it->second;
@@ -156,7 +166,7 @@ LaunchCfg Ctx::schedule(const MeshRec& m, uint32_t precision, uint64_t total) {
   }
   cfg.smem_nodes = std::min<uint32_t>(cfg.smem_nodes, m.dev.n_nodes);
   if (cfg.refill_at == 0 || cfg.refill_at > 32) cfg.refill_at = 16;
-  const int maxb = trace_max_blocks_per_sm(precision, cfg, m.dev.n_nodes);
+  const int maxb = trace_max_blocks_per_sm(variant, cfg, m.dev.n_nodes);
   if (cfg.blocks_per_sm == 0 || (int)cfg.blocks_per_sm > maxb) cfg.blocks_per_sm = std::max(1, maxb);
   if (cfg.chunk == 0) {
     const uint64_t warps = (uint64_t)num_sms * cfg.blocks_per_sm * (cfg.block / 32);
@@ -171,7 +181,7 @@ LaunchCfg Ctx::schedule(const MeshRec& m, uint32_t precision, uint64_t total) {
 // or uploaded one by one, traced together, finalised into d_out.
 tpmc_status Ctx::run(const MeshRec& m, const QueryDev* h_queries, uint32_t nq, const QueryDev* h_base,
                      const double* d_dirs, const double* d_S, const ItemDev* h_items, uint32_t n_items, uint64_t total,
-                     uint32_t precision, tpmc_result* d_out, const RecordsDev* rec) {
+                     uint32_t variant, tpmc_result* d_out, const RecordsDev* rec) {
   tpmc_status st;
   if ((st = grow(s_queries, sizeof(QueryDev) * (size_t)nq, "queries")) != TPMC_OK) return st;
   if ((st = grow(s_acc, sizeof(AccDev) * (size_t)nq, "accumulators")) != TPMC_OK) return st;
@@ -212,12 +222,12 @@ tpmc_status Ctx::run(const MeshRec& m, const QueryDev* h_queries, uint32_t nq, c
   a.count_work = counters ? 1u : 0u;
   a.vn_table = vn_table;
   if (rec) a.rec = *rec;
-  const LaunchCfg cfg = schedule(m, precision, total);
+  const LaunchCfg cfg = schedule(m, variant, total);
   a.chunk = cfg.chunk;
   a.smem_nodes = cfg.smem_nodes;
   a.refill_at = cfg.refill_at;
   last_cfg = cfg;
-  if (total > 0 && (e = launch_trace(a, precision, cfg, num_sms, stream)) != cudaSuccess) return cuda_fail(e, "trace kernel");
+  if (total > 0 && (e = launch_trace(a, variant, cfg, num_sms, stream)) != cudaSuccess) return cuda_fail(e, "trace kernel");
   if ((e = launch_finalize(d_queries, d_acc, nq, nullptr, d_out, stream)) != cudaSuccess)
     return cuda_fail(e, "finalize kernel");
   if ((e = cudaMemcpyAsync(h_err_word, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
@@ -460,7 +470,7 @@ static tpmc_status trace_common(Ctx* c, tpmc_mesh_id mesh, const tpmc_params* pa
   item.g_begin = 0; item.pid_begin = 0; item.count = N; item.query = 0;
   tpmc_status rs = c->grow(c->s_out, sizeof(tpmc_result), "result");
   if (rs == TPMC_OK)
-    rs = c->run(m, &q, 1, nullptr, nullptr, nullptr, &item, 1, N, params->precision, (tpmc_result*)c->s_out.ptr,
+    rs = c->run(m, &q, 1, nullptr, nullptr, nullptr, &item, 1, N, trace_variant(params), (tpmc_result*)c->s_out.ptr,
                 records ? &rec : nullptr);
   cudaError_t e = cudaSuccess;
   if (rs == TPMC_OK) e = cudaMemcpyAsync(out, c->s_out.ptr, sizeof(tpmc_result), cudaMemcpyDeviceToHost, c->stream);
@@ -564,7 +574,7 @@ static tpmc_status sweep_common(Ctx* c, tpmc_mesh_id mesh, const tpmc_params* ba
   const MeshRec& m = it->second;
   QueryDev q;
   if ((st = fill_query(m, base, N_each, &q)) != TPMC_OK) return st;
-  return c->run(m, nullptr, K, &q, d_dirs, d_S, nullptr, 0, (uint64_t)K * N_each, base->precision, d_out, nullptr);
+  return c->run(m, nullptr, K, &q, d_dirs, d_S, nullptr, 0, (uint64_t)K * N_each, trace_variant(base), d_out, nullptr);
 }
 
 tpmc_status tpmc_sweep(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* base, const double* h_dirs,

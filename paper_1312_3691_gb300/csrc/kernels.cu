@@ -3,12 +3,15 @@
 //   setup_kernel     FP64: free-stream set-up per query (Nomenclature; Eq. 10
 //                    flux; particle weight, §II.A), Rodrigues matrix (Eq. 15),
 //                    fixed-point scale, start table of the latitude inverse CDF.
-//   trace_kernel<R>  persistent, one warp = 32 particle slots refilled from a
+//   trace_kernel<R, MINB, CLL>
+//                    persistent, one warp = 32 particle slots refilled from a
 //                    global work counter by ballot; per slot: Philox draws,
-//                    seeding (Eq. 11, Eq. 14a-c, Eq. 15), BVH closest hit with a
-//                    watertight ray/triangle test (§II.A), Maxwell re-emission,
-//                    int64 fixed-point momentum sums, until the particle misses
-//                    or reaches max_bounces.  R = float (FP32 path) or double.
+//                    seeding (Eq. 11, Eq. 14a-c, Eq. 15; or the box CV),
+//                    BVH closest hit with a watertight ray/triangle test
+//                    (§II.A), Maxwell (or, with CLL, Cercignani-Lampis-Lord)
+//                    re-emission, int64 fixed-point momentum sums, until the
+//                    particle misses or reaches max_bounces.  R = float (FP32
+//                    path) or double; MINB = register-capped occupancy.
 //   finalize_kernel  FP64 reduction to force, torque, C_D and its error.
 //   panels_kernel    FP64 per-triangle pressure and shear.
 //
@@ -687,11 +690,54 @@ template <> struct Frame<double> {
 // flux-weighted half-range Maxwellian at T_W about the hit-side normal
 // (normal speed c_W sqrt(-ln u1), tangential c_W sqrt(-ln u2) at angle 2 pi u3
 // in the frame (t1, n x t1)); otherwise specular reflection.
+template <typename R> struct CllC;
+template <> struct CllC<float> {
+  static __device__ __forceinline__ float get(const QueryDev& q, int k) { return q.fcll[k]; }
+};
+template <> struct CllC<double> {
+  static __device__ __forceinline__ double get(const QueryDev& q, int k) { return q.cll[k]; }
+};
+
+// Cercignani-Lampis-Lord re-emission (Lord's sampling of the CL kernel), in
+// units of c_W about the hit-side normal n_out (sgn n): with the incident
+// normal speed v_n and tangential components (v_t1, v_t2) along (t1, n x t1),
+//   r = sqrt(-alpha_n ln u0), theta = 2 pi u1,
+//   v_n' = sqrt(r^2 + (1 - alpha_n) v_n^2 + 2 r sqrt(1 - alpha_n) v_n cos theta),
+//   rho = sqrt(-alpha_t ln u2), phi = 2 pi u3,
+//   v_t' = sqrt(1 - alpha_t) v_t + rho (cos phi, sin phi).
 template <typename R>
+__device__ __forceinline__ void reemit_cll(const QueryDev& q, R cw, const uint4& w, R sgn, const R n[3],
+                                           const R t1[3], R v[3]) {
+  const R t2[3] = {n[1] * t1[2] - n[2] * t1[1], n[2] * t1[0] - n[0] * t1[2], n[0] * t1[1] - n[1] * t1[0]};
+  const R inv_cw = (R)1 / cw;
+  const R vn = -sgn * (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) * inv_cw;
+  const R vt1 = (v[0] * t1[0] + v[1] * t1[1] + v[2] * t1[2]) * inv_cw;
+  const R vt2 = (v[0] * t2[0] + v[1] * t2[1] + v[2] * t2[2]) * inv_cw;
+  const R r = Fn<R>::sqrt(-CllC<R>::get(q, 0) * Fn<R>::log(uniform<R>(w.x)));
+  R st, ct;
+  Fn<R>::sincospi((R)2 * uniform<R>(w.y), &st, &ct);
+  const R b = CllC<R>::get(q, 1) * vn;
+  const R vn_out = Fn<R>::sqrt(fmax(r * r + b * b + (R)2 * r * b * ct, (R)0));
+  const R rho = Fn<R>::sqrt(-CllC<R>::get(q, 2) * Fn<R>::log(uniform<R>(w.z)));
+  R sp, cp;
+  Fn<R>::sincospi((R)2 * uniform<R>(w.w), &sp, &cp);
+  const R a1 = CllC<R>::get(q, 3) * vt1 + rho * cp, a2 = CllC<R>::get(q, 3) * vt2 + rho * sp;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v[i] = cw * (sgn * vn_out * n[i] + a1 * t1[i] + a2 * t2[i]);
+}
+
+// CLL: compiled into the kernel variants that serve launches holding a CLL query.
+template <typename R, bool CLL>
 __device__ __forceinline__ void reemit(const QueryDev& q, R cw, uint64_t pid, uint32_t bounce, const R n[3],
                                        const R t1[3], R v[3]) {
   const uint4 w = draws(q, pid, 2 + bounce);
   const R vdn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+  if constexpr (CLL) {
+    if (q.gsi_model == TPMC_GSI_CLL) {
+      reemit_cll<R>(q, cw, w, vdn < (R)0 ? (R)1 : (R)-1, n, t1, v);
+      return;
+    }
+  }
   if (uniform<double>(w.x) < q.eps) {
     const R sgn = vdn < (R)0 ? (R)1 : (R)-1;
     const R vn = cw * Fn<R>::sqrt(-Fn<R>::log(uniform<R>(w.y)));
@@ -818,7 +864,7 @@ constexpr uint32_t kQueue = 64;     // queue slots per warp (two seeding batches
 // MINB > 0: a register-capped instantiation for 128-thread blocks with at
 // least MINB resident blocks per SM (more warps to hide latency, at the cost
 // of spills inside the out-of-line seeding).
-template <typename R, int MINB>
+template <typename R, int MINB, bool CLL>
 __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : 1) trace_kernel(TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t n_stage = min(a.smem_nodes, a.mesh.n_nodes);
@@ -868,7 +914,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : 1) tra
 #pragma unroll
         for (int i = 0; i < 3; ++i) { hp[i] = ray.o[i] + tv.tbest * ray.d[i]; v_in[i] = ray.d[i]; }
         R v[3] = {ray.d[0], ray.d[1], ray.d[2]};
-        reemit<R>(q, HitConst<R>::cw(q), pid, bounce, nrm, t1, v);
+        reemit<R, CLL>(q, HitConst<R>::cw(q), pid, bounce, nrm, t1, v);
         R dv[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) { dv[i] = v_in[i] - v[i]; dvp[i] += dv[i]; }
@@ -1272,7 +1318,8 @@ cudaError_t launch_vn_table(float* d_table, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-size_t trace_smem_bytes(const LaunchCfg& cfg, uint32_t n_nodes, uint32_t precision) {
+size_t trace_smem_bytes(const LaunchCfg& cfg, uint32_t n_nodes, uint32_t variant) {
+  const uint32_t precision = variant & 1u;
   const size_t queue = (size_t)(cfg.block / 32) * kQueue *
                        (precision == TPMC_FP64 ? sizeof(Seeded<double>) : sizeof(Seeded<float>));
   return (size_t)std::min(cfg.smem_nodes, n_nodes) * 4 * sizeof(float4) + queue + (size_t)cfg.block * sizeof(LaneAcc);
@@ -1283,13 +1330,19 @@ using TraceFn = void (*)(TraceArgs);
 
 // Kernel instantiation for a schedule: the register-capped float variants
 // serve 128-thread blocks at 5 to 8 blocks per SM.
-TraceFn pick_trace(uint32_t precision, uint32_t block, uint32_t blocks_per_sm) {
-  if (precision == TPMC_FP64) return trace_kernel<double, 0>;
-  if (block <= 128 && blocks_per_sm >= 8) return trace_kernel<float, 8>;
-  if (block <= 128 && blocks_per_sm == 7) return trace_kernel<float, 7>;
-  if (block <= 128 && blocks_per_sm == 6) return trace_kernel<float, 6>;
-  if (block <= 128 && blocks_per_sm == 5) return trace_kernel<float, 5>;
-  return trace_kernel<float, 0>;
+template <bool CLL>
+TraceFn pick_trace_t(uint32_t precision, uint32_t block, uint32_t blocks_per_sm) {
+  if (precision == TPMC_FP64) return trace_kernel<double, 0, CLL>;
+  if (block <= 128 && blocks_per_sm >= 8) return trace_kernel<float, 8, CLL>;
+  if (block <= 128 && blocks_per_sm == 7) return trace_kernel<float, 7, CLL>;
+  if (block <= 128 && blocks_per_sm == 6) return trace_kernel<float, 6, CLL>;
+  if (block <= 128 && blocks_per_sm == 5) return trace_kernel<float, 5, CLL>;
+  return trace_kernel<float, 0, CLL>;
+}
+
+TraceFn pick_trace(uint32_t variant, uint32_t block, uint32_t blocks_per_sm) {
+  return (variant & kVariantCll) ? pick_trace_t<true>(variant & 1u, block, blocks_per_sm)
+                                 : pick_trace_t<false>(variant & 1u, block, blocks_per_sm);
 }
 
 int occupancy(TraceFn f, uint32_t block, size_t smem) {
@@ -1307,24 +1360,24 @@ int occupancy(TraceFn f, uint32_t block, size_t smem) {
 }  // namespace
 
 // Largest resident block count over the instantiations that can run `cfg`.
-int trace_max_blocks_per_sm(uint32_t precision, const LaunchCfg& cfg, uint32_t n_nodes) {
-  const size_t smem = trace_smem_bytes(cfg, n_nodes, precision);
+int trace_max_blocks_per_sm(uint32_t variant, const LaunchCfg& cfg, uint32_t n_nodes) {
+  const size_t smem = trace_smem_bytes(cfg, n_nodes, variant);
   if (smem > 227 * 1024) return 0;
-  int best = occupancy(pick_trace(precision, cfg.block, 1), cfg.block, smem);
-  if (precision == TPMC_FP32 && cfg.block <= 128) {
+  int best = occupancy(pick_trace(variant, cfg.block, 1), cfg.block, smem);
+  if ((variant & 1u) == TPMC_FP32 && cfg.block <= 128) {
     for (int minb : {5, 6, 7, 8}) {
-      const int nb = occupancy(pick_trace(precision, cfg.block, (uint32_t)minb), cfg.block, smem);
+      const int nb = occupancy(pick_trace(variant, cfg.block, (uint32_t)minb), cfg.block, smem);
       if (nb >= minb) best = std::max(best, nb);
     }
   }
   return best;
 }
 
-cudaError_t launch_trace(const TraceArgs& args, uint32_t precision, const LaunchCfg& cfg, int num_sms,
+cudaError_t launch_trace(const TraceArgs& args, uint32_t variant, const LaunchCfg& cfg, int num_sms,
                          cudaStream_t stream) {
-  const size_t smem = trace_smem_bytes(cfg, args.mesh.n_nodes, precision);
+  const size_t smem = trace_smem_bytes(cfg, args.mesh.n_nodes, variant);
   const uint32_t grid = (uint32_t)num_sms * cfg.blocks_per_sm;
-  const TraceFn f = pick_trace(precision, cfg.block, cfg.blocks_per_sm);
+  const TraceFn f = pick_trace(variant, cfg.block, cfg.blocks_per_sm);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   f<<<grid, cfg.block, smem, stream>>>(args);

@@ -46,11 +46,11 @@ struct ServeState;  // serve.cpp
 
 tpmc_status fill_query(const MeshRec& m, const tpmc_params* p, uint64_t N, QueryDev* q);
 
-inline uint64_t tune_key(uint32_t n_tri, uint32_t precision) {
-  // size classes: powers of 4 of the triangle count
+inline uint64_t tune_key(uint32_t n_tri, uint32_t variant) {
+  // size classes: powers of 4 of the triangle count; one table per kernel variant
   uint32_t cls = 0;
   while (n_tri > 1 && cls < 16) { n_tri >>= 2; ++cls; }
-  return ((uint64_t)precision << 32) | cls;
+  return ((uint64_t)variant << 32) | cls;
 }
 
 struct Ctx {
@@ -80,10 +80,10 @@ struct Ctx {
   tpmc_status alloc(void** p, size_t bytes, const char* what);
   void release(void* p);
   tpmc_status grow(Scratch& s, size_t bytes, const char* what);
-  LaunchCfg schedule(const MeshRec& m, uint32_t precision, uint64_t total);
+  LaunchCfg schedule(const MeshRec& m, uint32_t variant, uint64_t total);  // variant: see trace_variant
   tpmc_status run(const MeshRec& m, const QueryDev* h_queries, uint32_t nq, const QueryDev* h_base,
                   const double* d_dirs, const double* d_S, const ItemDev* h_items, uint32_t n_items,
-                  uint64_t total, uint32_t precision, tpmc_result* d_out, const RecordsDev* rec);
+                  uint64_t total, uint32_t variant, tpmc_result* d_out, const RecordsDev* rec);
   tpmc_status check_error_word();
   ~Ctx();
 };

@@ -7,7 +7,7 @@
 //      little work left, smallest first (they finish in this step), then to
 //      the large ones in arrival order,
 //   3. enqueues the step -- set-up of newly admitted queries, one persistent
-//      trace launch per (mesh, precision) group over work items from all of
+//      trace launch per (mesh, kernel variant) group over work items from all of
 //      the group's queries, the FP64 reduction of the queries that finish,
 //      the read-back -- while the previous step may still run (two steps in
 //      flight keep the GPU busy during the host's bookkeeping), and
@@ -41,7 +41,7 @@ constexpr int kGroupStreams = 4;                 // streams the groups of a step
 struct Request {
   tpmc_query_id id = 0;
   tpmc_mesh_id mesh = 0;
-  uint32_t precision = 0;
+  uint32_t variant = 0;     // trace-kernel variant (precision and surface model)
   uint32_t n_tri = 0;
   bool want_panels = false;
   QueryDev q;                  // inputs (set-up runs on the device at admission)
@@ -152,11 +152,11 @@ bool enqueue_step(ServeState* s, int b, const std::vector<Request*>& cand, cudaE
     take[r] = t;
     budget -= t;
   }
-  // groups by (mesh, precision) in the order of `order`
+  // groups by (mesh, kernel variant) in the order of `order`
   std::vector<std::pair<std::pair<tpmc_mesh_id, uint32_t>, std::vector<Request*>>> groups;
   for (Request* r : order) {
     if (take[r] == 0) continue;
-    const auto key = std::make_pair(r->mesh, r->precision);
+    const auto key = std::make_pair(r->mesh, r->variant);
     auto it = std::find_if(groups.begin(), groups.end(), [&](const auto& g) { return g.first == key; });
     if (it == groups.end()) {
       if ((int)groups.size() == kMaxGroups) continue;  // later groups wait for the next step
@@ -468,7 +468,7 @@ tpmc_status tpmc_submit(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* par
     r->id = c->next_query++;
   }
   r->mesh = mesh;
-  r->precision = params->precision;
+  r->variant = trace_variant(params);
   r->want_panels = params->want_panels != 0;
   r->N = N;
   r->t_submit = Clock::now();

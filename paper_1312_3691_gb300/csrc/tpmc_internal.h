@@ -60,6 +60,10 @@ struct QueryDev {
   uint32_t precision;
   uint32_t cv_kind;       // TPMC_CV_*
   double box_lo[3], box_hi[3];
+  uint32_t gsi_model;     // TPMC_GSI_*
+  uint32_t pad1;
+  double cll[4];          // CLL: alpha_n, sqrt(1 - alpha_n), alpha_t = sigma_t (2 - sigma_t), sqrt(1 - alpha_t)
+  float fcll[4];
   long long* panel;       // [n_tri][3] fixed-point per-triangle sums, or null
   // derived by the set-up kernel
   double S, cw, c_mp, gamma, q_inf, Dnorm, K1, vhat[3], R[9];
@@ -132,18 +136,26 @@ struct LaunchCfg {
 };
 
 // ------------------------------------------------------------ host launchers
+// Trace-kernel variant: the precision (TPMC_FP32 / TPMC_FP64) plus
+// kVariantCll when the launch holds a query with the CLL surface model, so
+// that launches without one run code compiled without that branch.
+constexpr uint32_t kVariantCll = 2u;
+inline uint32_t trace_variant(const tpmc_params* p) {
+  return p->precision | (p->gsi_model == TPMC_GSI_CLL ? kVariantCll : 0u);
+}
+
 cudaError_t launch_setup(QueryDev* d_queries, uint32_t nq, const QueryDev* d_base, const double* d_dirs,
                          const double* d_S, ItemDev* d_items, const uint32_t* d_slots, cudaStream_t stream);
 cudaError_t launch_vn_table(float* d_table, cudaStream_t stream);
-cudaError_t launch_trace(const TraceArgs& args, uint32_t precision, const LaunchCfg& cfg, int num_sms,
+cudaError_t launch_trace(const TraceArgs& args, uint32_t variant, const LaunchCfg& cfg, int num_sms,
                          cudaStream_t stream);
 cudaError_t launch_finalize(const QueryDev* d_queries, const AccDev* d_acc, uint32_t nq, const uint32_t* d_slots,
                             tpmc_result* d_out, cudaStream_t stream);
 cudaError_t launch_panels(const QueryDev* d_query, const long long* d_panel, const float4* frames,
                           const double* frames64, uint32_t n_tri, double* d_pressure, double* d_shear,
                           cudaStream_t stream);
-size_t trace_smem_bytes(const LaunchCfg& cfg, uint32_t n_nodes, uint32_t precision);
-int trace_max_blocks_per_sm(uint32_t precision, const LaunchCfg& cfg, uint32_t n_nodes);
+size_t trace_smem_bytes(const LaunchCfg& cfg, uint32_t n_nodes, uint32_t variant);
+int trace_max_blocks_per_sm(uint32_t variant, const LaunchCfg& cfg, uint32_t n_nodes);
 
 // ---------------------------------------------------------------- BVH (host)
 struct BvhBuild {

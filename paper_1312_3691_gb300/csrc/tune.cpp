@@ -3,7 +3,7 @@
 // Candidates: threads per block, shared-memory BVH nodes, resident blocks per
 // SM (the highest occupancy, 6 and 4) and the traversal-round refill threshold.  Each is timed with CUDA events on a short run of
 // the caller's query; the fastest is kept for the mesh's size class (powers of
-// 4 of the triangle count) and precision, and later launches on meshes of that
+// 4 of the triangle count) and kernel variant, and later launches on meshes of that
 // class use it.
 #include <algorithm>
 #include <cstring>
@@ -42,7 +42,7 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
           cfg.block = block;
           cfg.smem_nodes = std::min(sm_nodes, nn);
           cfg.refill_at = refill;
-          const int maxb = trace_max_blocks_per_sm(params->precision, cfg, nn);
+          const int maxb = trace_max_blocks_per_sm(trace_variant(params), cfg, nn);
           if (maxb < 1 || (occ != 0 && occ >= (uint32_t)maxb)) continue;
           cfg.blocks_per_sm = occ == 0 ? (uint32_t)maxb : occ;
           cfg.chunk = 0;
@@ -61,7 +61,7 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
       c->manual_launch = true;
       c->manual = cfg;
       cudaEventRecord(e0, c->stream);
-      st = c->run(m, &q, 1, nullptr, nullptr, nullptr, &item, 1, N_trial, params->precision,
+      st = c->run(m, &q, 1, nullptr, nullptr, nullptr, &item, 1, N_trial, trace_variant(params),
                   (tpmc_result*)c->s_out.ptr, nullptr);
       cudaEventRecord(e1, c->stream);
       if (st != TPMC_OK) break;
@@ -79,7 +79,7 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
   c->manual = old_manual;
   if (st != TPMC_OK) return st;
   if ((st = c->check_error_word()) != TPMC_OK) return st;
-  c->tuned[tune_key(m.dev.n_tri, params->precision)] = best_cfg;
+  c->tuned[tune_key(m.dev.n_tri, trace_variant(params))] = best_cfg;
   if (best) {
     best->block = best_cfg.block;
     best->blocks_per_sm = best_cfg.blocks_per_sm;

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libtpmc.so")
 TPMC_OK, TPMC_EINVAL, TPMC_ENOMEM, TPMC_EBUSY, TPMC_ETIMEOUT, TPMC_ECUDA, TPMC_ENOTFOUND = range(7)
 TPMC_FP32, TPMC_FP64 = 0, 1
 TPMC_CV_SPHERE, TPMC_CV_BOX_FLUX, TPMC_CV_BOX_MAXWELL = 0, 1, 2
+TPMC_GSI_MAXWELL, TPMC_GSI_CLL = 0, 1
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EBUSY", 4: "ETIMEOUT", 5: "ECUDA", 6: "ENOTFOUND"}
 
 _D3 = ctypes.c_double * 3
@@ -32,7 +33,8 @@ class tpmc_params(ctypes.Structure):
         ("max_bounces", ctypes.c_uint32), ("precision", ctypes.c_uint32), ("seed", ctypes.c_uint64),
         ("stream_id", ctypes.c_uint32), ("want_panels", ctypes.c_uint32),
         ("cv_kind", ctypes.c_uint32), ("pad_cv", ctypes.c_uint32), ("box_lo", _D3), ("box_hi", _D3),
-        ("l_ref", ctypes.c_double),
+        ("l_ref", ctypes.c_double), ("gsi_model", ctypes.c_uint32), ("pad_gsi", ctypes.c_uint32),
+        ("alpha_n", ctypes.c_double), ("sigma_t", ctypes.c_double),
     ]
 
 
@@ -206,7 +208,7 @@ def tpmc_mesh_info(ctx, mesh: int) -> dict:
 def make_params(*, n, T_inf, m, V, dir, T_W, eps_diffuse, A_ref, ref_point=(0, 0, 0), r_cv=0.0,
                 center=(0, 0, 0), max_bounces=64, precision=TPMC_FP32, seed=0, stream_id=0,
                 want_panels=False, cv_kind=TPMC_CV_SPHERE, box_lo=(0, 0, 0), box_hi=(0, 0, 0),
-                l_ref=0.0) -> tpmc_params:
+                l_ref=0.0, gsi_model=TPMC_GSI_MAXWELL, alpha_n=1.0, sigma_t=1.0) -> tpmc_params:
     p = tpmc_params()
     p.n, p.T_inf, p.m, p.V = float(n), float(T_inf), float(m), float(V)
     p.dir[:] = [float(x) for x in dir]
@@ -220,6 +222,7 @@ def make_params(*, n, T_inf, m, V, dir, T_W, eps_diffuse, A_ref, ref_point=(0, 0
     p.box_lo[:] = [float(x) for x in box_lo]
     p.box_hi[:] = [float(x) for x in box_hi]
     p.l_ref = float(l_ref)
+    p.gsi_model, p.alpha_n, p.sigma_t = int(gsi_model), float(alpha_n), float(sigma_t)
     return p
 
 

@@ -319,6 +319,57 @@ def test_sweep_equals_separate_queries(T, ctx):
         T.tpmc_mesh_unload(ctx, mesh)
 
 
+# ------------------------------------------ Cercignani-Lampis-Lord surfaces
+@pytest.mark.parametrize("precision,shape,alpha_n,sigma_t", [
+    ("fp32", "hemisphere", 0.6, 0.4), ("fp64", "hemisphere", 0.6, 0.4), ("fp32", "satellite", 0.8, 0.9),
+])
+def test_cll_matches_oracle(T, orc, ctx, precision, shape, alpha_n, sigma_t):
+    """CLL re-emission on concave bodies (many bounces) against the oracle on the same streams."""
+    if shape == "hemisphere":
+        case = W.hemisphere_case(N=50_021, S=6.0)
+    else:
+        case = W.satellite_case(N=30_011)
+    p = dict(case["params"], gsi_model=1, alpha_n=alpha_n, sigma_t=sigma_t)
+    prec = T.TPMC_FP32 if precision == "fp32" else T.TPMC_FP64
+    res, rec, ores, orec = _run_pair(T, orc, ctx, case["xyz"], case["tri"], p, case["N"], prec)
+    ident = _assert_paths(rec, orec)
+    assert (rec["n_hits"] >= 2).sum() > (1000 if shape == "hemisphere" else 30)  # multiple reflections
+    if precision == "fp64":
+        np.testing.assert_allclose(rec["dv"][ident], orec["dv"][ident], rtol=0, atol=1e-8 * case["params"]["V"])
+    assert cd_close(res["CD"], ores["CD"], ores["CD_sigma"])
+
+
+def test_cll_full_size_diffuse_limit_is_exact(T, orc, ctx):
+    """1e7 particles: CLL with both coefficients 1 is the diffuse law, so the
+    sphere's C_D is the exact (panel-sum) value within the error."""
+    xyz, tri = M.icosphere(3)
+    Vhat = np.array([0.3, -0.5, 0.81]) / np.linalg.norm([0.3, -0.5, 0.81])
+    params = dict(**W.base_state(S=5.0), dir=tuple(Vhat), eps_diffuse=0.0, A_ref=math.pi, r_cv=1.2, seed=5,
+                  max_bounces=8, gsi_model=1, alpha_n=1.0, sigma_t=1.0)
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    try:
+        r = T.tpmc_trace(ctx, mesh, T.make_params(**params), 10_000_000)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    F = orc.panel_sum(xyz, tri, Vhat, 5.0, 1.0, math.sqrt(0.3))
+    ref = F @ Vhat / (0.5 * 25.0 * math.pi)
+    assert abs(r["CD"] - ref) <= 1e-4 * ref + 3.5 * r["CD_sigma"], (r["CD"], ref, r["CD_sigma"])
+
+
+def test_cll_rejects_coefficients_outside_the_unit_interval(T, ctx):
+    xyz, tri = M.icosphere(1)
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    try:
+        base = dict(**W.base_state(S=5.0), dir=(0, 0, 1.0), eps_diffuse=1.0, A_ref=math.pi, r_cv=1.2, gsi_model=1)
+        for an, st in ((1.2, 0.5), (0.5, -0.1), (float("nan"), 0.5)):
+            with pytest.raises(T.TpmcError):
+                T.tpmc_trace(ctx, mesh, T.make_params(**base, alpha_n=an, sigma_t=st), 1000)
+        with pytest.raises(T.TpmcError):
+            T.tpmc_trace(ctx, mesh, T.make_params(**dict(base, gsi_model=5)), 1000)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+
+
 # --------------------------------------------- rectangular control volume
 def _box_case(T, alpha_deg, kind, N, S=5.0):
     a = math.radians(alpha_deg)
@@ -492,6 +543,11 @@ def test_serving_results_equal_alone_and_in_the_mix(T, ctx):
             N = int(np.exp(rng.uniform(np.log(1e4), np.log(3e6))))
             p = dict(**W.base_state(S=S), dir=tuple(d), eps_diffuse=0.9, A_ref=1.0, seed=1000 + i,
                      max_bounces=64)
+            if i % 4 == 3:  # some queries use the CLL surface model (their own kernel variant)
+                p.update(gsi_model=1, alpha_n=0.7, sigma_t=0.5)
+            if i % 5 == 4:  # and some seed on the box control volume
+                c, rb = M.bounding_sphere(meshes[mi][0])
+                p.update(cv_kind=1, box_lo=tuple(c - 1.05 * rb), box_hi=tuple(c + 1.05 * rb))
             queries.append((ids[mi], p, N))
         handles = [T.tpmc_submit(ctx, m, T.make_params(**p), N) for m, p, N in queries]
         mixed = [T.tpmc_poll(ctx, h, -1) for h in handles]
