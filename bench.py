@@ -50,7 +50,7 @@ FLOPS_PER_HIT = 60           # re-emission, momentum difference, torque, quantis
 # source it was taken on (keyed by the SHA-256 of kernels.cu).
 # Mean over the four bench groups of dram__bytes_read.sum + dram__bytes_write.sum
 # for one full-size launch (9.6e8 particles).
-TRACE_TRAFFIC = {"73c0a81d5c53edc0ebf35332dda29bf85040ae4b97caa6b12a07d489d7789730": 23_535_936}
+TRACE_TRAFFIC = {"6d3ab4cfc245647606ab9f0c79811c90de42fa23a614071cfda80f1a63c004c1": 270_522_112}
 
 
 def kernel_source_hash() -> str:
