@@ -9,8 +9,11 @@
 //   3. enqueues the step -- set-up of newly admitted queries, one persistent
 //      trace launch per (mesh, kernel variant) group over work items from all of
 //      the group's queries, the FP64 reduction of the queries that finish,
-//      the read-back -- while the previous step may still run (two steps in
-//      flight keep the GPU busy during the host's bookkeeping), and
+//      the read-back -- while the previous step may still run.  Each of the
+//      two step buffers has its own streams, so a step's trace launches start
+//      on the SMs that the previous step's launch tails free up; the
+//      reduction waits for the traces of both steps, since a finishing query
+//      may have had work in the previous one, and
 //   4. waits for the older step on the host (a CUDA event; no device-side
 //      wait), publishes its finished results and frees their slots.
 // A query's particles keep their ids 0..N-1 whatever steps they land in, and
@@ -31,7 +34,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr uint32_t kSlots = 1024;
 constexpr size_t kMaxQueue = 1u << 16;
-constexpr uint64_t kStepParticles = 1ull << 24;  // particle budget of one step
+constexpr uint64_t kStepParticles = 1ull << 25;  // particle budget of one step
 constexpr uint64_t kSmallQuery = kStepParticles / 4;  // work left below which a query goes first
 constexpr int kInFlight = 2;                     // steps enqueued ahead of the host
 constexpr int kMaxGroups = 64;                   // trace launches per step
@@ -68,6 +71,11 @@ struct StepBuf {
   unsigned long long* d_counters = nullptr;
   int* d_err = nullptr;
   cudaEvent_t ev = nullptr;
+  cudaStream_t st = nullptr;                     // set-up, reduction, read-back
+  cudaStream_t group_stream[kGroupStreams] = {};  // trace launches
+  cudaEvent_t group_done[kGroupStreams] = {};
+  cudaEvent_t ready = nullptr;                   // set-up done
+  cudaEvent_t traces_done = nullptr;             // every trace launch of the step done
   std::vector<Request*> members, finishing;
 };
 
@@ -80,10 +88,6 @@ struct ServeState {
   std::deque<Request*> queue;
   std::map<tpmc_query_id, Request*> all;
   std::vector<Request*> slots;
-  cudaStream_t stream = nullptr;
-  cudaStream_t group_stream[kGroupStreams] = {};
-  cudaEvent_t group_done[kGroupStreams] = {};
-  cudaEvent_t ready = nullptr;
   QueryDev* d_q = nullptr;
   AccDev* d_acc = nullptr;
   StepBuf buf[kInFlight];
@@ -128,7 +132,7 @@ void admit(ServeState* s) {
 
 // Builds and enqueues one step in buffer b (caller does not hold s->m).
 // Returns false when there was nothing to run.
-bool enqueue_step(ServeState* s, int b, const std::vector<Request*>& cand, cudaError_t& e) {
+bool enqueue_step(ServeState* s, int b, int prev, const std::vector<Request*>& cand, cudaError_t& e) {
   Ctx* c = s->ctx;
   StepBuf& B = s->buf[b];
   B.members.clear();
@@ -166,7 +170,7 @@ bool enqueue_step(ServeState* s, int b, const std::vector<Request*>& cand, cudaE
     it->second.push_back(r);
   }
   if (groups.empty()) return false;
-  cudaStream_t st = s->stream;
+  cudaStream_t st = B.st;
   // set-up of newly admitted queries, straight into their slots
   uint32_t n_fresh = 0;
   for (auto& g : groups)
@@ -187,7 +191,7 @@ bool enqueue_step(ServeState* s, int b, const std::vector<Request*>& cand, cudaE
   if (e == cudaSuccess) e = cudaMemsetAsync(B.d_counters, 0, kMaxGroups * sizeof(unsigned long long), st);
   // the groups run on their own streams once the set-up is done, so that one
   // launch's tail overlaps the next launch's start
-  if (e == cudaSuccess) e = cudaEventRecord(s->ready, st);
+  if (e == cudaSuccess) e = cudaEventRecord(B.ready, st);
   bool used[kGroupStreams] = {};
   uint32_t n_items = 0;
   for (size_t gi = 0; gi < groups.size(); ++gi) {
@@ -214,8 +218,8 @@ bool enqueue_step(ServeState* s, int b, const std::vector<Request*>& cand, cudaE
       cfg = c->schedule(mr, groups[gi].first.second, g);
     }
     const int gs = (int)(gi % kGroupStreams);
-    cudaStream_t gst = s->group_stream[gs];
-    if (!used[gs] && e == cudaSuccess) e = cudaStreamWaitEvent(gst, s->ready, 0);
+    cudaStream_t gst = B.group_stream[gs];
+    if (!used[gs] && e == cudaSuccess) e = cudaStreamWaitEvent(gst, B.ready, 0);
     used[gs] = true;
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(B.d_items + first_item, B.h_items + first_item, (n_items - first_item) * sizeof(ItemDev),
@@ -238,9 +242,12 @@ bool enqueue_step(ServeState* s, int b, const std::vector<Request*>& cand, cudaE
   }
   for (int gs = 0; gs < kGroupStreams && e == cudaSuccess; ++gs) {
     if (!used[gs]) continue;
-    e = cudaEventRecord(s->group_done[gs], s->group_stream[gs]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->group_done[gs], 0);
+    e = cudaEventRecord(B.group_done[gs], B.group_stream[gs]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, B.group_done[gs], 0);
   }
+  if (e == cudaSuccess) e = cudaEventRecord(B.traces_done, st);
+  // the reduction also waits for the previous step's traces (still in flight)
+  if (prev >= 0 && e == cudaSuccess) e = cudaStreamWaitEvent(st, s->buf[prev].traces_done, 0);
   for (size_t i = 0; i < B.finishing.size(); ++i) B.h_fin[i] = (uint32_t)B.finishing[i]->slot;
   if (!B.finishing.empty() && e == cudaSuccess) {
     e = cudaMemcpyAsync(B.d_fin, B.h_fin, B.finishing.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
@@ -339,7 +346,9 @@ void loop(ServeState* s) {
     }
     cudaError_t e = cudaSuccess;
     if (free_buf >= 0) {
-      const bool pushed = enqueue_step(s, free_buf, cand, e);
+      // inflight is changed only by this thread, so it can be read here unlocked
+      const int prev = s->inflight.empty() ? -1 : s->inflight.back();
+      const bool pushed = enqueue_step(s, free_buf, prev, cand, e);
       if (pushed) {
         std::lock_guard<std::mutex> lk(s->m);
         s->inflight.push_back(free_buf);
@@ -356,26 +365,48 @@ void loop(ServeState* s) {
   while (!s->inflight.empty()) retire_step(s, cudaSuccess);
 }
 
+// Waits for and destroys the streams and events of the step buffers (null ones are skipped).
+void destroy_streams(ServeState* s) {
+  for (int b = 0; b < kInFlight; ++b) {
+    StepBuf& B = s->buf[b];
+    for (int g = 0; g < kGroupStreams; ++g) {
+      if (B.group_stream[g]) { cudaStreamSynchronize(B.group_stream[g]); cudaStreamDestroy(B.group_stream[g]); }
+      if (B.group_done[g]) cudaEventDestroy(B.group_done[g]);
+    }
+    if (B.st) { cudaStreamSynchronize(B.st); cudaStreamDestroy(B.st); }
+    if (B.ev) cudaEventDestroy(B.ev);
+    if (B.ready) cudaEventDestroy(B.ready);
+    if (B.traces_done) cudaEventDestroy(B.traces_done);
+  }
+}
+
 tpmc_status start_serving(Ctx* c) {
   ServeState* s = new ServeState();
   s->ctx = c;
   s->slots.assign(kSlots, nullptr);
-  cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-  for (int b = 0; b < kInFlight && e == cudaSuccess; ++b)
-    e = cudaEventCreateWithFlags(&s->buf[b].ev, cudaEventBlockingSync | cudaEventDisableTiming);
-  for (int g = 0; g < kGroupStreams && e == cudaSuccess; ++g) {
-    e = cudaStreamCreateWithFlags(&s->group_stream[g], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->group_done[g], cudaEventDisableTiming);
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < kInFlight && e == cudaSuccess; ++b) {
+    StepBuf& B = s->buf[b];
+    e = cudaEventCreateWithFlags(&B.ev, cudaEventBlockingSync | cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B.ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B.traces_done, cudaEventDisableTiming);
+    for (int g = 0; g < kGroupStreams && e == cudaSuccess; ++g) {
+      e = cudaStreamCreateWithFlags(&B.group_stream[g], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B.group_done[g], cudaEventDisableTiming);
+    }
   }
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ready, cudaEventDisableTiming);
-  if (e != cudaSuccess) { delete s; return cuda_fail(e, "serving stream"); }
+  if (e != cudaSuccess) {
+    destroy_streams(s);
+    delete s;
+    return cuda_fail(e, "serving stream");
+  }
   const size_t per_buf_dev = kSlots * (sizeof(ItemDev) + 2 * sizeof(uint32_t) + sizeof(tpmc_result)) +
                              kMaxGroups * sizeof(unsigned long long) + 256;
   const size_t dev_bytes = kSlots * (sizeof(QueryDev) + sizeof(AccDev)) + kInFlight * per_buf_dev + 256;
   tpmc_status st = c->alloc(&s->d_block, dev_bytes, "serving slots");
   if (st != TPMC_OK) {
-    cudaStreamDestroy(s->stream);
-    for (int b = 0; b < kInFlight; ++b) if (s->buf[b].ev) cudaEventDestroy(s->buf[b].ev);
+    destroy_streams(s);
     delete s;
     return st;
   }
@@ -385,8 +416,7 @@ tpmc_status start_serving(Ctx* c) {
   const size_t per_buf_host = kSlots * (sizeof(ItemDev) + 2 * sizeof(uint32_t) + sizeof(tpmc_result)) + 64;
   if ((e = cudaMallocHost(&s->h_block, kInFlight * per_buf_host)) != cudaSuccess) {
     c->release(s->d_block);
-    cudaStreamDestroy(s->stream);
-    for (int b = 0; b < kInFlight; ++b) cudaEventDestroy(s->buf[b].ev);
+    destroy_streams(s);
     delete s;
     return cuda_fail(e, "serving host buffers");
   }
@@ -423,21 +453,13 @@ void stop_serving(Ctx* c) {
   }
   s->cv_work.notify_all();
   if (s->th.joinable()) s->th.join();
-  cudaStreamSynchronize(s->stream);
+  destroy_streams(s);
   for (auto& kv : s->all) {
     if (kv.second->d_panel) c->release(kv.second->d_panel);
     delete kv.second;
   }
   c->release(s->d_block);
   cudaFreeHost(s->h_block);
-  for (int b = 0; b < kInFlight; ++b) cudaEventDestroy(s->buf[b].ev);
-  for (int g = 0; g < kGroupStreams; ++g) {
-    cudaStreamSynchronize(s->group_stream[g]);
-    cudaStreamDestroy(s->group_stream[g]);
-    cudaEventDestroy(s->group_done[g]);
-  }
-  cudaEventDestroy(s->ready);
-  cudaStreamDestroy(s->stream);
   delete s;
   c->serve = nullptr;
 }
