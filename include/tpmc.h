@@ -74,9 +74,9 @@ enum { TPMC_FP32 = 0, TPMC_FP64 = 1 };
  *                        inconsistent seeding whose incidence-dependent bias
  *                        the paper reports.
  * Faces are ordered +x, -x, +y, -y, +z, -z (x_a = box_hi[a], then box_lo[a]).
- * Both box kinds use the same Philox draws as the sphere: block 0 holds the
- * two face coordinates, the normal speed and the tangential radius, block 1
- * the tangential angle. */
+ * Both box kinds use the same Philox draws as the sphere: the top 23 bits of
+ * block 0's four words give the two face coordinates, the normal speed and
+ * the tangential radius; 23 of their low bits give the tangential angle. */
 enum { TPMC_CV_SPHERE = 0, TPMC_CV_BOX_FLUX = 1, TPMC_CV_BOX_MAXWELL = 2 };
 
 /* Gas-surface interaction (tpmc_params.gsi_model).

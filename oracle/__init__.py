@@ -133,6 +133,8 @@ def lib():
         L.orc_sphere_cd_quadrature.argtypes = [_D, _D, _D, ctypes.c_int]
         L.orc_cylinder_cd_quadrature.restype = _D
         L.orc_cylinder_cd_quadrature.argtypes = [_D, _D, _D, _D, _D, _D, ctypes.c_int]
+        L.orc_seed_uniforms.restype = None
+        L.orc_seed_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, _PD]
         L.orc_philox4x32_10.restype = None
         L.orc_philox4x32_10.argtypes = [_PU32, _PU32, _PU32]
         L.orc_surface_force.restype = None
@@ -235,6 +237,12 @@ def gsi(v, nrm, t1, u, eps, cw) -> np.ndarray:
     out = np.zeros(3)
     uu = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(4))
     lib().orc_gsi(_pd(_vec3(v)), _pd(_vec3(nrm)), _pd(_vec3(t1)), _pd(uu), float(eps), float(cw), _pd(out))
+    return out
+
+
+def seed_uniforms(seed, stream, pid) -> np.ndarray:
+    out = np.zeros(5)
+    lib().orc_seed_uniforms(int(seed), int(stream), int(pid), _pd(out))
     return out
 
 

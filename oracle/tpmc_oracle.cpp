@@ -82,14 +82,30 @@ double uniform_from_word(uint32_t w) { return ((double)(w >> 9) + 0.5) * 0x1p-23
 //   key     = (seed low 32 bits, seed high 32 bits)
 //   counter = (particle id low, particle id high, stream id, block)
 //   block 0 : seeding   -> u_x (position), u_theta, u_vn, u_r (Box-Muller radius)
-//   block 1 : seeding   -> u_a (Box-Muller angle); the other three words unused
+//             from the top 23 bits of its four words, and u_a (Box-Muller
+//             angle) from 23 of the low bits the other four leave unused:
+//             bits 0-8 of word 0, 0-8 of word 1 and 0-4 of word 2
 //   block 2+b: bounce b -> u_gsi (diffuse or specular), u1, u2, u3 (re-emission)
-void draw_block(uint64_t seed, uint32_t stream, uint64_t pid, uint32_t block, double u[4]) {
+// (Block 1 is not drawn.)
+void draw_words(uint64_t seed, uint32_t stream, uint64_t pid, uint32_t block, uint32_t w[4]) {
   const uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)(pid >> 32), stream, block};
   const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-  uint32_t w[4];
   philox4x32_10(ctr, key, w);
+}
+
+void draw_block(uint64_t seed, uint32_t stream, uint64_t pid, uint32_t block, double u[4]) {
+  uint32_t w[4];
+  draw_words(seed, stream, pid, block, w);
   for (int i = 0; i < 4; ++i) u[i] = uniform_from_word(w[i]);
+}
+
+// The five seeding uniforms of particle pid (see the layout above).
+void seed_uniforms(uint64_t seed, uint32_t stream, uint64_t pid, double u[5]) {
+  uint32_t w[4];
+  draw_words(seed, stream, pid, 0, w);
+  for (int i = 0; i < 4; ++i) u[i] = uniform_from_word(w[i]);
+  const uint32_t low = (w[0] & 0x1FFu) | ((w[1] & 0x1FFu) << 9) | ((w[2] & 0x1Fu) << 18);
+  u[4] = uniform_from_word(low << 9);
 }
 
 // ---------------------------------------------------------------------------
@@ -513,6 +529,7 @@ typedef struct {
 
 void orc_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) { philox4x32_10(ctr, key, out); }
 double orc_uniform(uint32_t w) { return uniform_from_word(w); }
+void orc_seed_uniforms(uint64_t seed, uint32_t stream, uint64_t pid, double* out) { seed_uniforms(seed, stream, pid, out); }
 double orc_gamma_coefficient(double S) { return gamma_coefficient(S); }
 double orc_position_norm(double S) { return position_norm(S); }
 double orc_g_phi(double phi, double S) { return g_phi(phi, S); }
@@ -763,9 +780,10 @@ int orc_trace(const void* mesh_handle, const orc_params* p, uint64_t N_total, ui
     const uint64_t lo = count * (uint64_t)tid / threads, hi = count * (uint64_t)(tid + 1) / threads;
     for (uint64_t k = lo; k < hi; ++k) {
       const uint64_t pid = pid_begin + k;
-      double u0[4], u1[4];
-      draw_block(p->seed, p->stream, pid, 0, u0);
-      draw_block(p->seed, p->stream, pid, 1, u1);
+      double us[5];
+      seed_uniforms(p->seed, p->stream, pid, us);
+      const double* u0 = us;       // u_x, u_theta, u_vn, u_r
+      const double* u1 = us + 4;   // u_a
       V3 pos, v;
       if (box) {
         // Rectangular CV: the face owning this id; a uniform point on it;

@@ -392,7 +392,7 @@ __device__ __forceinline__ R truncated_normal_inverse(R u, R s) {
 // same Box-Muller pair as on the sphere).
 template <typename R>
 __device__ __forceinline__ void seed_box(const QueryDev& q, const QC<R>& c, const float* vn_table, uint64_t pid,
-                                         const uint4& w0, const uint4& w1, R pos[3], R vel[3]) {
+                                         const uint4& w0, uint32_t w_a, R pos[3], R vel[3]) {
   int f = 0;
 #pragma unroll
   for (int k = 0; k < 5; ++k) f += pid >= q.face_end[k] ? 1 : 0;
@@ -404,7 +404,7 @@ __device__ __forceinline__ void seed_box(const QueryDev& q, const QC<R>& c, cons
                                              : truncated_normal_inverse<R>(uniform<R>(w0.z), s_f);
   const R rad = Fn<R>::sqrt(-Fn<R>::log(uniform<R>(w0.w)));
   R sa, ca;
-  Fn<R>::sincospi((R)2 * uniform<R>(w1.x), &sa, &ca);
+  Fn<R>::sincospi((R)2 * uniform<R>(w_a), &sa, &ca);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (i == ax) {
@@ -421,10 +421,12 @@ __device__ __forceinline__ void seed_box(const QueryDev& q, const QC<R>& c, cons
 template <typename R>
 __device__ __forceinline__ void seed_particle(const QueryDev& q, const QC<R>& c, const float* vn_table, uint64_t pid,
                                               R pos[3], R vel[3]) {
+  // one Philox block: u_x, u_theta, u_vn, u_r from the top 23 bits of its
+  // words, u_a (Box-Muller angle) from 23 low bits they leave unused
   const uint4 w0 = draws(q, pid, 0);
-  const uint4 w1 = draws(q, pid, 1);
+  const uint32_t w_a = ((w0.x & 0x1FFu) | ((w0.y & 0x1FFu) << 9) | ((w0.z & 0x1Fu) << 18)) << 9;
   if (q.cv_kind != TPMC_CV_SPHERE) {
-    seed_box<R>(q, c, vn_table, pid, w0, w1, pos, vel);
+    seed_box<R>(q, c, vn_table, pid, w0, w_a, pos, vel);
     return;
   }
   const R x = latitude_inverse<R>(uniform<R>(w0.x), q, c);
@@ -434,7 +436,7 @@ __device__ __forceinline__ void seed_particle(const QueryDev& q, const QC<R>& c,
   const R vn = normal_speed_inverse<R>(uniform<R>(w0.z), c.S * x, vn_table);
   const R rad = Fn<R>::sqrt(-Fn<R>::log(uniform<R>(w0.w)));
   R sa, ca;
-  Fn<R>::sincospi((R)2 * uniform<R>(w1.x), &sa, &ca);
+  Fn<R>::sincospi((R)2 * uniform<R>(w_a), &sa, &ca);
   const R vt1 = c.S * cphi + rad * ca;
   const R vt2 = rad * sa;
   // stream-frame vectors: out = (cphi ct, cphi st, -x), n = -out, t1 = (x ct, x st, cphi), t2 = (st, -ct, 0)

@@ -44,6 +44,24 @@ def test_uniform_mapping(orc):
         assert float(np.float32(u)) == u
 
 
+def test_seeding_uniforms_layout_and_independence(orc):
+    """The five seeding uniforms come from one Philox block: the top 23 bits of
+    its four words, and a fifth from bits 0-8 of words 0 and 1 and 0-4 of word
+    2, rebuilt here from the published generator's output."""
+    seed, stream = 0x0123456789ABCDEF, 77
+    for pid in (0, 1, 12345, 2 ** 33 + 5):
+        w = orc.philox4x32_10([pid & 0xFFFFFFFF, pid >> 32, stream, 0], [seed & 0xFFFFFFFF, seed >> 32])
+        low = (int(w[0]) & 0x1FF) | ((int(w[1]) & 0x1FF) << 9) | ((int(w[2]) & 0x1F) << 18)
+        want = [((int(x) >> 9) + 0.5) * 2.0 ** -23 for x in w] + [(low + 0.5) * 2.0 ** -23]
+        assert list(orc.seed_uniforms(seed, stream, pid)) == want
+    # over many particles: each uniform is uniform, and the fifth is uncorrelated with the others
+    U = np.array([orc.seed_uniforms(seed, stream, pid) for pid in range(20_000)])
+    for k in range(5):
+        assert stats.kstest(U[:, k], "uniform").pvalue > 1e-3
+    C = np.corrcoef(U.T)
+    assert np.max(np.abs(C - np.eye(5))) < 4.0 / math.sqrt(len(U))
+
+
 # ------------------------------------------------------------------ Gamma
 def _mean_speed_quadrature(S):
     """<|v|> (units of c) of a drifting Maxwellian with mean speed ratio S, by 2-D quadrature."""
