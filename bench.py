@@ -50,7 +50,7 @@ FLOPS_PER_HIT = 60           # re-emission, momentum difference, torque, quantis
 # source it was taken on (keyed by the SHA-256 of kernels.cu).
 # Mean over the four bench groups of dram__bytes_read.sum + dram__bytes_write.sum
 # for one full-size launch (9.6e8 particles).
-TRACE_TRAFFIC = {"6d3ab4cfc245647606ab9f0c79811c90de42fa23a614071cfda80f1a63c004c1": 270_522_112}
+TRACE_TRAFFIC = {"2a2f972ae7ba157c4104e2fb96e6fd615f3b106cdfae6788e5b50e5ab78ae1ba": 295_899_456}
 
 
 def kernel_source_hash() -> str:
@@ -202,6 +202,40 @@ def cpu_baseline_and_cd_error(results_by_group, budget_s=12.0):
             "sample": "; ".join(sample_desc) + f"; plate {rates['plate']:.4g}/s, cylinder {rates['cylinder']:.4g}/s,"
                       " combined for equal particle counts"}
     return base, cd
+
+
+def other_configs_vs_oracle(T, ctx):
+    """C_D of the sphere (FP64, 1e5 particles) and of the concave satellite (FP32,
+    the first 1e5 particle ids) against the oracle on the same particles, with the
+    oracle's rate on them (host cores)."""
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    out = {}
+    c1 = W.icosphere_case(N=100_000)
+    c3 = W.satellite_case(N=100_000)
+    for name, case, prec in (("C1_icosphere_fp64_1e5", c1, T.TPMC_FP64), ("C3_satellite_fp32_1e5", c3, T.TPMC_FP32)):
+        mesh = T.tpmc_mesh_load(ctx, case["xyz"], case["tri"])
+        try:
+            g = T.tpmc_trace(ctx, mesh, T.make_params(**case["params"], precision=prec), case["N"])
+        finally:
+            T.tpmc_mesh_unload(ctx, mesh)
+        om = oracle.Mesh(case["xyz"], case["tri"])
+        t0 = time.perf_counter()
+        o, _, _ = oracle.trace(om, oracle.make_params(**case["params"], threads=threads), case["N"])
+        t_orc = time.perf_counter() - t0
+        row = {"gpu_CD": g["CD"], "oracle_CD": o["CD"], "CD_sigma": o["CD_sigma"],
+               "rel_diff": abs(g["CD"] - o["CD"]) / abs(o["CD"]),
+               "torque_rel_diff": float(np.linalg.norm(np.asarray(g["torque"]) - o["torque"]) /
+                                        max(np.linalg.norm(o["torque"]), 1e-300)),
+               "gpu_ms": g["ms"], "oracle_particles_per_s": case["N"] / t_orc, "oracle_cores": threads}
+        if name.startswith("C1"):
+            Vhat = np.asarray(case["params"]["dir"])
+            F = oracle.panel_sum(case["xyz"], case["tri"], Vhat, 7.5, 1.0, math.sqrt(0.3))
+            row["exact_faceted_CD"] = float(F @ Vhat / (0.5 * 7.5 ** 2 * math.pi))
+        out[name] = row
+    return out
 
 
 def run_reference(args):
@@ -621,9 +655,10 @@ def run_ours(args):
         extras["serving"] = measure_serving(T, ctx, rate=100.0)
         extras["serving_high_load"] = measure_serving(T, ctx, rate=200.0)
     if rank == 0:
-        cpu_base, cd_err = (None, None)
+        cpu_base, cd_err, cd_other = (None, None, None)
         if not args.no_cpu_baseline:
             cpu_base, cd_err = cpu_baseline_and_cd_error(results_by_group)
+            cd_other = other_configs_vs_oracle(T, ctx)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
@@ -643,7 +678,7 @@ def run_ours(args):
                          "work_per_step": work},
             "clocks": clocks,
             "cpu_baseline": cpu_base,
-            "cd_error": cd_err,
+            "cd_error": cd_err, "cd_error_other_configs": cd_other,
             "serve": {k: extras["serving"][k] for k in ("p50_ms", "p99_ms", "throughput_particles_per_s", "plain")}
             if "serving" in extras else None,
             "extras": extras,

@@ -564,6 +564,60 @@ def test_serving_results_equal_alone_and_in_the_mix(T, ctx):
             T.tpmc_mesh_unload(ctx, i)
 
 
+# ---------------------------------------------------------------- edge cases
+def test_particle_ids_beyond_2_to_32(T, orc, ctx):
+    """N = 2^32 + 2^22 on the plate: 64-bit particle ids in the Philox counter and
+    the work counters, and the fixed-point bound at that N; C_D matches the exact
+    plate drag, and the last particles' ids are traced like the oracle's."""
+    xyz, tri, cases = W.sweep_cases("plate", N_each=1, n_alpha=32)
+    c = cases[len(cases) - 10]
+    N = (1 << 32) + (1 << 22)
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    try:
+        r = T.tpmc_trace(ctx, mesh, T.make_params(**c["params"]), N)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    assert r["n_particles"] == N
+    Vhat = np.asarray(c["params"]["dir"])
+    F = orc.panel_sum(xyz, tri, Vhat, c["S"], c["eps"], math.sqrt(0.3), two_sided=True)
+    ref = F @ Vhat / (0.5 * c["S"] ** 2 * c["params"]["A_ref"])
+    assert cd_close(r["CD"], ref, r["CD_sigma"])
+    assert r["CD_sigma"] / r["CD"] < 1e-4
+
+
+@pytest.mark.parametrize("S", [0.05, 49.5])
+def test_speed_ratio_extremes_on_the_sphere(T, orc, ctx, S):
+    """Near-rest and hyperthermal free streams (the ends of the accepted S range)."""
+    xyz, tri = M.icosphere(3)
+    Vhat = np.array([0.6, 0.0, -0.8])
+    params = dict(**W.base_state(S=S), dir=tuple(Vhat), eps_diffuse=1.0, A_ref=math.pi, r_cv=1.2, seed=31,
+                  max_bounces=8)
+    res, rec, ores, orec = _run_pair(T, orc, ctx, xyz, tri, params, 40_009, T.TPMC_FP32)
+    _assert_paths(rec, orec)
+    np.testing.assert_allclose(rec["vel"], orec["vel"], rtol=2e-5, atol=2e-4)
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    try:
+        r = T.tpmc_trace(ctx, mesh, T.make_params(**params), 20_000_000)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    F = orc.panel_sum(xyz, tri, Vhat, S, 1.0, math.sqrt(0.3))
+    ref = F @ Vhat / (0.5 * S * S * math.pi)
+    assert cd_close(r["CD"], ref, r["CD_sigma"])
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_flow_along_the_stream_axis(T, orc, ctx, sign):
+    """Eq. 15's degenerate rotations (beta = 0 and pi) on both paths."""
+    xyz, tri = M.cylinder()
+    params = dict(**W.base_state(S=5.0), dir=(0.0, 0.0, sign), eps_diffuse=1.0, A_ref=2.0, r_cv=1.2, seed=8,
+                  max_bounces=8)
+    for prec in (T.TPMC_FP32, T.TPMC_FP64):
+        res, rec, ores, orec = _run_pair(T, orc, ctx, xyz, tri, params, 20_011, prec)
+        _assert_paths(rec, orec)
+        np.testing.assert_allclose(rec["pos"], orec["pos"], rtol=0, atol=2e-5)
+        assert cd_close(res["CD"], ores["CD"], ores["CD_sigma"])
+
+
 # ------------------------------------------- full size of the benchmark sweep
 @pytest.mark.parametrize("shape", ["plate", "cylinder"])
 def test_full_size_case_sampled_against_oracle(T, orc, ctx, shape):
