@@ -91,11 +91,12 @@ template <> struct QC<float> {
   float S, cw, r_cv, sqrtpi_4S, K1, Dinv, scale;
   float Rm[9], vhat[3], center[3], ref[3];
   __device__ __forceinline__ void load(const QueryDev& q) {
-    S = q.fS; cw = q.fcw; r_cv = q.fr_cv; sqrtpi_4S = q.fsqrtpi_4S; K1 = q.fK1; Dinv = q.fD_inv; scale = q.fscale;
+    S = q.fc[kFcS]; cw = q.fc[kFcCw]; r_cv = q.fc[kFcRcv]; sqrtpi_4S = q.fc[kFcSqrtpi4S];
+    K1 = q.fc[kFcK1]; Dinv = q.fc[kFcDinv]; scale = q.fc[kFcScale];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Rm[i] = q.fR[i];
+    for (int i = 0; i < 9; ++i) Rm[i] = q.fc[kFcR + i];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) { vhat[i] = q.fvhat[i]; center[i] = q.fcenter[i]; ref[i] = q.fref[i]; }
+    for (int i = 0; i < 3; ++i) { vhat[i] = q.fc[kFcVhat + i]; center[i] = q.fc[kFcCenter + i]; ref[i] = q.fc[kFcRef + i]; }
   }
 };
 template <> struct QC<double> {
@@ -135,19 +136,45 @@ __device__ __forceinline__ float z_table_start(const float* tab, int n, float z,
   return (1.0f - w) * __ldg(&tab[j]) + w * __ldg(&tab[j + 1]);
 }
 
-// x = H^-1(u).  Float: start from the query's table at z = Phi^-1(u) (error
-// ~1e-4), then one Newton step (error ~1e-7 over all tails, S >= 0.5): a
-// fixed step count keeps the warp converged.  Double: the same start, then a
+// Float latitude solve near a pole, in w = 1 - x (up) or w = 1 + x (down).
+// The probability within w of the pole is the integral of h over that end
+// interval; with g = D h, g' = sqrt(pi) S erfc(-S t) and g'' = 2 S^2 e^{-S^2 t^2},
+// it is the cubic c0 w + c1 w^2 + c2 w^3 (Taylor, next term below 3e-7
+// relative for w < 0.002), coefficients per query from the FP64 set-up.
+// Newton from w = q / c0, one step: w, and cos(phi) = sqrt(w (2 - w)), to
+// ~1e-7 relative, which x itself cannot carry in float this close to +-1.
+__device__ __noinline__ float latitude_pole(float q, float c0, float c1, float c2, bool up, float* cphi) {
+  float w = q / c0;
+  const float f = ((c2 * w + c1) * w + c0) * w - q;
+  const float d = (3.0f * c2 * w + 2.0f * c1) * w + c0;
+  w = fminf(fmaxf(w - f / d, 0.0f), 1.0f);
+  *cphi = sqrtf(w * (2.0f - w));
+  return up ? 1.0f - w : w - 1.0f;
+}
+
+constexpr float kPoleW = 0.002f;  // pole solves within this distance of x = +-1
+
+// x = H^-1(u), and cphi = cos(phi) = sqrt(1 - x^2).  Float: start from the
+// query's table at z = Phi^-1(u) (error ~1e-4), then one Newton step (error
+// ~1e-7 over all tails): a fixed step count keeps the warp converged; within
+// kPoleW of a pole, the pole solve above.  Double: the same start, then a
 // safeguarded Newton loop (on log H in the lower tail) to double precision.
 template <typename R>
-__device__ R latitude_inverse(R u, const QueryDev& q, const QC<R>& c) {
+__device__ R latitude_inverse(R u, const QueryDev& q, const QC<R>& c, R* cphi) {
   const float z = normcdfinvf((float)u);
   R x = (R)z_table_start(q.htab, kHTable + 1, z, (float)kZLo, (float)((kZHi - kZLo) / kHTable));
   if constexpr (sizeof(R) == 4) {
     const R H = latitude_cdf<R>(x, c.S, c.sqrtpi_4S, c.K1, c.Dinv);
     const R h = latitude_pdf<R>(x, c.S, c.Dinv);
     if (h > (R)0) x -= (H - u) / h;
-    return fmin(fmax(x, (R)-1), (R)1);
+    x = fmin(fmax(x, (R)-1), (R)1);
+    *cphi = Fn<R>::sqrt(((R)1 - x) * ((R)1 + x));
+    // within kPoleW of a pole, the pole solve (rare; the common path stays branch-free)
+    if (x > 1.0f - kPoleW)
+      x = latitude_pole(1.0f - u, q.fc[kFcPole], q.fc[kFcPole + 1], q.fc[kFcPole + 2], true, cphi);
+    else if (x < kPoleW - 1.0f)
+      x = latitude_pole(u, q.fc[kFcPole + 3], q.fc[kFcPole + 4], q.fc[kFcPole + 5], false, cphi);
+    return x;
   } else {
     R lo = -1, hi = 1;
     const bool logmode = u < (R)0.0625;
@@ -171,7 +198,9 @@ __device__ R latitude_inverse(R u, const QueryDev& q, const QC<R>& c) {
       x += dx;
       if (!(x > lo && x < hi)) x = (R)0.5 * (lo + hi);
     }
-    return fmin(fmax(x, (R)-1), (R)1);
+    x = fmin(fmax(x, (R)-1), (R)1);
+    *cphi = Fn<R>::sqrt(((R)1 - x) * ((R)1 + x));
+    return x;
   }
 }
 
@@ -429,8 +458,8 @@ __device__ __forceinline__ void seed_particle(const QueryDev& q, const QC<R>& c,
     seed_box<R>(q, c, vn_table, pid, w0, w_a, pos, vel);
     return;
   }
-  const R x = latitude_inverse<R>(uniform<R>(w0.x), q, c);
-  const R cphi = Fn<R>::sqrt(((R)1 - x) * ((R)1 + x));
+  R cphi;
+  const R x = latitude_inverse<R>(uniform<R>(w0.x), q, c, &cphi);
   R st, ct;
   Fn<R>::sincospi((R)2 * uniform<R>(w0.y), &st, &ct);
   const R vn = normal_speed_inverse<R>(uniform<R>(w0.z), c.S * x, vn_table);
@@ -811,10 +840,10 @@ __device__ __forceinline__ uint32_t find_item(const ItemDev* items, uint32_t n_i
 // Per-query constants of the traced (not seeded) part, in the path's precision.
 template <typename R> struct HitConst;
 template <> struct HitConst<float> {
-  static __device__ __forceinline__ float cw(const QueryDev& q) { return q.fcw; }
-  static __device__ __forceinline__ float scale(const QueryDev& q) { return q.fscale; }
-  static __device__ __forceinline__ float ref(const QueryDev& q, int i) { return q.fref[i]; }
-  static __device__ __forceinline__ float vhat(const QueryDev& q, int i) { return q.fvhat[i]; }
+  static __device__ __forceinline__ float cw(const QueryDev& q) { return q.fc[kFcCw]; }
+  static __device__ __forceinline__ float scale(const QueryDev& q) { return q.fc[kFcScale]; }
+  static __device__ __forceinline__ float ref(const QueryDev& q, int i) { return q.fc[kFcRef + i]; }
+  static __device__ __forceinline__ float vhat(const QueryDev& q, int i) { return q.fc[kFcVhat + i]; }
 };
 template <> struct HitConst<double> {
   static __device__ __forceinline__ double cw(const QueryDev& q) { return q.cw; }
@@ -865,9 +894,11 @@ constexpr uint32_t kQueue = 64;     // queue slots per warp (two seeding batches
 // bounce) or finish their particle and take the next one from the queue.
 // MINB > 0: a register-capped instantiation for 128-thread blocks with at
 // least MINB resident blocks per SM (more warps to hide latency, at the cost
-// of spills inside the out-of-line seeding).
+// of spills inside the out-of-line seeding).  MINB = 0: 256-thread blocks,
+// two per SM in float (at most 128 registers), one in double.
 template <typename R, int MINB, bool CLL>
-__global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : 1) trace_kernel(TraceArgs a) {
+__global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeof(R) == 4 ? 2 : 1))
+    trace_kernel(TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t n_stage = min(a.smem_nodes, a.mesh.n_nodes);
   float4* s_nodes = reinterpret_cast<float4*>(smem);
@@ -1121,7 +1152,7 @@ __global__ void setup_kernel(QueryDev* qs, const QueryDev* base, const double* d
         Rm[3] = kx * ky * oc;      Rm[4] = cs + ky * ky * oc; Rm[5] = -kx * sn;
         Rm[6] = -ky * sn;          Rm[7] = kx * sn;           Rm[8] = cs;
       }
-      for (int i = 0; i < 9; ++i) { q.R[i] = Rm[i]; q.fR[i] = (float)Rm[i]; }
+      for (int i = 0; i < 9; ++i) { q.R[i] = Rm[i]; q.fc[kFcR + i] = (float)Rm[i]; }
       const double eS = exp(-S * S), erS = erf(S);
       q.Dnorm = eS + kSqrtPiD * (1.0 + 2.0 * S * S) * erS / (2.0 * S);
       q.K1 = kSqrtPiD / (4.0 * S) * (2.0 * S * S + 1.0) * erfc(S) - 0.5 * eS;
@@ -1161,17 +1192,27 @@ __global__ void setup_kernel(QueryDev* qs, const QueryDev* base, const double* d
       if (shift < 8) st = TPMC_EINVAL;
       q.shift = shift;
       q.quantum = ldexp(1.0, -shift);
-      q.fS = (float)S;
-      q.fcw = (float)q.cw;
-      q.fr_cv = (float)q.r_cv;
-      q.fsqrtpi_4S = (float)(kSqrtPiD / (4.0 * S));
-      q.fK1 = (float)q.K1;
-      q.fD_inv = (float)(1.0 / q.Dnorm);
-      q.fscale = (float)ldexp(1.0, shift);
+      q.fc[kFcS] = (float)S;
+      q.fc[kFcCw] = (float)q.cw;
+      q.fc[kFcRcv] = (float)q.r_cv;
+      q.fc[kFcSqrtpi4S] = (float)(kSqrtPiD / (4.0 * S));
+      q.fc[kFcK1] = (float)q.K1;
+      q.fc[kFcDinv] = (float)(1.0 / q.Dnorm);
+      // tail-mass cubics of the latitude law at the poles (see latitude_pole):
+      //   x -> +1: h(1) w - h'(1) w^2 / 2 + h''(1) w^3 / 6,  x -> -1: h(-1) w + h'(-1) w^2 / 2 + h''(-1) w^3 / 6,
+      //   h(1) = [e^{-S^2} + sqrt(pi) S erfc(-S)] / D,  h(-1) = e^{-S^2} [1 - sqrt(pi) S erfcx(S)] / D,
+      //   h'(+-1) = sqrt(pi) S erfc(-+S) / D,  h''(+-1) = 2 S^2 e^{-S^2} / D
+      q.fc[kFcPole + 0] = (float)((eS + kSqrtPiD * S * erfc(-S)) / q.Dnorm);
+      q.fc[kFcPole + 1] = (float)(-0.5 * kSqrtPiD * S * erfc(-S) / q.Dnorm);
+      q.fc[kFcPole + 2] = (float)(S * S * eS / (3.0 * q.Dnorm));
+      q.fc[kFcPole + 3] = (float)(eS * (1.0 - kSqrtPiD * S * erfcx(S)) / q.Dnorm);
+      q.fc[kFcPole + 4] = (float)(0.5 * kSqrtPiD * S * erfc(S) / q.Dnorm);
+      q.fc[kFcPole + 5] = (float)(S * S * eS / (3.0 * q.Dnorm));
+      q.fc[kFcScale] = (float)ldexp(1.0, shift);
       for (int i = 0; i < 3; ++i) {
-        q.fvhat[i] = (float)vh[i];
-        q.fcenter[i] = (float)q.center[i];
-        q.fref[i] = (float)q.ref[i];
+        q.fc[kFcVhat + i] = (float)vh[i];
+        q.fc[kFcCenter + i] = (float)q.center[i];
+        q.fc[kFcRef + i] = (float)q.ref[i];
       }
     }
     q.status = st;

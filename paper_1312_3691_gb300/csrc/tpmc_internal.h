@@ -48,6 +48,16 @@ struct MeshDev {
 };
 
 // ------------------------------------------------------------- query (device)
+// Layout of QueryDev::fc, the FP32 constants of a query.
+enum : int {
+  kFcS = 0, kFcCw = 1, kFcRcv = 2, kFcSqrtpi4S = 3,  // S, c_W / c_mp, CV radius, sqrt(pi) / (4 S)
+  kFcK1 = 4, kFcDinv = 5, kFcScale = 6,              // latitude K1, 1 / D, fixed-point scale
+  kFcR = 7,                                           // [9] Rodrigues matrix (Eq. 15), row major
+  kFcCenter = 16, kFcVhat = 19, kFcRef = 22,          // [3] each
+  kFcPole = 25,                                       // [6] latitude tail-mass cubics at x = +1, then -1
+  kFcCount = 32
+};
+
 // One query: inputs copied from tpmc_params, derived values written by the
 // FP64 set-up kernel (flux normalisation, rotation, start table).
 struct QueryDev {
@@ -70,8 +80,8 @@ struct QueryDev {
   double quantum;         // 2^-shift
   int32_t shift;          // fixed-point scale 2^shift
   int32_t status;         // tpmc_status of the set-up
-  float fS, fcw, fr_cv, fsqrtpi_4S, fK1, fD_inv, fscale;
-  float fR[9], fvhat[3], fcenter[3], fref[3];
+  // FP32 copies of the query constants (kFc* indices)
+  float fc[kFcCount];
   float htab[kHTable + 1];
   // box CV (cv_kind != sphere): face f = 2a + k is x_a = hi_a (k = 0) or lo_a
   // (k = 1) and owns particle ids [face_end[f-1], face_end[f]); s_f is its

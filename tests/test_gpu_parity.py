@@ -605,6 +605,31 @@ def test_speed_ratio_extremes_on_the_sphere(T, orc, ctx, S):
     assert cd_close(r["CD"], ref, r["CD_sigma"])
 
 
+@pytest.mark.parametrize("S", [0.05, 7.5])
+def test_seeded_positions_near_the_poles(T, orc, ctx, S):
+    """FP32 seeding within 0.002 of the CV's poles solves for 1 -+ sin(phi)
+    directly, so positions there match the oracle to 2e-6 m."""
+    xyz = np.array([[0.0, 0.0, 0.0], [0.01, 0.0, 0.0], [0.0, 0.01, 0.0]])
+    tri = np.array([[0, 1, 2]], dtype=np.uint32)
+    Vhat = np.array([0.3, -0.2, 0.93]) / np.linalg.norm([0.3, -0.2, 0.93])
+    params = dict(**W.base_state(S=S), dir=tuple(Vhat), eps_diffuse=1.0, A_ref=1.0, r_cv=1.2, seed=99,
+                  max_bounces=4)
+    N = 1_000_003
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    try:
+        _, rec = T.tpmc_trace_records(ctx, mesh, T.make_params(**params), N, K=2)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    _, _, orec = orc.trace(orc.Mesh(xyz, tri), orc.make_params(**params), N, records=True, K=2)
+    sin_phi = -(orec["pos"] @ Vhat) / 1.2  # +1 at the upstream pole
+    pole = np.abs(sin_phi) > 0.998
+    assert pole.sum() > 200
+    err = np.linalg.norm(rec["pos"] - orec["pos"], axis=1)
+    assert err[pole].max() < 2e-6, err[pole].max()
+    # away from the poles: 2e-5 m, and 6e-5 m below S = 0.35, where the float latitude CDF cancels O(1/S) terms
+    assert err[~pole].max() < (6e-5 if S < 0.35 else 2e-5), err[~pole].max()
+
+
 @pytest.mark.parametrize("sign", [1.0, -1.0])
 def test_flow_along_the_stream_axis(T, orc, ctx, sign):
     """Eq. 15's degenerate rotations (beta = 0 and pi) on both paths."""
