@@ -46,6 +46,8 @@ FLOPS_PER_NODE_VISIT = 50    # two child boxes: 6 FMA + 6 min/max + 6 min/max + 
 FLOPS_PER_TRI_TEST = 45      # watertight test: 9 sub, 6 FMA, 9 mul/sub, 5 det/T, signs, 1 div
 FLOPS_PER_PARTICLE = 300     # seeding: two inverse-CDF solves, Box-Muller, rotations
 FLOPS_PER_HIT = 60           # re-emission, momentum difference, torque, quantisation
+BYTES_PER_NODE_VISIT = 64    # one BVH node: both child boxes and child codes
+BYTES_PER_TRI_TEST = 48      # three float4 vertices
 # DRAM bytes per trace launch from an ncu capture, valid only for the kernel
 # source it was taken on (keyed by the SHA-256 of kernels.cu).
 # Mean over the four bench groups of dram__bytes_read.sum + dram__bytes_write.sum
@@ -644,6 +646,18 @@ def run_ours(args):
     flops_per_launch = flops_per_step / len(d_in)
     achieved = flops_per_launch / (launch_avg_ms / 1e3) / 1e12
     traffic = TRACE_TRAFFIC.get(kernel_source_hash())
+    # measured ceilings: particles/s <= min(FP32 rate / flops per particle, L2 rate / bytes per particle)
+    ceil = T.tpmc_measure_ceilings(ctx)
+    fpp = flops_per_step / particles_step
+    bpp = (BYTES_PER_NODE_VISIT * work["nodes"] + BYTES_PER_TRI_TEST * work["tris"]) / particles_step
+    bound_fp32 = ceil["fp32_tflops"] * 1e12 / fpp
+    bound_l2 = ceil["l2_read_gbs"] * 1e9 / bpp
+    rate_gpu = particles_step / (t_step / 1e3)
+    ceilings = {"fp32_tflops_measured": ceil["fp32_tflops"], "l2_read_gbs_measured": ceil["l2_read_gbs"],
+                "flops_per_particle": fpp, "l2_bytes_per_particle": bpp,
+                "particles_per_s_fp32_bound": bound_fp32, "particles_per_s_l2_bound": bound_l2,
+                "binding": "fp32" if bound_fp32 <= bound_l2 else "l2",
+                "frac": rate_gpu / min(bound_fp32, bound_l2)}
 
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -675,7 +689,7 @@ def run_ours(args):
                          "kernel": "trace_kernel<float>",
                          "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
                                        f"(FMA) x {sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
-                         "work_per_step": work},
+                         "work_per_step": work, "ceilings_measured": ceilings},
             "clocks": clocks,
             "cpu_baseline": cpu_base,
             "cd_error": cd_err, "cd_error_other_configs": cd_other,

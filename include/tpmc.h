@@ -288,6 +288,20 @@ tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* param
 tpmc_status tpmc_set_launch(tpmc_ctx* ctx, const tpmc_launch* cfg);
 tpmc_status tpmc_get_launch(tpmc_ctx* ctx, tpmc_mesh_id mesh, uint32_t precision, tpmc_launch* out);
 
+/* ---- measurement ---------------------------------------------------------- */
+
+/* Measures on the context's device the two ceilings of the trace kernel's
+ * roofline (the kernel works in FP32 on node and triangle data that stays in
+ * L1/L2):
+ *   *fp32_tflops  FP32 FMA rate of independent dependent-FMA chains on every
+ *                 SM, 2 flops per FMA, best of 5 launches;
+ *   *l2_read_gbs  read bandwidth of a 32 MiB buffer streamed 64 times from L2
+ *                 with loads that bypass L1, best of 5 launches.
+ * Runs on the context's stream and waits for it; takes about 50 ms; holds
+ * 33 MiB of the context's memory budget during the call.
+ * Errors: EINVAL (NULL argument), ENOMEM (budget), ECUDA. */
+tpmc_status tpmc_measure_ceilings(tpmc_ctx* ctx, double* fp32_tflops, double* l2_read_gbs);
+
 #ifdef __cplusplus
 }
 #endif

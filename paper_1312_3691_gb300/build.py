@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libtpmc.so")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["kernels.cu", "noalloc.cu"]
+CU_SOURCES = ["kernels.cu", "noalloc.cu", "ceilings.cu"]
 CPP_SOURCES = ["api.cpp", "bvh.cpp", "serve.cpp", "tune.cpp"]
 HEADERS = ["tpmc_internal.h", "runtime.h", os.path.join("..", "..", "include", "tpmc.h")]
 

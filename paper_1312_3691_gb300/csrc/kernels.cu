@@ -143,13 +143,14 @@ __device__ __forceinline__ float z_table_start(const float* tab, int n, float z,
 // relative for w < 0.002), coefficients per query from the FP64 set-up.
 // Newton from w = q / c0, one step: w, and cos(phi) = sqrt(w (2 - w)), to
 // ~1e-7 relative, which x itself cannot carry in float this close to +-1.
-__device__ __noinline__ float latitude_pole(float q, float c0, float c1, float c2, bool up, float* cphi) {
+// Returns (x, cos(phi)) by value: an out-of-line call that wrote through a
+// pointer would keep the caller's variable in local memory.
+__device__ __noinline__ float2 latitude_pole(float q, float c0, float c1, float c2, bool up) {
   float w = q / c0;
   const float f = ((c2 * w + c1) * w + c0) * w - q;
   const float d = (3.0f * c2 * w + 2.0f * c1) * w + c0;
   w = fminf(fmaxf(w - f / d, 0.0f), 1.0f);
-  *cphi = sqrtf(w * (2.0f - w));
-  return up ? 1.0f - w : w - 1.0f;
+  return make_float2(up ? 1.0f - w : w - 1.0f, sqrtf(w * (2.0f - w)));
 }
 
 constexpr float kPoleW = 0.002f;  // pole solves within this distance of x = +-1
@@ -170,10 +171,13 @@ __device__ R latitude_inverse(R u, const QueryDev& q, const QC<R>& c, R* cphi) {
     x = fmin(fmax(x, (R)-1), (R)1);
     *cphi = Fn<R>::sqrt(((R)1 - x) * ((R)1 + x));
     // within kPoleW of a pole, the pole solve (rare; the common path stays branch-free)
-    if (x > 1.0f - kPoleW)
-      x = latitude_pole(1.0f - u, q.fc[kFcPole], q.fc[kFcPole + 1], q.fc[kFcPole + 2], true, cphi);
-    else if (x < kPoleW - 1.0f)
-      x = latitude_pole(u, q.fc[kFcPole + 3], q.fc[kFcPole + 4], q.fc[kFcPole + 5], false, cphi);
+    if (x > 1.0f - kPoleW || x < kPoleW - 1.0f) {
+      const bool up = x > 0.0f;
+      const int k = up ? kFcPole : kFcPole + 3;
+      const float2 r = latitude_pole(up ? 1.0f - u : u, q.fc[k], q.fc[k + 1], q.fc[k + 2], up);
+      x = r.x;
+      *cphi = r.y;
+    }
     return x;
   } else {
     R lo = -1, hi = 1;

@@ -109,6 +109,7 @@ SIGNATURES = {
     "tpmc_tune": [_P, ctypes.c_uint32, ctypes.POINTER(tpmc_params), ctypes.c_uint64, ctypes.POINTER(tpmc_launch)],
     "tpmc_set_launch": [_P, ctypes.POINTER(tpmc_launch)],
     "tpmc_get_launch": [_P, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(tpmc_launch)],
+    "tpmc_measure_ceilings": [_P, _PD, _PD],
 }
 
 _lib = None
@@ -321,3 +322,11 @@ def tpmc_get_launch(ctx, mesh: int, precision: int = TPMC_FP32) -> dict:
     b = tpmc_launch()
     _check(lib().tpmc_get_launch(ctx, int(mesh), int(precision), ctypes.byref(b)), "tpmc_get_launch", ctx)
     return {n: getattr(b, n) for n, _ in b._fields_}
+
+
+def tpmc_measure_ceilings(ctx) -> dict:
+    """FP32 FMA rate (TFLOP/s) and L2 read bandwidth (GB/s) measured on the context's device."""
+    f = ctypes.c_double()
+    b = ctypes.c_double()
+    _check(lib().tpmc_measure_ceilings(ctx, ctypes.byref(f), ctypes.byref(b)), "tpmc_measure_ceilings", ctx)
+    return {"fp32_tflops": f.value, "l2_read_gbs": b.value}

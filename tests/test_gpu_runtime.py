@@ -102,3 +102,17 @@ def test_panels_through_serving(T, ctx):
         np.testing.assert_array_equal(sd, ss)
     finally:
         T.tpmc_mesh_unload(ctx, mesh)
+
+
+def test_measured_ceilings_are_plausible_for_the_device(T, ctx):
+    """The FMA loop cannot beat the SM count x 128 FP32 lanes x 2 flops at the
+    maximum clock by more than the packed-FMA factor, and the L2 stream must be
+    faster than a DRAM copy yet below the L1 rate of all SMs."""
+    import torch
+
+    props = torch.cuda.get_device_properties(0)
+    c = T.tpmc_measure_ceilings(ctx)
+    lanes_peak = props.multi_processor_count * 128 * 2 * 2.2e9 / 1e12
+    assert 0.2 * lanes_peak < c["fp32_tflops"] < 2.05 * lanes_peak, (c, lanes_peak)
+    assert 2_000.0 < c["l2_read_gbs"] < props.multi_processor_count * 128 * 2.2, c
+    assert T.lib().tpmc_measure_ceilings(ctx, None, None) == T.TPMC_EINVAL
