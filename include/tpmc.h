@@ -240,7 +240,7 @@ tpmc_status tpmc_trace_records(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_para
  * speed ratio, in one persistent launch.  h_dirs: host [K][3]; h_S: host [K]
  * speed ratios (V = S c_mp); item k uses stream_id = base->stream_id + k.
  * Per-panel loads are not kept.  Results in h_out[K].
- * Errors as tpmc_trace; EINVAL for K = 0. */
+ * Errors as tpmc_trace; EINVAL for K = 0 or K > 2^24. */
 tpmc_status tpmc_sweep(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* base, const double* h_dirs,
                        const double* h_S, uint32_t K, uint64_t N_each, tpmc_result* h_out);
 

@@ -566,7 +566,7 @@ static tpmc_status sweep_common(Ctx* c, tpmc_mesh_id mesh, const tpmc_params* ba
                                 const double* d_S, uint32_t K, uint64_t N_each, tpmc_result* d_out) {
   tpmc_status st = validate_params(base);
   if (st != TPMC_OK) return st;
-  if (K == 0) return fail(TPMC_EINVAL, "K must be >= 1");
+  if (K == 0 || K > kMaxLaunchQueries) return fail(TPMC_EINVAL, "K must be in [1, 2^24]");
   if (N_each == 0 || N_each > (1ull << 34)) return fail(TPMC_EINVAL, "N_each must be in [1, 2^34]");
   if ((uint64_t)K * N_each > (1ull << 50)) return fail(TPMC_EINVAL, "K * N_each too large");
   auto it = c->meshes.find(mesh);

@@ -858,12 +858,42 @@ template <> struct HitConst<double> {
 
 // A seeded particle waiting in its warp's queue (shared memory).
 template <typename R>
-struct Seeded {
+struct alignas(sizeof(R) == 4 ? 16 : 8) Seeded {
   R pos[3], vel[3];
-  uint64_t pid;
-  uint32_t q;
-  uint32_t pad;
+  uint64_t pq;  // particle id in bits 0-39, query slot above
 };
+static_assert(sizeof(Seeded<float>) == 32, "a float queue slot is two 16-byte vectors");
+
+// Float slots are written and read as two 16-byte vectors: eight lanes'
+// 16-byte accesses at a 32-byte stride take two shared-memory wavefronts,
+// where 4-byte fields at that stride would conflict eight ways.
+template <typename R>
+__device__ __forceinline__ void slot_store(Seeded<R>& e, const R pos[3], const R vel[3], uint64_t pq) {
+  if constexpr (sizeof(R) == 4) {
+    float4* v = reinterpret_cast<float4*>(&e);
+    v[0] = make_float4(pos[0], pos[1], pos[2], vel[0]);
+    v[1] = make_float4(vel[1], vel[2], __uint_as_float((uint32_t)pq), __uint_as_float((uint32_t)(pq >> 32)));
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { e.pos[i] = pos[i]; e.vel[i] = vel[i]; }
+    e.pq = pq;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ uint64_t slot_load(const Seeded<R>& e, R pos[3], R vel[3]) {
+  if constexpr (sizeof(R) == 4) {
+    const float4* v = reinterpret_cast<const float4*>(&e);
+    const float4 a = v[0], b = v[1];
+    pos[0] = a.x; pos[1] = a.y; pos[2] = a.z;
+    vel[0] = a.w; vel[1] = b.x; vel[2] = b.y;
+    return (uint64_t)__float_as_uint(b.z) | ((uint64_t)__float_as_uint(b.w) << 32);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { pos[i] = e.pos[i]; vel[i] = e.vel[i]; }
+    return e.pq;
+  }
+}
 
 // Seeds particle pid of query qi into a queue slot.  Kept out of line: the
 // seeding temporaries then do not stay live across the traversal loop.
@@ -874,10 +904,7 @@ __device__ __noinline__ void seed_into(const TraceArgs& a, uint32_t qi, uint64_t
   c.load(q);
   R pos[3], vel[3];
   seed_particle<R>(q, c, a.vn_table, pid, pos, vel);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) { e.pos[i] = pos[i]; e.vel[i] = vel[i]; }
-  e.pid = pid;
-  e.q = qi;
+  slot_store<R>(e, pos, vel, pid | ((uint64_t)qi << kSlotPidBits));
   if (a.rec.pos != nullptr) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -1043,16 +1070,16 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
       const uint32_t take = min(n_need, q_count);
       const uint32_t rank = __popc(need & lt_mask);
       if (((need >> lane) & 1u) && rank < take) {
-        const Seeded<R>& e = queue[(q_head + rank) & (kQueue - 1)];
-        pid = e.pid;
-        const int nq = (int)e.q;
+        R pos[3], vel[3];
+        const uint64_t pq = slot_load<R>(queue[(q_head + rank) & (kQueue - 1)], pos, vel);
+        pid = pq & ((1ull << kSlotPidBits) - 1);
+        const int nq = (int)(pq >> kSlotPidBits);
         if (nq != acc.q) {
           if (a.count_work) { work_flush(a.acc, acc.q, n_nodes, n_tris); n_nodes = n_tris = 0; }
           lane_flush(a.acc, acc);
           lane_reset(acc, nq);
         }
         qi = nq;
-        R pos[3] = {e.pos[0], e.pos[1], e.pos[2]}, vel[3] = {e.vel[0], e.vel[1], e.vel[2]};
         const R speed = Fn<R>::sqrt(vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
         make_ray<R>(ray, pos, vel, (sizeof(R) == 4 ? (R)1e-6 : (R)1e-9) / speed);
         trav_begin(tv);

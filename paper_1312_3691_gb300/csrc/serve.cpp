@@ -34,6 +34,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr uint32_t kSlots = 1024;
 constexpr size_t kMaxQueue = 1u << 16;
+static_assert(kMaxQueue <= kMaxLaunchQueries, "a step's query slots must fit the queue word");
 constexpr uint64_t kStepParticles = 1ull << 25;  // particle budget of one step
 constexpr uint64_t kSmallQuery = kStepParticles / 4;  // work left below which a query goes first
 constexpr int kInFlight = 2;                     // steps enqueued ahead of the host

@@ -22,6 +22,10 @@ constexpr double kZLo = -5.5, kZHi = 5.5;
 // (kVnNS rows, s in [-8, 16]) and z_j = kZLo + j kVnStep (kVnNZ columns); 69 KB.
 constexpr double kVnSLo = -8.0, kVnStep = 0.125;
 constexpr int kVnNS = 193, kVnNZ = 89;
+// A queued particle keeps its id and query slot in one 64-bit word: ids
+// below 2^40 (N <= 2^34) and at most 2^24 query slots per launch.
+constexpr int kSlotPidBits = 40;
+constexpr uint32_t kMaxLaunchQueries = 1u << 24;
 constexpr int kMaxStack = 64;    // BVH traversal stack (the builder keeps depth below)
 constexpr int kMaxRecordK = 64;  // hits recorded per particle in verification runs
 

@@ -116,3 +116,23 @@ def test_measured_ceilings_are_plausible_for_the_device(T, ctx):
     assert 0.2 * lanes_peak < c["fp32_tflops"] < 2.05 * lanes_peak, (c, lanes_peak)
     assert 2_000.0 < c["l2_read_gbs"] < props.multi_processor_count * 128 * 2.2, c
     assert T.lib().tpmc_measure_ceilings(ctx, None, None) == T.TPMC_EINVAL
+
+
+def test_sweep_rejects_more_items_than_a_queue_slot_can_name(T, ctx):
+    """A queued particle names its query in 24 bits, so a sweep holds at most
+    2^24 items; one more is rejected before any work is enqueued."""
+    import ctypes
+
+    import torch
+
+    xyz, tri = M.plate(1.0)
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    try:
+        p = T.make_params(**W.base_state(S=5.0), dir=(0.0, 0.0, 1.0), eps_diffuse=1.0, A_ref=1.0)
+        out = torch.zeros(T.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+        st = T.lib().tpmc_sweep_device(ctx, mesh, ctypes.byref(p), None, None, (1 << 24) + 1, 1,
+                                       ctypes.c_void_p(out.data_ptr()))
+        assert st == T.TPMC_EINVAL
+        assert "2^24" in T.lib().tpmc_last_error(ctx).decode()
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
