@@ -49,15 +49,19 @@ FLOPS_PER_HIT = 60           # re-emission, momentum difference, torque, quantis
 BYTES_PER_NODE_VISIT = 64    # one BVH node: both child boxes and child codes
 BYTES_PER_TRI_TEST = 48      # three float4 vertices
 # DRAM bytes per trace launch from an ncu capture, valid only for the kernel
-# source it was taken on (keyed by the SHA-256 of kernels.cu).
+# source and the BVH builder it was taken with (keyed by the SHA-256 of
+# kernels.cu followed by bvh.cpp).
 # Mean over the four bench groups of dram__bytes_read.sum + dram__bytes_write.sum
 # for one full-size launch (9.6e8 particles).
-TRACE_TRAFFIC = {"998cc2b91bb74675fd288781407e73c1e662fcd5df69d4dd996d8152b9945dec": 303_394_112}
+TRACE_TRAFFIC = {"4541b224b0db07b23715e77821e22dfe7dbf5cbcda5cbda516682aac30cad4b2": 284_617_664}
 
 
 def kernel_source_hash() -> str:
-    with open(os.path.join(ROOT, "paper_1312_3691_gb300", "csrc", "kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    h = hashlib.sha256()
+    for name in ("kernels.cu", "bvh.cpp"):
+        with open(os.path.join(ROOT, "paper_1312_3691_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def rank_stream_base(rank: int, group: int) -> int:

@@ -165,6 +165,9 @@ typedef struct {
   uint32_t leaf_max;            /* largest leaf                                          */
   double bound_center[3], bound_radius;
   uint64_t device_bytes;
+  uint32_t n_refs;              /* triangle references in the leaves: spatial splits    */
+                                /* put parts of some triangles in several leaves         */
+  uint32_t pad_;
 } tpmc_mesh_stats;
 
 /* Launch schedule of the trace kernel (chosen by tpmc_tune or set by hand). */
@@ -201,8 +204,9 @@ tpmc_status tpmc_set_counters(tpmc_ctx* ctx, int enable);
 /* ---- geometry (§II.A: "satellite surfaces are represented by a triangulation") */
 
 /* Copies the mesh (xyz: host [n_vert][3] m; tri: host [n_tri][3] vertex
- * indices), builds its bounding-volume hierarchy on the host and keeps both on
- * the device.  Triangles are two-sided; the winding fixes the sign of the
+ * indices), builds its bounding-volume hierarchy on the host (surface-area
+ * heuristic with spatial splits: at most 1.5 references per triangle) and
+ * keeps both on the device.  Triangles are two-sided; the winding fixes the sign of the
  * geometric normal used for panel pressure.  Zero-area triangles are kept in
  * the numbering but never hit (counted in tpmc_mesh_stats.n_skipped).
  * Errors: EINVAL (n_vert = 0 with n_tri > 0, index out of range, non-finite

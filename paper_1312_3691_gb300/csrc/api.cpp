@@ -421,6 +421,7 @@ tpmc_status tpmc_mesh_info(tpmc_ctx* ctx, tpmc_mesh_id mesh, tpmc_mesh_stats* ou
   for (int i = 0; i < 3; ++i) out->bound_center[i] = m.center[i];
   out->bound_radius = m.radius;
   out->device_bytes = m.bytes;
+  out->n_refs = m.dev.n_tri_leaf;
   return TPMC_OK;
 }
 

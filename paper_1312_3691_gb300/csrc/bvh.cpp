@@ -2,12 +2,22 @@
 //
 // The paper represents the spacecraft by a triangulation and relies on
 // "well-known ray-tracing methods" for the closest intersection (§II.A); it
-// does not name a structure.  This builder makes a binary BVH by binned
-// surface-area heuristic (16 bins per axis), then lays it out for the GPU:
-// each node carries both children's boxes (one 64-byte fetch decides both),
-// nodes are numbered breadth first so that the top k nodes form a block that
-// the trace kernel stages in shared memory, and triangles are stored in leaf
-// order (48 bytes each in float, 96 in double).
+// does not name a structure.  This builder makes a binary BVH by the surface
+// area heuristic with spatial splits (Stich, Friedrich & Dietrich, "Spatial
+// splits in bounding volume hierarchies", HPG 2009): besides binned object
+// splits it considers planes that cut triangles, so that a triangle may be
+// referenced by several leaves, each with the box of its part on that side.
+// Long thin triangles that meet at a point (the fans that close a cylinder or
+// a dish) otherwise give boxes that all overlap there.  Then it lays the tree
+// out for the GPU: each node carries both children's boxes (one 64-byte fetch
+// decides both), nodes are numbered breadth first so that the top k nodes
+// form a block that the trace kernel stages in shared memory, and triangle
+// references are stored in leaf order (48 bytes each in float, 96 in double).
+//
+// A closest hit stays exact: the parts of a triangle cover it, every part's
+// box contains its part, so the ray meets the box of the part that holds the
+// hit point no later than the hit, and ties between references of one
+// triangle compare equal.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -47,19 +57,107 @@ struct Box {
 struct Prim {
   Box box;
   double c[3];
+  const double* v[3];  // vertices
   uint32_t id;
 };
+
+// A reference to prims[p] restricted to `box` (a part of its bounding box).
+struct Ref {
+  Box box;
+  uint32_t p;
+};
+
+Box intersect(const Box& a, const Box& b) {
+  Box r;
+  for (int k = 0; k < 3; ++k) {
+    r.lo[k] = std::max(a.lo[k], b.lo[k]);
+    r.hi[k] = std::min(a.hi[k], b.hi[k]);
+  }
+  for (int k = 0; k < 3; ++k)
+    if (!(r.lo[k] <= r.hi[k])) return Box();
+  return r;
+}
+
+// Splits the part of triangle `t` inside `box` by the plane x_axis = plane:
+// the boxes of the polygon's vertices and edge crossings on each side,
+// clipped to `box`.  Either side may come back empty.
+void split_ref(const Prim& t, const Box& box, int axis, double plane, Box& left, Box& right) {
+  left = Box();
+  right = Box();
+  for (int i = 0; i < 3; ++i) {
+    const double* a = t.v[i];
+    const double* b = t.v[(i + 1) % 3];
+    if (a[axis] <= plane) left.grow(a);
+    if (a[axis] >= plane) right.grow(a);
+    if ((a[axis] < plane && b[axis] > plane) || (a[axis] > plane && b[axis] < plane)) {
+      const double s = (plane - a[axis]) / (b[axis] - a[axis]);
+      double x[3];
+      for (int k = 0; k < 3; ++k) x[k] = a[k] + s * (b[k] - a[k]);
+      x[axis] = plane;
+      left.grow(x);
+      right.grow(x);
+    }
+  }
+  if (!left.empty()) left.hi[axis] = std::min(left.hi[axis], plane);
+  if (!right.empty()) right.lo[axis] = std::max(right.lo[axis], plane);
+  left = intersect(left, box);
+  right = intersect(right, box);
+}
+
+// Grows bins[b], b0 <= b <= b1, by the box of the part of triangle `t` inside
+// `box` that lies in slab b, [lo + b w, lo + (b + 1) w] along `axis` (the
+// first and last slab open outwards): the box of the triangle's vertices and
+// of its edges' crossings with the planes between the slabs.  A vertex on a
+// plane counts on both sides of it.
+void add_parts(const Prim& t, const Box& box, int axis, double lo, double w, int b0, int b1, Box* bins) {
+  Box part[32];
+  for (int i = 0; i < 3; ++i) {
+    const double* p = t.v[i];
+    const double* q = t.v[(i + 1) % 3];
+    const int bp = std::min(std::max((int)((p[axis] - lo) / w), b0), b1);
+    part[bp - b0].grow(p);
+    const double pa = p[axis], qa = q[axis];
+    if (pa == qa) continue;
+    const double e_lo = std::min(pa, qa), e_hi = std::max(pa, qa);
+    for (int b = b0; b < b1; ++b) {
+      const double x = lo + (b + 1) * w;
+      if (x < e_lo || x > e_hi) continue;
+      const double s = (x - pa) / (qa - pa);
+      double c[3];
+      for (int k = 0; k < 3; ++k) c[k] = p[k] + s * (q[k] - p[k]);
+      c[axis] = x;
+      part[b - b0].grow(c);
+      part[b + 1 - b0].grow(c);
+    }
+  }
+  for (int b = b0; b <= b1; ++b) {
+    Box& pb = part[b - b0];
+    if (pb.empty()) continue;
+    if (b > b0) pb.lo[axis] = std::max(pb.lo[axis], lo + b * w);
+    if (b < b1) pb.hi[axis] = std::min(pb.hi[axis], lo + (b + 1) * w);
+    bins[b].grow(intersect(pb, box));
+  }
+}
 
 struct BNode {       // binary build node
   Box box;
   int32_t left = -1, right = -1;  // children (build indices) for inner nodes
-  uint32_t first = 0, count = 0;  // leaf range in prims
+  uint32_t first = 0, count = 0;  // leaf range in the leaf-order reference list
   uint32_t depth = 0;
 };
 
-constexpr int kBins = 16;
+constexpr int kBins = 16;           // object-split bins per axis
+constexpr int kSpatialBins = 8;     // spatial-split bins per axis
+static_assert(kSpatialBins <= 32, "add_parts keeps at most 32 parts");
 constexpr double kCostNode = 1.0;
 constexpr double kCostTri = 1.2;
+// Spatial splits are tried where the best object split's children overlap by
+// more than this share of the root's surface area.  A smaller share spends the
+// reference budget near the fan centres at the top of the tree; on the
+// 4,096-triangle cylinder 1e-3 halves the triangle tests per particle, where
+// 1e-5 removes a quarter.
+constexpr double kSpatialAlpha = 1e-3;
+constexpr double kRefBudget = 0.5;      // at most this many extra references per triangle, in total
 constexpr uint32_t kMaxDepth = kMaxStack - 20;  // SAH below this depth, median splits after
 
 }  // namespace
@@ -114,101 +212,191 @@ bool build_bvh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t
     Prim p;
     p.box.grow(a); p.box.grow(b); p.box.grow(c);
     for (int k = 0; k < 3; ++k) p.c[k] = (a[k] + b[k] + c[k]) / 3.0;
+    p.v[0] = a; p.v[1] = b; p.v[2] = c;
     p.id = i;
     prims.push_back(p);
   }
 
-  // ---- binned SAH build (iterative) ----
+  // ---- SAH build with spatial splits (iterative, depth first) ----
   std::vector<BNode> bn;
-  bn.reserve(2 * prims.size() / std::max(1u, max_leaf / 2) + 4);
-  std::vector<int32_t> todo;
+  std::vector<uint32_t> leaf_refs;  // prims index of each reference, in leaf order
+  const size_t max_refs =
+      std::min<size_t>((size_t)(prims.size() * (1.0 + kRefBudget)) + 1, (size_t)(1u << 24) - 1);
+  size_t n_refs = prims.size();
+  struct Task {
+    int32_t node;
+    std::vector<Ref> refs;
+  };
+  std::vector<Task> todo;
+  double root_area = 0.0;
   if (!prims.empty()) {
+    Task t;
+    t.node = 0;
+    t.refs.resize(prims.size());
     BNode root;
-    root.first = 0; root.count = (uint32_t)prims.size();
-    for (const Prim& p : prims) root.box.grow(p.box);
+    for (uint32_t k = 0; k < prims.size(); ++k) {
+      t.refs[k].box = prims[k].box;
+      t.refs[k].p = k;
+      root.box.grow(prims[k].box);
+    }
+    root_area = root.box.area();
     bn.push_back(root);
-    todo.push_back(0);
+    todo.push_back(std::move(t));
   }
-  std::vector<Prim> tmp;
   while (!todo.empty()) {
-    const int32_t ni = todo.back();
+    Task task = std::move(todo.back());
     todo.pop_back();
-    BNode nd = bn[ni];
-    const uint32_t first = nd.first, count = nd.count;
-    // centroid bounds
+    std::vector<Ref>& refs = task.refs;
+    const int32_t ni = task.node;
+    const BNode nd = bn[ni];
+    const uint32_t count = (uint32_t)refs.size();
+    const double inv_area = 1.0 / std::max(nd.box.area(), 1e-300);
+
+    // object split: binned SAH over the centroids of the reference boxes
     Box cb;
-    for (uint32_t k = first; k < first + count; ++k) cb.grow(prims[k].c);
-    int best_axis = -1, best_bin = -1;
-    double best_cost = INFINITY;
+    for (const Ref& r : refs) {
+      double c[3];
+      for (int k = 0; k < 3; ++k) c[k] = 0.5 * (r.box.lo[k] + r.box.hi[k]);
+      cb.grow(c);
+    }
+    int obj_axis = -1, obj_bin = -1;
+    double obj_cost = INFINITY, obj_overlap = 0.0;
+    auto centroid_bin = [&](const Ref& r, int a) {
+      const double ext = cb.hi[a] - cb.lo[a];
+      int b = (int)((0.5 * (r.box.lo[a] + r.box.hi[a]) - cb.lo[a]) / ext * kBins);
+      return std::min(std::max(b, 0), kBins - 1);
+    };
     if (count > 1) {
       for (int a = 0; a < 3; ++a) {
-        const double ext = cb.hi[a] - cb.lo[a];
-        if (!(ext > 0.0)) continue;
+        if (!(cb.hi[a] - cb.lo[a] > 0.0)) continue;
         Box bins[kBins];
         uint32_t cnt[kBins] = {0};
-        for (uint32_t k = first; k < first + count; ++k) {
-          int b = (int)((prims[k].c[a] - cb.lo[a]) / ext * kBins);
-          b = std::min(std::max(b, 0), kBins - 1);
-          bins[b].grow(prims[k].box);
+        for (const Ref& r : refs) {
+          const int b = centroid_bin(r, a);
+          bins[b].grow(r.box);
           ++cnt[b];
         }
         Box lbox[kBins], rbox[kBins];
         uint32_t lcnt[kBins], rcnt[kBins];
-        Box acc; uint32_t c = 0;
+        Box acc;
+        uint32_t c = 0;
         for (int b = 0; b < kBins; ++b) { acc.grow(bins[b]); c += cnt[b]; lbox[b] = acc; lcnt[b] = c; }
-        acc = Box(); c = 0;
+        acc = Box();
+        c = 0;
         for (int b = kBins - 1; b >= 0; --b) { acc.grow(bins[b]); c += cnt[b]; rbox[b] = acc; rcnt[b] = c; }
         for (int b = 0; b + 1 < kBins; ++b) {
           if (lcnt[b] == 0 || rcnt[b + 1] == 0) continue;
-          const double cost = kCostNode + kCostTri * (lbox[b].area() * lcnt[b] + rbox[b + 1].area() * rcnt[b + 1]) /
-                                              std::max(nd.box.area(), 1e-300);
-          if (cost < best_cost) { best_cost = cost; best_axis = a; best_bin = b; }
+          const double cost =
+              kCostNode + kCostTri * (lbox[b].area() * lcnt[b] + rbox[b + 1].area() * rcnt[b + 1]) * inv_area;
+          if (cost < obj_cost) {
+            obj_cost = cost;
+            obj_axis = a;
+            obj_bin = b;
+            obj_overlap = intersect(lbox[b], rbox[b + 1]).area();
+          }
         }
       }
     }
+
+    // spatial split: planes at bin boundaries of the node box; a reference
+    // that spans several bins adds the box of its part to each of them
+    int sp_axis = -1, sp_bin = -1;
+    double sp_cost = INFINITY;
+    const bool try_spatial = count > 1 && nd.depth < kMaxDepth && n_refs + count <= max_refs &&
+                             obj_overlap > kSpatialAlpha * root_area;
+    if (try_spatial) {
+      for (int a = 0; a < 3; ++a) {
+        const double lo = nd.box.lo[a], ext = nd.box.hi[a] - nd.box.lo[a];
+        if (!(ext > 0.0)) continue;
+        const double w = ext / kSpatialBins;
+        auto bin_of = [&](double x) { return std::min(std::max((int)((x - lo) / w), 0), kSpatialBins - 1); };
+        Box bins[kSpatialBins];
+        uint32_t enter[kSpatialBins] = {0}, leave[kSpatialBins] = {0};
+        for (const Ref& r : refs) {
+          const int b0 = bin_of(r.box.lo[a]), b1 = bin_of(r.box.hi[a]);
+          ++enter[b0];
+          ++leave[b1];
+          if (b0 == b1) {
+            bins[b0].grow(r.box);
+          } else {
+            add_parts(prims[r.p], r.box, a, lo, w, b0, b1, bins);
+          }
+        }
+        Box rbox[kSpatialBins];
+        uint32_t rcnt[kSpatialBins];
+        Box acc;
+        uint32_t c = 0;
+        for (int b = kSpatialBins - 1; b >= 0; --b) { acc.grow(bins[b]); c += leave[b]; rbox[b] = acc; rcnt[b] = c; }
+        acc = Box();
+        c = 0;
+        for (int b = 0; b + 1 < kSpatialBins; ++b) {
+          acc.grow(bins[b]);
+          c += enter[b];
+          if (c == 0 || rcnt[b + 1] == 0 || (c == count && rcnt[b + 1] == count)) continue;
+          const double cost = kCostNode + kCostTri * (acc.area() * c + rbox[b + 1].area() * rcnt[b + 1]) * inv_area;
+          if (cost < sp_cost) { sp_cost = cost; sp_axis = a; sp_bin = b; }
+        }
+      }
+    }
+
     const double leaf_cost = kCostTri * count;
     const bool must_split = count > max_leaf;
+    const double best_cost = std::min(obj_cost, sp_cost);
     bool make_leaf = count <= 1 || nd.depth >= kMaxDepth || (!must_split && best_cost >= leaf_cost);
-    uint32_t mid = first;
-    if (!make_leaf) {
-      if (best_axis >= 0) {
-        const double ext = cb.hi[best_axis] - cb.lo[best_axis];
-        auto is_left = [&](const Prim& p) {
-          int b = (int)((p.c[best_axis] - cb.lo[best_axis]) / ext * kBins);
-          b = std::min(std::max(b, 0), kBins - 1);
-          return b <= best_bin;
-        };
-        mid = (uint32_t)(std::partition(prims.begin() + first, prims.begin() + first + count, is_left) -
-                         prims.begin());
-      }
-      if (mid == first || mid == first + count) {
-        // all centroids coincide (or no useful bin): split the range in half
-        mid = first + count / 2;
-      }
-      if (count > max_leaf && nd.depth >= kMaxDepth) make_leaf = true;
+    if (make_leaf && count <= 127) {
+      bn[ni].first = (uint32_t)leaf_refs.size();
+      bn[ni].count = count;
+      for (const Ref& r : refs) leaf_refs.push_back(r.p);
+      continue;
     }
-    if (make_leaf) {
-      if (count > 127) {
-        // depth limit reached with an oversized leaf: split by median regardless
-        mid = first + count / 2;
-      } else {
-        bn[ni].left = bn[ni].right = -1;
-        continue;
+    std::vector<Ref> lref, rref;
+    bool split_done = false;
+    if (!make_leaf && sp_cost < obj_cost) {
+      const int a = sp_axis;
+      const double lo = nd.box.lo[a], w = (nd.box.hi[a] - nd.box.lo[a]) / kSpatialBins;
+      const double plane = lo + (sp_bin + 1) * w;
+      auto bin_of = [&](double x) { return std::min(std::max((int)((x - lo) / w), 0), kSpatialBins - 1); };
+      for (const Ref& r : refs) {
+        const int b0 = bin_of(r.box.lo[a]), b1 = bin_of(r.box.hi[a]);
+        if (b1 <= sp_bin) {
+          lref.push_back(r);
+        } else if (b0 > sp_bin) {
+          rref.push_back(r);
+        } else {
+          Ref l = r, rr = r;
+          split_ref(prims[r.p], r.box, a, plane, l.box, rr.box);
+          if (!l.box.empty()) lref.push_back(l);
+          if (!rr.box.empty()) rref.push_back(rr);
+        }
+      }
+      split_done = !lref.empty() && !rref.empty() && (lref.size() < count || rref.size() < count);
+      if (split_done) n_refs += lref.size() + rref.size() - count;
+      else { lref.clear(); rref.clear(); }
+    }
+    if (!split_done) {
+      if (!make_leaf && obj_axis >= 0) {
+        for (const Ref& r : refs) (centroid_bin(r, obj_axis) <= obj_bin ? lref : rref).push_back(r);
+      }
+      if (lref.empty() || rref.empty()) {
+        // all centroids coincide, no useful bin, or an oversized leaf at the
+        // depth limit: split the list in half
+        lref.assign(refs.begin(), refs.begin() + count / 2);
+        rref.assign(refs.begin() + count / 2, refs.end());
       }
     }
+    std::vector<Ref>().swap(refs);
     BNode l, r;
-    l.first = first; l.count = mid - first; l.depth = nd.depth + 1;
-    r.first = mid; r.count = first + count - mid; r.depth = nd.depth + 1;
-    for (uint32_t k = l.first; k < l.first + l.count; ++k) l.box.grow(prims[k].box);
-    for (uint32_t k = r.first; k < r.first + r.count; ++k) r.box.grow(prims[k].box);
+    l.depth = r.depth = nd.depth + 1;
+    for (const Ref& x : lref) l.box.grow(x.box);
+    for (const Ref& x : rref) r.box.grow(x.box);
     const int32_t li = (int32_t)bn.size();
     bn.push_back(l);
     const int32_t ri = (int32_t)bn.size();
     bn.push_back(r);
     bn[ni].left = li;
     bn[ni].right = ri;
-    todo.push_back(ri);
-    todo.push_back(li);
+    todo.push_back(Task{ri, std::move(rref)});
+    todo.push_back(Task{li, std::move(lref)});
   }
 
   // ---- GPU layout: inner nodes in breadth-first order, leaves in place ----
@@ -234,11 +422,11 @@ bool build_bvh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t
   out->nodes = (float*)std::calloc(std::max<size_t>(n_nodes, 1) * 16, sizeof(float));
 
   // triangles in leaf order
-  out->n_leaf_tris = (uint32_t)prims.size();
-  out->tris = (float*)std::calloc(std::max<size_t>(prims.size(), 1) * 12, sizeof(float));
-  out->tris64 = (double*)std::calloc(std::max<size_t>(prims.size(), 1) * 12, sizeof(double));
-  for (size_t k = 0; k < prims.size(); ++k) {
-    const uint32_t i = prims[k].id;
+  out->n_leaf_tris = (uint32_t)leaf_refs.size();
+  out->tris = (float*)std::calloc(std::max<size_t>(leaf_refs.size(), 1) * 12, sizeof(float));
+  out->tris64 = (double*)std::calloc(std::max<size_t>(leaf_refs.size(), 1) * 12, sizeof(double));
+  for (size_t k = 0; k < leaf_refs.size(); ++k) {
+    const uint32_t i = prims[leaf_refs[k]].id;
     for (int v = 0; v < 3; ++v) {
       const double* p = xyz + 3 * (uint64_t)tri[3 * i + v];
       for (int a = 0; a < 3; ++a) {

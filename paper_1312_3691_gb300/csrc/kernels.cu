@@ -601,6 +601,29 @@ __device__ __forceinline__ void slab(R lo, R hi, R inv, R oi, R& tn, R& tf) {
 // while other lanes are still searching.
 constexpr int kDone = (int)0x80000000;  // no valid leaf code: first + count would exceed 2^24
 
+// Traversal stack entry: a stacked child and its entry distance.  In float
+// the pair is one 8-byte local-memory access per push and per pop (two 4-byte
+// arrays took two).
+template <typename R> struct StackE;
+template <> struct __align__(8) StackE<float> { int node; float t; };
+template <> struct __align__(16) StackE<double> { double t; int node; int pad; };
+__device__ __forceinline__ void stack_put(StackE<float>* s, int i, int node, float t) {
+  *reinterpret_cast<int2*>(s + i) = make_int2(node, __float_as_int(t));
+}
+__device__ __forceinline__ void stack_put(StackE<double>* s, int i, int node, double t) {
+  s[i].t = t;
+  s[i].node = node;
+}
+__device__ __forceinline__ void stack_get(const StackE<float>* s, int i, int& node, float& t) {
+  const int2 v = *reinterpret_cast<const int2*>(s + i);
+  node = v.x;
+  t = __int_as_float(v.y);
+}
+__device__ __forceinline__ void stack_get(const StackE<double>* s, int i, int& node, double& t) {
+  node = s[i].node;
+  t = s[i].t;
+}
+
 template <typename R>
 struct Trav {
   R tbest;
@@ -621,10 +644,13 @@ __device__ __forceinline__ void trav_begin(Trav<R>& t) {
 
 // Next stacked candidate whose entry distance is still below the best hit.
 template <typename R>
-__device__ __forceinline__ int trav_pop(Trav<R>& t, const int* stack_node, const R* stack_t) {
+__device__ __forceinline__ int trav_pop(Trav<R>& t, const StackE<R>* stack) {
   while (t.sp > 0) {
     --t.sp;
-    if (stack_t[t.sp] <= t.tbest) return stack_node[t.sp];
+    int node;
+    R te;
+    stack_get(stack, t.sp, node, te);
+    if (te <= t.tbest) return node;
   }
   return kDone;
 }
@@ -633,7 +659,7 @@ __device__ __forceinline__ int trav_pop(Trav<R>& t, const int* stack_node, const
 // stack the farther one; the first leaf reached is postponed.
 template <typename R>
 __device__ __forceinline__ void trav_inner(const MeshDev& m, const float4* __restrict__ s_nodes, uint32_t n_stage,
-                                           const Ray<R>& r, Trav<R>& t, int* stack_node, R* stack_t, uint32_t& n_nodes,
+                                           const Ray<R>& r, Trav<R>& t, StackE<R>* stack, uint32_t& n_nodes,
                                            int* err) {
   ++n_nodes;
   float4 n0, n1, n2, n3;
@@ -665,8 +691,7 @@ __device__ __forceinline__ void trav_inner(const MeshDev& m, const float4* __res
       t.leaf = 0;
       return;
     }
-    stack_node[t.sp] = c1;
-    stack_t[t.sp] = tfar;
+    stack_put(stack, t.sp, c1, tfar);
     ++t.sp;
     t.cur = c0;
   } else if (h0) {
@@ -674,11 +699,11 @@ __device__ __forceinline__ void trav_inner(const MeshDev& m, const float4* __res
   } else if (h1) {
     t.cur = c1;
   } else {
-    t.cur = trav_pop(t, stack_node, stack_t);
+    t.cur = trav_pop(t, stack);
   }
   if (t.cur < 0 && t.cur != kDone && t.leaf == 0) {
     t.leaf = t.cur;
-    t.cur = trav_pop(t, stack_node, stack_t);
+    t.cur = trav_pop(t, stack);
   }
 }
 
@@ -686,7 +711,7 @@ __device__ __forceinline__ void trav_inner(const MeshDev& m, const float4* __res
 // the postponed one.  Returns true when the ray's traversal is finished.
 template <typename R>
 __device__ __forceinline__ bool trav_leaf(const MeshDev& m, const Ray<R>& r, uint32_t last, Trav<R>& t,
-                                          const int* stack_node, const R* stack_t, uint32_t& n_tris) {
+                                          const StackE<R>* stack, uint32_t& n_tris) {
   const uint32_t code = ~(uint32_t)t.leaf;
   const uint32_t first = code & 0xFFFFFFu, count = code >> 24;
   for (uint32_t k = first; k < first + count; ++k) {
@@ -699,7 +724,7 @@ __device__ __forceinline__ bool trav_leaf(const MeshDev& m, const Ray<R>& r, uin
   t.leaf = 0;
   if (t.cur < 0 && t.cur != kDone) {
     t.leaf = t.cur;
-    t.cur = trav_pop(t, stack_node, stack_t);
+    t.cur = trav_pop(t, stack);
   }
   return t.leaf == 0 && t.cur == kDone;
 }
@@ -962,8 +987,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
   Ray<R> ray;
   Trav<R> tv;
   trav_begin(tv);
-  int stack_node[kMaxStack];
-  R stack_t[kMaxStack];
+  StackE<R> stack[kMaxStack];
   uint32_t n_nodes = 0, n_tris = 0;
 
   for (;;) {
@@ -1105,10 +1129,10 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
     for (;;) {
       while (__any_sync(kFull, has && !tdone && tv.cur >= 0 && tv.leaf == 0)) {
         if (has && !tdone && tv.cur >= 0)
-          trav_inner<R>(a.mesh, s_nodes, n_stage, ray, tv, stack_node, stack_t, n_nodes, a.error);
+          trav_inner<R>(a.mesh, s_nodes, n_stage, ray, tv, stack, n_nodes, a.error);
       }
       if (has && !tdone) {
-        if (tv.leaf != 0) tdone = trav_leaf<R>(a.mesh, ray, last, tv, stack_node, stack_t, n_tris);
+        if (tv.leaf != 0) tdone = trav_leaf<R>(a.mesh, ray, last, tv, stack, n_tris);
         else if (tv.cur == kDone) tdone = true;
       }
       const unsigned fin = __ballot_sync(kFull, has && tdone);

@@ -643,6 +643,26 @@ def test_flow_along_the_stream_axis(T, orc, ctx, sign):
         assert cd_close(res["CD"], ores["CD"], ores["CD_sigma"])
 
 
+def test_spatial_splits_keep_the_closest_hit(T, orc, ctx):
+    """The cylinder's end caps are fans of 128 triangles that meet at the cap
+    centre, so the builder cuts some of them into parts held by different
+    leaves.  A near-parallel end-on stream (S = 40) lands on the whole cap,
+    centre included, and at a small tilt grazes the rim; every hit must still
+    be the oracle's brute-force closest hit."""
+    xyz, tri = M.cylinder()
+    mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+    info = T.tpmc_mesh_info(ctx, mesh)
+    T.tpmc_mesh_unload(ctx, mesh)
+    assert len(tri) < info["n_refs"] <= 1.5 * len(tri) + 1
+    for d in ((0.0, 0.0, -1.0), (0.05, -0.02, 1.0)):
+        params = dict(**W.base_state(S=40.0), dir=d, eps_diffuse=0.5, A_ref=math.pi * 0.25, r_cv=1.13,
+                      seed=31, max_bounces=8)
+        res, rec, ores, orec = _run_pair(T, orc, ctx, xyz, tri, params, 30_011, T.TPMC_FP32)
+        _assert_paths(rec, orec)
+        assert (rec["n_hits"] > 0).sum() > 4_000
+        assert cd_close(res["CD"], ores["CD"], ores["CD_sigma"])
+
+
 # ------------------------------------------- full size of the benchmark sweep
 @pytest.mark.parametrize("shape", ["plate", "cylinder"])
 def test_full_size_case_sampled_against_oracle(T, orc, ctx, shape):
