@@ -53,7 +53,7 @@ BYTES_PER_TRI_TEST = 48      # three float4 vertices
 # kernels.cu followed by bvh.cpp).
 # Mean over the four bench groups of dram__bytes_read.sum + dram__bytes_write.sum
 # for one full-size launch (9.6e8 particles).
-TRACE_TRAFFIC = {"4541b224b0db07b23715e77821e22dfe7dbf5cbcda5cbda516682aac30cad4b2": 284_617_664}
+TRACE_TRAFFIC = {"51bf14e32f0954e752e9b3167474bd768b12b02985a1eadfa3e5b931328a97bd": 114_790_144}
 
 
 def kernel_source_hash() -> str:

@@ -165,7 +165,10 @@ LaunchCfg Ctx::schedule(const MeshRec& m, uint32_t variant, uint64_t total) {
     cfg.chunk = 0;
   }
   cfg.smem_nodes = std::min<uint32_t>(cfg.smem_nodes, m.dev.n_nodes);
-  if (cfg.refill_at == 0 || cfg.refill_at > 32) cfg.refill_at = 16;
+  // A traversal round ends once this many lanes have finished their rays.
+  // Same-box sweeps after the spatial-split BVH: 24 is 6 % faster than 16 on
+  // the cylinder sweep, equal on the plate and the satellite; 32 is slower.
+  if (cfg.refill_at == 0 || cfg.refill_at > 32) cfg.refill_at = 24;
   const int maxb = trace_max_blocks_per_sm(variant, cfg, m.dev.n_nodes);
   if (cfg.blocks_per_sm == 0 || (int)cfg.blocks_per_sm > maxb) cfg.blocks_per_sm = std::max(1, maxb);
   if (cfg.chunk == 0) {

@@ -524,13 +524,29 @@ __device__ __forceinline__ double edge_fn(double a, double b, double c, double d
 template <typename R>
 struct Ray {
   R o[3], d[3], inv[3], oi[3];
-  R Sx, Sy, Sz;
-  uint32_t k;  // axis permutation: kx | ky << 2 | kz << 4
   R tlo;
-  __device__ __forceinline__ int kx() const { return k & 3; }
-  __device__ __forceinline__ int ky() const { return (k >> 2) & 3; }
-  __device__ __forceinline__ int kz() const { return (k >> 4) & 3; }
 };
+
+// Woop, Benthin & Wald (JCGT 2013): shear the ray onto +z of a permuted frame.
+template <typename R>
+struct Shear {
+  R Sx, Sy, Sz;
+  int kx, ky, kz;
+};
+
+template <typename R>
+__device__ __forceinline__ Shear<R> make_shear(const R d[3]) {
+  Shear<R> s;
+  const R ax = Fn<R>::fabs(d[0]), ay = Fn<R>::fabs(d[1]), az = Fn<R>::fabs(d[2]);
+  s.kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+  s.kx = s.kz == 2 ? 0 : s.kz + 1;
+  s.ky = s.kx == 2 ? 0 : s.kx + 1;
+  if (pick(d, s.kz) < (R)0) { const int t = s.kx; s.kx = s.ky; s.ky = t; }
+  s.Sz = (R)1 / pick(d, s.kz);
+  s.Sx = pick(d, s.kx) * s.Sz;
+  s.Sy = pick(d, s.ky) * s.Sz;
+  return s;
+}
 
 template <typename R>
 __device__ __forceinline__ void make_ray(Ray<R>& r, const R o[3], const R d[3], R tlo) {
@@ -542,31 +558,21 @@ __device__ __forceinline__ void make_ray(Ray<R>& r, const R o[3], const R d[3], 
     r.inv[i] = (R)1 / di;
     r.oi[i] = o[i] * r.inv[i];
   }
-  // Woop, Benthin & Wald (JCGT 2013): shear the ray onto +z of a permuted frame.
-  const R ax = Fn<R>::fabs(d[0]), ay = Fn<R>::fabs(d[1]), az = Fn<R>::fabs(d[2]);
-  int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
-  int kx = kz == 2 ? 0 : kz + 1;
-  int ky = kx == 2 ? 0 : kx + 1;
-  if (pick(d, kz) < (R)0) { const int t = kx; kx = ky; ky = t; }
-  r.k = (uint32_t)kx | ((uint32_t)ky << 2) | ((uint32_t)kz << 4);
-  r.Sz = (R)1 / pick(d, kz);
-  r.Sx = pick(d, kx) * r.Sz;
-  r.Sy = pick(d, ky) * r.Sz;
   r.tlo = tlo;
 }
 
 // Watertight ray/triangle test; updates (tbest, best) by nearest t, then lower index.
 template <typename R>
-__device__ __forceinline__ void test_triangle(const Ray<R>& r, const R V0[3], const R V1[3], const R V2[3],
+__device__ __forceinline__ void test_triangle(const Ray<R>& r, const Shear<R>& sh, const R V0[3], const R V1[3], const R V2[3],
                                               uint32_t id, R& tbest, uint32_t& best) {
   R A[3], B[3], C[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) { A[i] = V0[i] - r.o[i]; B[i] = V1[i] - r.o[i]; C[i] = V2[i] - r.o[i]; }
-  const int kx = r.kx(), ky = r.ky(), kz = r.kz();
+  const int kx = sh.kx, ky = sh.ky, kz = sh.kz;
   const R Akz = pick(A, kz), Bkz = pick(B, kz), Ckz = pick(C, kz);
-  const R Ax = pick(A, kx) - r.Sx * Akz, Ay = pick(A, ky) - r.Sy * Akz;
-  const R Bx = pick(B, kx) - r.Sx * Bkz, By = pick(B, ky) - r.Sy * Bkz;
-  const R Cx = pick(C, kx) - r.Sx * Ckz, Cy = pick(C, ky) - r.Sy * Ckz;
+  const R Ax = pick(A, kx) - sh.Sx * Akz, Ay = pick(A, ky) - sh.Sy * Akz;
+  const R Bx = pick(B, kx) - sh.Sx * Bkz, By = pick(B, ky) - sh.Sy * Bkz;
+  const R Cx = pick(C, kx) - sh.Sx * Ckz, Cy = pick(C, ky) - sh.Sy * Ckz;
   R U = edge_fn(Cx, By, Cy, Bx);
   R V = edge_fn(Ax, Cy, Ay, Cx);
   R W = edge_fn(Bx, Ay, By, Ax);
@@ -579,7 +585,7 @@ __device__ __forceinline__ void test_triangle(const Ray<R>& r, const R V0[3], co
   if ((U < (R)0 || V < (R)0 || W < (R)0) && (U > (R)0 || V > (R)0 || W > (R)0)) return;
   R det = U + V + W;
   if (det == (R)0) return;
-  R T = U * (r.Sz * Akz) + V * (r.Sz * Bkz) + W * (r.Sz * Ckz);
+  R T = U * (sh.Sz * Akz) + V * (sh.Sz * Bkz) + W * (sh.Sz * Ckz);
   if (det < (R)0) { det = -det; T = -T; }
   if (T <= r.tlo * det || T > tbest * det) return;
   const R t = T / det;
@@ -714,12 +720,13 @@ __device__ __forceinline__ bool trav_leaf(const MeshDev& m, const Ray<R>& r, uin
                                           const StackE<R>* stack, uint32_t& n_tris) {
   const uint32_t code = ~(uint32_t)t.leaf;
   const uint32_t first = code & 0xFFFFFFu, count = code >> 24;
+  const Shear<R> sh = make_shear<R>(r.d);
   for (uint32_t k = first; k < first + count; ++k) {
     R V0[3], V1[3], V2[3];
     const uint32_t id = TriLoad<R>::load(m, k, V0, V1, V2);
     if (id == last) continue;
     ++n_tris;
-    test_triangle<R>(r, V0, V1, V2, id, t.tbest, t.best);
+    test_triangle<R>(r, sh, V0, V1, V2, id, t.tbest, t.best);
   }
   t.leaf = 0;
   if (t.cur < 0 && t.cur != kDone) {
@@ -975,7 +982,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
   uint32_t pool_rem = 0;
   bool drained = false;
   // lane's cached work item (for seeding)
-  uint64_t it_g0 = 1, it_g1 = 0, it_pid0 = 0;
+  uint64_t it_g1 = 0, it_off = 0;  // cached item: end of its work range, pid - g
   uint32_t it_q = 0;
 
   // lane's particle
@@ -1076,14 +1083,13 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
           const uint32_t nb = min(32u, pool_rem);
           if (lane < nb) {
             const uint64_t g = pool_base + lane;
-            if (!(g >= it_g0 && g < it_g1)) {
+            if (g >= it_g1) {  // a lane's work indices only grow
               const ItemDev item = a.items[find_item(a.items, a.n_items, g)];
-              it_g0 = item.g_begin;
               it_g1 = item.g_begin + item.count;
-              it_pid0 = item.pid_begin;
+              it_off = item.pid_begin - item.g_begin;
               it_q = item.query;
             }
-            seed_into<R>(a, it_q, it_pid0 + (g - it_g0), queue[(q_head + q_count + lane) & (kQueue - 1)]);
+            seed_into<R>(a, it_q, g + it_off, queue[(q_head + q_count + lane) & (kQueue - 1)]);
           }
           pool_base += nb;
           pool_rem -= nb;

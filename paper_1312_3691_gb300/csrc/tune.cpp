@@ -37,7 +37,7 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
   for (uint32_t block : {64u, 128u, 256u})
     for (uint32_t sm_nodes : {0u, 256u}) {
       for (uint32_t occ : {0u, 6u, 4u})  // 0: the highest occupancy
-        for (uint32_t refill : {4u, 8u, 16u}) {
+        for (uint32_t refill : {8u, 16u, 24u}) {
           LaunchCfg cfg;
           cfg.block = block;
           cfg.smem_nodes = std::min(sm_nodes, nn);
