@@ -340,9 +340,10 @@ __device__ R normal_speed_inverse(R u, R s, const float* tab) {
     const float target = upper ? 1.0f - u : u;
     float Z, Zs, gs = 0.0f;
     if (s >= 0.0f) {
-      Z = expf(-s * s) + sp * erfcf(-s);
+      const float es = expf(-s * s), ecs = erfcf(s);  // erfc(-s) = 2 - erfc(s), in [1, 2]
+      Z = es + sp * (2.0f - ecs);
       Zs = Z;
-      gs = sp * erfcf(s) - expf(-s * s);
+      gs = sp * ecs - es;
     } else {
       Zs = 1.0f + sp * erfcxf(-s);
       Z = Zs;

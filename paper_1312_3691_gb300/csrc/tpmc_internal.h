@@ -146,7 +146,7 @@ struct LaunchCfg {
   uint32_t blocks_per_sm = 4;
   uint32_t chunk = 0;
   uint32_t smem_nodes = 0;
-  uint32_t refill_at = 16;
+  uint32_t refill_at = 0;      // 0: the default (24)
 };
 
 // ------------------------------------------------------------ host launchers
