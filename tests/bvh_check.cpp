@@ -1,0 +1,169 @@
+// Host check of the BVH builder (paper_1312_3691_gb300/csrc/bvh.cpp).
+//
+// Builds the hierarchy exactly as tpmc_mesh_load does, then, for every ray of
+// a ray file, finds the closest hit twice with one and the same double
+// precision ray/triangle test: by walking the built tree (the float boxes
+// as laid out for the GPU, culled against the best hit so far, inclusive)
+// and by brute force over all triangles.  Nearest t wins; equal t goes to the
+// lower triangle index.  A tree that loses any part of a triangle (a spatial
+// split that drops a piece, a box that does not contain its part) shows up as
+// a ray whose two answers differ.  Also checks that every triangle with
+// nonzero area is referenced by some leaf and that leaves respect the size
+// limit (more than max_leaf only where the depth limit stops the build, and
+// never more than 127).
+//
+// usage: bvh_check MESH RAYS MAX_LEAF
+//   MESH: uint32 n_vert, uint32 n_tri, double xyz[n_vert][3], uint32 tri[n_tri][3]
+//   RAYS: uint32 n_rays, double ray[n_rays][6] (origin, direction)
+// prints one line: rays mismatches hits n_tri n_refs n_nodes depth leaf_max unreferenced oversized
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "tpmc_internal.h"
+
+namespace {
+
+bool read_all(const char* path, std::vector<unsigned char>& out) {
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return false;
+  unsigned char buf[1 << 16];
+  size_t n;
+  while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) out.insert(out.end(), buf, buf + n);
+  std::fclose(f);
+  return true;
+}
+
+// Moller-Trumbore; boundary inclusive.  Returns t or -1.
+double hit(const double* o, const double* d, const double* a, const double* b, const double* c) {
+  double e1[3], e2[3], s[3];
+  for (int i = 0; i < 3; ++i) { e1[i] = b[i] - a[i]; e2[i] = c[i] - a[i]; s[i] = o[i] - a[i]; }
+  const double p[3] = {d[1] * e2[2] - d[2] * e2[1], d[2] * e2[0] - d[0] * e2[2], d[0] * e2[1] - d[1] * e2[0]};
+  const double det = e1[0] * p[0] + e1[1] * p[1] + e1[2] * p[2];
+  if (det == 0.0) return -1.0;
+  const double inv = 1.0 / det;
+  const double u = (s[0] * p[0] + s[1] * p[1] + s[2] * p[2]) * inv;
+  if (u < 0.0 || u > 1.0) return -1.0;
+  const double q[3] = {s[1] * e1[2] - s[2] * e1[1], s[2] * e1[0] - s[0] * e1[2], s[0] * e1[1] - s[1] * e1[0]};
+  const double v = (d[0] * q[0] + d[1] * q[1] + d[2] * q[2]) * inv;
+  if (v < 0.0 || u + v > 1.0) return -1.0;
+  const double t = (e2[0] * q[0] + e2[1] * q[1] + e2[2] * q[2]) * inv;
+  return t > 1e-12 ? t : -1.0;
+}
+
+struct Best {
+  double t = INFINITY;
+  uint32_t id = 0xFFFFFFFFu;
+  void offer(double t2, uint32_t id2) {
+    if (t2 < 0.0) return;
+    if (t2 < t || (t2 == t && id2 < id)) { t = t2; id = id2; }
+  }
+};
+
+}  // namespace
+
+int main(int argc, char** argv) {
+  if (argc < 4) return 2;
+  std::vector<unsigned char> mb, rb;
+  if (!read_all(argv[1], mb) || !read_all(argv[2], rb)) return 3;
+  const uint32_t max_leaf = (uint32_t)std::atoi(argv[3]);
+  uint32_t nv, nt, nr;
+  std::memcpy(&nv, mb.data(), 4);
+  std::memcpy(&nt, mb.data() + 4, 4);
+  std::vector<double> xyz(3 * (size_t)nv);
+  std::vector<uint32_t> tri(3 * (size_t)nt);
+  std::memcpy(xyz.data(), mb.data() + 8, xyz.size() * 8);
+  std::memcpy(tri.data(), mb.data() + 8 + xyz.size() * 8, tri.size() * 4);
+  std::memcpy(&nr, rb.data(), 4);
+  std::vector<double> rays(6 * (size_t)nr);
+  std::memcpy(rays.data(), rb.data() + 4, rays.size() * 8);
+
+  tpmc::BvhBuild b;
+  const char* err = nullptr;
+  if (!tpmc::build_bvh(xyz.data(), nv, tri.data(), nt, max_leaf, &b, &err)) {
+    std::printf("build failed: %s\n", err ? err : "?");
+    return 4;
+  }
+  auto vert = [&](uint32_t t, int k) { return xyz.data() + 3 * (size_t)tri[3 * (size_t)t + k]; };
+
+  // references: every triangle with nonzero area appears in some leaf
+  std::vector<char> seen(nt, 0);
+  for (uint32_t k = 0; k < b.n_leaf_tris; ++k) {
+    uint32_t id;
+    std::memcpy(&id, b.tris + 12 * (size_t)k + 3, 4);
+    if (id < nt) seen[id] = 1;
+  }
+  uint32_t unreferenced = 0;
+  for (uint32_t t = 0; t < nt; ++t) {
+    const double* a = vert(t, 0);
+    const double* bb = vert(t, 1);
+    const double* c = vert(t, 2);
+    const double e1[3] = {bb[0] - a[0], bb[1] - a[1], bb[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    const double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    const bool nonzero = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]) > 0.0;
+    if (nonzero && !seen[t]) ++unreferenced;
+  }
+
+  // leaves within the size limit
+  uint32_t oversized = 0;
+  std::vector<int32_t> stack;
+  for (size_t g = 0; g < b.n_nodes; ++g)
+    for (int c = 0; c < 2; ++c) {
+      int32_t code;
+      std::memcpy(&code, b.nodes + 16 * g + 12 + c, 4);
+      if (code < 0 && ((~(uint32_t)code) >> 24) > 127u) ++oversized;
+    }
+
+  uint64_t mismatches = 0, hits = 0;
+  for (uint32_t r = 0; r < nr; ++r) {
+    const double* o = rays.data() + 6 * (size_t)r;
+    const double* d = o + 3;
+    Best brute;
+    for (uint32_t t = 0; t < nt; ++t) brute.offer(hit(o, d, vert(t, 0), vert(t, 1), vert(t, 2)), t);
+    Best walk;
+    if (b.n_nodes > 0) {
+      stack.assign(1, 0);
+      while (!stack.empty()) {
+        const int32_t node = stack.back();
+        stack.pop_back();
+        const float* nd = b.nodes + 16 * (size_t)node;
+        for (int c = 0; c < 2; ++c) {
+          const float* xy = nd + 4 * c;
+          const float* z = nd + 8 + 2 * c;
+          const double lo[3] = {xy[0], xy[2], z[0]}, hi[3] = {xy[1], xy[3], z[1]};
+          double tn = 0.0, tf = walk.t;
+          for (int i = 0; i < 3; ++i) {
+            if (d[i] == 0.0) {
+              if (o[i] < lo[i] || o[i] > hi[i]) tn = INFINITY;
+              continue;
+            }
+            const double t0 = (lo[i] - o[i]) / d[i], t1 = (hi[i] - o[i]) / d[i];
+            tn = std::fmax(tn, std::fmin(t0, t1));
+            tf = std::fmin(tf, std::fmax(t0, t1));
+          }
+          if (!(tn <= tf)) continue;
+          int32_t code;
+          std::memcpy(&code, nd + 12 + c, 4);
+          if (code >= 0) {
+            stack.push_back(code);
+          } else {
+            const uint32_t u = ~(uint32_t)code, first = u & 0xFFFFFFu, count = u >> 24;
+            for (uint32_t k = first; k < first + count; ++k) {
+              uint32_t id;
+              std::memcpy(&id, b.tris + 12 * (size_t)k + 3, 4);
+              walk.offer(hit(o, d, vert(id, 0), vert(id, 1), vert(id, 2)), id);
+            }
+          }
+        }
+      }
+    }
+    if (brute.id != 0xFFFFFFFFu) ++hits;
+    if (brute.id != walk.id || !(brute.t == walk.t || (std::isinf(brute.t) && std::isinf(walk.t)))) ++mismatches;
+  }
+  std::printf("%u %llu %llu %u %u %zu %u %u %u %u\n", nr, (unsigned long long)mismatches, (unsigned long long)hits, nt,
+              b.n_leaf_tris, b.n_nodes, b.depth, b.leaf_max, unreferenced, oversized);
+  b.release();
+  return 0;
+}
