@@ -186,8 +186,8 @@ struct BvhBuild {
   void release();
 };
 
-// Builds a binned-SAH BVH over the mesh.  Returns false (with a message) on
-// invalid input.
+// Builds a BVH over the mesh by the surface-area heuristic with spatial
+// splits.  Returns false (with a message) on invalid input.
 bool build_bvh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t n_tri, uint32_t max_leaf,
                BvhBuild* out, const char** err);
 
