@@ -643,6 +643,44 @@ def test_flow_along_the_stream_axis(T, orc, ctx, sign):
         assert cd_close(res["CD"], ores["CD"], ores["CD_sigma"])
 
 
+def test_rotating_mesh_and_flow_together_on_the_gpu(T, orc, ctx):
+    """Eq. 15 on the CUDA path: with the stream along +z, a rotation Q about a
+    horizontal axis is the rotation the set-up builds for the flow Q z, so
+    turning the mesh, the CV centre, the moment point and the flow by Q must
+    turn every path rigidly.  FP64: the same hits and the same C_D to 1e-9;
+    FP32: the same hits away from edges."""
+    import math as m
+
+    xyz, tri = M.satellite(8000)
+    c, rb = M.bounding_sphere(xyz)
+    u = np.array([m.cos(0.3), m.sin(0.3), 0.0])
+    Kx = np.array([[0, -u[2], u[1]], [u[2], 0, -u[0]], [-u[1], u[0], 0]])
+    Q = np.eye(3) + m.sin(0.7) * Kx + (1 - m.cos(0.7)) * Kx @ Kx
+    z = np.array([0.0, 0.0, 1.0])
+    base = dict(**W.base_state(S=7.0), eps_diffuse=0.9, A_ref=2.0, r_cv=1.05 * rb, max_bounces=64, seed=7)
+    N = 20_011
+    for prec in (T.TPMC_FP64, T.TPMC_FP32):
+        runs = []
+        for X, d, cc in ((xyz, z, c), (xyz @ Q.T, Q @ z, Q @ c)):
+            mesh = T.tpmc_mesh_load(ctx, X, tri)
+            try:
+                runs.append(T.tpmc_trace_records(ctx, mesh, T.make_params(**base, dir=tuple(d), center=tuple(cc),
+                                                                           ref_point=tuple(cc), precision=prec), N, K=K))
+            finally:
+                T.tpmc_mesh_unload(ctx, mesh)
+        (r1, a), (r2, b) = runs
+        same = (a["n_hits"] == b["n_hits"]) & (a["tri"] == b["tri"]).all(axis=1)
+        assert (a["n_hits"] > 0).sum() > 1000
+        if prec == T.TPMC_FP64:
+            assert same.mean() > 0.999
+            np.testing.assert_allclose(b["pos"], a["pos"] @ Q.T, rtol=0, atol=1e-11)
+            assert abs(r2["CD"] - r1["CD"]) <= 1e-9 * abs(r1["CD"])
+        else:
+            assert same.mean() > 0.99
+            np.testing.assert_allclose(b["pos"], a["pos"] @ Q.T, rtol=0, atol=5e-6)
+            assert cd_close(r2["CD"], r1["CD"], r1["CD_sigma"])
+
+
 def test_spatial_splits_keep_the_closest_hit(T, orc, ctx):
     """The cylinder's end caps are fans of 128 triangles that meet at the cap
     centre, so the builder cuts some of them into parts held by different

@@ -56,6 +56,44 @@ def _solve_hits(xyz, tri, o, d, t_min=1e-12):
     return best
 
 
+def _horizontal_rotation(axis_angle=0.3, angle=0.7):
+    u = np.array([math.cos(axis_angle), math.sin(axis_angle), 0.0])
+    K = np.array([[0, -u[2], u[1]], [u[2], 0, -u[0]], [-u[1], u[0], 0]])
+    return np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * K @ K
+
+
+def test_rotating_mesh_and_flow_together_rotates_every_path(orc):
+    """Eq. 15 and the rest of the path are rotation equivariant.  With the
+    stream along +z, a rotation Q about a horizontal axis is exactly the
+    rotation Eq. 15 builds for the flow Q z, so turning the mesh, the control
+    volume's centre, the moment point and the flow by Q turns every seeded
+    particle and every path rigidly: same hits, positions and momentum
+    transfers rotated by Q, the same C_D.  A transposed rotation, a rotation
+    that ignores the flow's azimuth, or a re-emission frame that does not
+    follow the surface breaks this."""
+    xyz, tri = M.satellite(8000)
+    c, rb = M.bounding_sphere(xyz)
+    Q = _horizontal_rotation()
+    z = np.array([0.0, 0.0, 1.0])
+    R = np.stack([orc.rodrigues(Q @ z, e) for e in np.eye(3)], axis=1)
+    np.testing.assert_allclose(R, Q, atol=1e-15)
+    base = dict(**W.base_state(S=7.0), eps_diffuse=0.9, A_ref=2.0, r_cv=1.05 * rb, max_bounces=64, seed=7)
+    N = 20_000
+    r1, _, a = orc.trace(orc.Mesh(xyz, tri), orc.make_params(**base, dir=tuple(z), center=tuple(c),
+                                                            ref_point=tuple(c)), N, records=True)
+    r2, _, b = orc.trace(orc.Mesh(xyz @ Q.T, tri), orc.make_params(**base, dir=tuple(Q @ z), center=tuple(Q @ c),
+                                                                  ref_point=tuple(Q @ c)), N, records=True)
+    assert (a["n_hits"] > 0).sum() > 1000 and a["n_hits"].max() >= 3
+    same = (a["n_hits"] == b["n_hits"]) & (a["tri"] == b["tri"]).all(axis=1)
+    assert same.mean() > 0.999
+    np.testing.assert_allclose(b["pos"], a["pos"] @ Q.T, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(b["dv"][same], a["dv"][same] @ Q.T, rtol=0, atol=1e-11)
+    assert abs(r2["CD"] - r1["CD"]) <= 1e-9 * abs(r1["CD"])
+    np.testing.assert_allclose(r2["force"], Q @ np.array(r1["force"]), rtol=0, atol=1e-9 * np.abs(r1["force"]).max())
+    np.testing.assert_allclose(r2["torque"], Q @ np.array(r1["torque"]), rtol=0,
+                               atol=1e-9 * np.abs(r1["torque"]).max())
+
+
 def test_closest_hit_matches_linear_solve(orc):
     xyz, tri = M.icosphere(2, 1.0)
     mesh = orc.Mesh(xyz, tri)
