@@ -235,6 +235,17 @@ tpmc_status tpmc_trace(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* para
  * memory.  Errors: ENOTFOUND, EINVAL (n_tri mismatch). */
 tpmc_status tpmc_panels(tpmc_ctx* ctx, tpmc_query_id query, double* pressure, double* shear, uint32_t n_tri);
 
+/* The per-triangle momentum sums behind tpmc_panels (§II.A: the force is the
+ * weighted sum of the momentum the particles deliver): dv_q, a host buffer of
+ * [n_tri][3] int64, receives for each triangle the sum over its hits of
+ * (v_in - v_out) in units of tpmc_result.fixed_quantum (c_mp units), the same
+ * integers whose sum over triangles is tpmc_result.sum_dv_q, bit for bit.  The
+ * force on triangle i in N is dv_q[i] * fixed_quantum * weight * m * c_mp.
+ * Keeps the panel memory, so tpmc_panels may follow.
+ * Errors: ENOTFOUND (no panel loads kept for the query), EINVAL (NULL dv_q,
+ * n_tri mismatch), ECUDA. */
+tpmc_status tpmc_panel_sums(tpmc_ctx* ctx, tpmc_query_id query, int64_t* dv_q, uint32_t n_tri);
+
 /* Same as tpmc_trace and also fills per-particle records (verification).
  * Errors as tpmc_trace, plus EINVAL for K > 64 or N > 2^26. */
 tpmc_status tpmc_trace_records(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* params, uint64_t N,

@@ -566,6 +566,23 @@ tpmc_status tpmc_panels(tpmc_ctx* ctx, tpmc_query_id query, double* pressure, do
   return TPMC_OK;
 }
 
+tpmc_status tpmc_panel_sums(tpmc_ctx* ctx, tpmc_query_id query, int64_t* dv_q, uint32_t n_tri) {
+  if (!ctx) return fail(TPMC_EINVAL, "ctx is NULL");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!dv_q) return fail(TPMC_EINVAL, "dv_q is NULL");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  auto it = c->panels.find(query);
+  if (it == c->panels.end()) return fail(TPMC_ENOTFOUND, "no panel loads kept for this query");
+  const PanelRec& pr = it->second;
+  if (n_tri != pr.n_tri) return fail(TPMC_EINVAL, "n_tri does not match the mesh");
+  cudaSetDevice(c->device);
+  cudaError_t e = cudaMemcpyAsync(dv_q, pr.d_panel, (size_t)n_tri * 3 * sizeof(long long), cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "panel sums");
+  return TPMC_OK;
+}
+
 static tpmc_status sweep_common(Ctx* c, tpmc_mesh_id mesh, const tpmc_params* base, const double* d_dirs,
                                 const double* d_S, uint32_t K, uint64_t N_each, tpmc_result* d_out) {
   tpmc_status st = validate_params(base);

@@ -96,6 +96,7 @@ SIGNATURES = {
     "tpmc_mesh_info": [_P, ctypes.c_uint32, ctypes.POINTER(tpmc_mesh_stats)],
     "tpmc_trace": [_P, ctypes.c_uint32, ctypes.POINTER(tpmc_params), ctypes.c_uint64, ctypes.POINTER(tpmc_result)],
     "tpmc_panels": [_P, ctypes.c_uint64, _PD, _PD, ctypes.c_uint32],
+    "tpmc_panel_sums": [_P, ctypes.c_uint64, _P, ctypes.c_uint32],
     "tpmc_trace_records": [_P, ctypes.c_uint32, ctypes.POINTER(tpmc_params), ctypes.c_uint64,
                            ctypes.POINTER(tpmc_records), ctypes.POINTER(tpmc_result)],
     "tpmc_sweep": [_P, ctypes.c_uint32, ctypes.POINTER(tpmc_params), _PD, _PD, ctypes.c_uint32, ctypes.c_uint64,
@@ -253,6 +254,13 @@ def tpmc_panels(ctx, query_id: int, n_tri: int):
     s = np.zeros(n_tri)
     _check(lib().tpmc_panels(ctx, int(query_id), _pd(p), _pd(s), int(n_tri)), "tpmc_panels", ctx)
     return p, s
+
+
+def tpmc_panel_sums(ctx, query_id: int, n_tri: int):
+    q = np.zeros((n_tri, 3), dtype=np.int64)
+    _check(lib().tpmc_panel_sums(ctx, int(query_id), q.ctypes.data_as(ctypes.c_void_p), int(n_tri)),
+           "tpmc_panel_sums", ctx)
+    return q
 
 
 def tpmc_sweep(ctx, mesh: int, base: tpmc_params, dirs, S, N_each: int):

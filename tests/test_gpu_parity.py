@@ -173,6 +173,7 @@ def test_panels_match_oracle(T, orc, ctx):
     mesh = T.tpmc_mesh_load(ctx, xyz, tri)
     try:
         res = T.tpmc_trace(ctx, mesh, _gpu_params(T, params, T.TPMC_FP64, want_panels=True), N)
+        dq = T.tpmc_panel_sums(ctx, res["query_id"], tri.shape[0])
         pg, sg = T.tpmc_panels(ctx, res["query_id"], tri.shape[0])
         with pytest.raises(T.TpmcError):
             T.tpmc_panels(ctx, res["query_id"], tri.shape[0])  # released after the first read
@@ -192,9 +193,12 @@ def test_panels_match_oracle(T, orc, ctx):
     tol = 1e-6 * np.abs(p_ref).max()
     np.testing.assert_allclose(pg, p_ref, rtol=1e-6, atol=tol)
     np.testing.assert_allclose(sg, s_ref, rtol=1e-6, atol=tol)
-    # conservation: the per-triangle loads add up to the total force
-    Ftot = -(pg * area)[:, None] * nrm
-    assert np.isfinite(Ftot).all()
+    # conservation: the per-triangle integer sums add up to the total, bit for bit
+    assert dq.sum(axis=0).tolist() == list(res["sum_dv_q"])
+    # each hit is rounded to the quantum once: far below 1e-9 of the largest panel sum here
+    np.testing.assert_allclose(dq * res["fixed_quantum"], pdv, rtol=1e-9, atol=1e-9 * np.abs(pdv).max())
+    with pytest.raises(T.TpmcError):
+        T.tpmc_panel_sums(ctx, res["query_id"], tri.shape[0])  # released with the panels
 
 
 # ------------------------------------------------------------ edge cases
