@@ -305,6 +305,30 @@ def test_plate_runs_match_derived_eq3_not_printed(orc, T_inf):
                 assert abs(res["CD"] - printed) > 8 * res["CD_sigma"]
 
 
+@pytest.mark.parametrize("eps", [1.0, 0.0])
+def test_plate_is_mirror_symmetric_in_alpha(orc, eps):
+    """C_D(alpha) = C_D(-alpha), and the force mirrors: its component along the
+    plate (the lift side) flips sign, the others keep theirs.  Independent
+    streams, so the two runs agree within their standard errors; this pins the
+    sign conventions without a closed form."""
+    xyz, tri = M.plate()
+    c, rb = M.bounding_sphere(xyz)
+    st = W.base_state(S=5.0)
+    a = math.radians(35.0)
+    runs = [_run(orc, xyz, tri, dict(**st, dir=W.plate_alpha_dir(sg * a), eps_diffuse=eps, A_ref=1.0,
+                                     r_cv=1.05 * rb, center=tuple(c), seed=23), 300_000)[0] for sg in (1, -1)]
+    p, m = runs
+    sig = math.hypot(p["CD_sigma"], m["CD_sigma"])
+    assert abs(p["CD"] - m["CD"]) <= 4.0 * sig
+    Fp, Fm = np.array(p["force"]), np.array(m["force"])
+    sF = np.linalg.norm(Fp) * sig / p["CD"]
+    mirror = np.array([-1.0, 1.0, 1.0])
+    assert np.all(np.abs(Fm - mirror * Fp) <= 4.0 * sF + 1e-15)
+    assert abs(Fp[1]) <= 4.0 * sF and abs(Fm[1]) <= 4.0 * sF
+    if eps > 0:
+        assert Fp[0] > 10 * sF and Fm[0] < -10 * sF  # diffuse walls carry a tangential force
+
+
 def test_plate_drag_decreases_with_alpha_and_stays_positive_edge_on(orc):
     # §III.C: C_D falls from alpha = 0 to 90 deg and is non-zero edge-on at S = 7
     xyz, tri = M.plate()
