@@ -296,8 +296,12 @@ tpmc_status tpmc_poll(tpmc_ctx* ctx, tpmc_query_id query, int timeout_ms, tpmc_r
 
 /* ---- schedule ------------------------------------------------------------ */
 
-/* Measures candidate schedules on `mesh` with short launches and keeps the
- * fastest for meshes of its size class and this precision. */
+/* Measures candidate schedules on `mesh` and keeps the fastest for meshes of
+ * its size class and this precision.  Each candidate traces N_trial / 4 and
+ * then N_trial particles of one query built from `params`; it is scored by the
+ * marginal rate between the two, so that fixed per-launch costs do not decide
+ * (N_trial of a few million or more keeps the difference above the noise).
+ * The kept schedule leaves the chunk automatic. */
 tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* params, uint64_t N_trial,
                       tpmc_launch* best);
 tpmc_status tpmc_set_launch(tpmc_ctx* ctx, const tpmc_launch* cfg);

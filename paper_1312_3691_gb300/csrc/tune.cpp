@@ -54,22 +54,41 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
   cudaEventCreate(&e1);
   const bool had_manual = c->manual_launch;
   const LaunchCfg old_manual = c->manual;
-  float best_ms = 1e30f;
+  // Each candidate runs a quarter of N_trial and then all of it; the score is
+  // the marginal rate (N_trial - N_trial / 4) / (t_full - t_quarter), so the
+  // fixed costs of a launch (set-up, reduction, the tail of its last warps)
+  // drop out and the choice holds for the long launches of sweeps.  The
+  // chunk stays automatic, so each later launch sizes it from its own total.
+  const uint64_t quarter = std::max<uint64_t>(1, N_trial / 4);
+  double best_rate = -1.0;
   LaunchCfg best_cfg;
   for (int pass = 0; pass < 2; ++pass) {  // pass 0 warms caches and clocks
     for (const LaunchCfg& cfg : cands) {
       c->manual_launch = true;
       c->manual = cfg;
-      cudaEventRecord(e0, c->stream);
-      st = c->run(m, &q, 1, nullptr, nullptr, nullptr, &item, 1, N_trial, trace_variant(params),
-                  (tpmc_result*)c->s_out.ptr, nullptr);
-      cudaEventRecord(e1, c->stream);
+      float ms[2] = {0.0f, 0.0f};
+      LaunchCfg used;
+      for (int k = 0; k < 2 && st == TPMC_OK; ++k) {
+        item.count = k == 0 ? quarter : N_trial;
+        cudaEventRecord(e0, c->stream);
+        st = c->run(m, &q, 1, nullptr, nullptr, nullptr, &item, 1, item.count, trace_variant(params),
+                    (tpmc_result*)c->s_out.ptr, nullptr);
+        cudaEventRecord(e1, c->stream);
+        if (st != TPMC_OK) break;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) { st = cuda_fail(e, "tune"); break; }
+        cudaEventElapsedTime(&ms[k], e0, e1);
+        used = c->last_cfg;
+      }
       if (st != TPMC_OK) break;
-      cudaError_t e = cudaEventSynchronize(e1);
-      if (e != cudaSuccess) { st = cuda_fail(e, "tune"); break; }
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (pass == 1 && ms < best_ms) { best_ms = ms; best_cfg = c->last_cfg; }
+      const double dt = (double)ms[1] - (double)ms[0];
+      const double rate = (N_trial > quarter && dt > 0.0) ? (double)(N_trial - quarter) / dt
+                                                          : (double)N_trial / std::max((double)ms[1], 1e-6);
+      if (pass == 1 && rate > best_rate) {
+        best_rate = rate;
+        best_cfg = used;
+        best_cfg.chunk = 0;
+      }
     }
     if (st != TPMC_OK) break;
   }
