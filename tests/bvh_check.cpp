@@ -36,13 +36,18 @@ bool read_all(const char* path, std::vector<unsigned char>& out) {
   return true;
 }
 
-// Moller-Trumbore; boundary inclusive.  Returns t or -1.
+// Moller-Trumbore; boundary inclusive.  Returns t or -1.  A determinant below
+// 1e-12 of |e1| |e2| |d| (a collinear triangle, or a ray in the triangle's
+// plane) counts as no hit: rounding would otherwise turn it into a spurious
+// hit far from the triangle.
 double hit(const double* o, const double* d, const double* a, const double* b, const double* c) {
   double e1[3], e2[3], s[3];
   for (int i = 0; i < 3; ++i) { e1[i] = b[i] - a[i]; e2[i] = c[i] - a[i]; s[i] = o[i] - a[i]; }
   const double p[3] = {d[1] * e2[2] - d[2] * e2[1], d[2] * e2[0] - d[0] * e2[2], d[0] * e2[1] - d[1] * e2[0]};
   const double det = e1[0] * p[0] + e1[1] * p[1] + e1[2] * p[2];
-  if (det == 0.0) return -1.0;
+  const double scale = std::sqrt((e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]) *
+                                 (e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]) * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+  if (!(std::fabs(det) > 1e-12 * scale)) return -1.0;
   const double inv = 1.0 / det;
   const double u = (s[0] * p[0] + s[1] * p[1] + s[2] * p[2]) * inv;
   if (u < 0.0 || u > 1.0) return -1.0;
