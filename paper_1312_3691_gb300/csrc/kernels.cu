@@ -663,14 +663,15 @@ __device__ __forceinline__ int trav_pop(Trav<R>& t, const StackE<R>* stack) {
 }
 
 // One inner node: test both children, continue with the nearer hit child,
-// stack the farther one; the first leaf reached is postponed.
-template <typename R>
+// stack the farther one; the first leaf reached is postponed.  STAGE: nodes
+// below n_stage come from the copy in shared memory.
+template <typename R, bool STAGE>
 __device__ __forceinline__ void trav_inner(const MeshDev& m, const float4* __restrict__ s_nodes, uint32_t n_stage,
                                            const Ray<R>& r, Trav<R>& t, StackE<R>* stack, uint32_t& n_nodes,
                                            int* err) {
   ++n_nodes;
   float4 n0, n1, n2, n3;
-  if ((uint32_t)t.cur < n_stage) {
+  if (STAGE && (uint32_t)t.cur < n_stage) {
     n0 = s_nodes[4 * t.cur]; n1 = s_nodes[4 * t.cur + 1]; n2 = s_nodes[4 * t.cur + 2]; n3 = s_nodes[4 * t.cur + 3];
   } else {
     const float4* g = m.nodes + 4 * (size_t)t.cur;
@@ -1134,9 +1135,17 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
     // ---- 4. traversal round: inner nodes until every searching lane holds a
     // leaf (lanes with a leaf keep descending meanwhile), then the leaves
     for (;;) {
-      while (__any_sync(kFull, has && !tdone && tv.cur >= 0 && tv.leaf == 0)) {
-        if (has && !tdone && tv.cur >= 0)
-          trav_inner<R>(a.mesh, s_nodes, n_stage, ray, tv, stack, n_nodes, a.error);
+      // without staged nodes, the shared-memory check leaves the node loop
+      if (n_stage == 0) {
+        while (__any_sync(kFull, has && !tdone && tv.cur >= 0 && tv.leaf == 0)) {
+          if (has && !tdone && tv.cur >= 0)
+            trav_inner<R, false>(a.mesh, s_nodes, n_stage, ray, tv, stack, n_nodes, a.error);
+        }
+      } else {
+        while (__any_sync(kFull, has && !tdone && tv.cur >= 0 && tv.leaf == 0)) {
+          if (has && !tdone && tv.cur >= 0)
+            trav_inner<R, true>(a.mesh, s_nodes, n_stage, ray, tv, stack, n_nodes, a.error);
+        }
       }
       if (has && !tdone) {
         if (tv.leaf != 0) tdone = trav_leaf<R>(a.mesh, ray, last, tv, stack, n_tris);
