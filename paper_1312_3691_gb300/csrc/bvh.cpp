@@ -365,6 +365,11 @@ bool build_bvh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t
         } else {
           Ref l = r, rr = r;
           split_ref(prims[r.p], r.box, a, plane, l.box, rr.box);
+          if (l.box.empty() && rr.box.empty()) {
+            // rounding left neither side a box: keep the whole part on both
+            l.box = r.box;
+            rr.box = r.box;
+          }
           if (!l.box.empty()) lref.push_back(l);
           if (!rr.box.empty()) rref.push_back(rr);
         }
