@@ -167,7 +167,8 @@ typedef struct {
   uint64_t device_bytes;
   uint32_t n_refs;              /* triangle references in the leaves: spatial splits    */
                                 /* put parts of some triangles in several leaves         */
-  uint32_t pad_;
+  uint32_t n_exposed;           /* triangle sides with the whole mesh behind them: a    */
+                                /* particle re-emitted from one is not traced further    */
 } tpmc_mesh_stats;
 
 /* Launch schedule of the trace kernel (chosen by tpmc_tune or set by hand). */

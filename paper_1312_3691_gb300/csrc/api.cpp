@@ -382,6 +382,7 @@ tpmc_status tpmc_mesh_load(tpmc_ctx* ctx, const double* xyz, uint32_t n_vert, co
   m.depth = b.depth;
   m.leaf_max = b.leaf_max;
   m.n_skipped = b.n_skipped;
+  m.n_exposed = b.n_exposed;
   m.n_vert = n_vert;
   m.bytes = total;
   m.h_xyz.assign(xyz, xyz + 3 * (size_t)n_vert);
@@ -425,6 +426,7 @@ tpmc_status tpmc_mesh_info(tpmc_ctx* ctx, tpmc_mesh_id mesh, tpmc_mesh_stats* ou
   out->bound_radius = m.radius;
   out->device_bytes = m.bytes;
   out->n_refs = m.dev.n_tri_leaf;
+  out->n_exposed = m.n_exposed;
   return TPMC_OK;
 }
 

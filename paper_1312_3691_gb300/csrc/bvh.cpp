@@ -18,11 +18,17 @@
 // box contains its part, so the ray meets the box of the part that holds the
 // hit point no later than the hit, and ties between references of one
 // triangle compare equal.
+//
+// It also marks each triangle side that the whole mesh lies behind (every
+// face of a convex body, both sides of a flat sheet): a particle re-emitted
+// from such a side has nothing ahead of it, so the trace kernel skips its
+// traversal.  The marks go in the spare word of the triangle's frame.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <thread>
 #include <vector>
 
 #include "tpmc_internal.h"
@@ -139,6 +145,16 @@ void add_parts(const Prim& t, const Box& box, int axis, double lo, double w, int
   }
 }
 
+// Largest (sign = +1) or smallest (sign = -1) value of n . (x - o) over box b.
+double box_extreme(const Box& b, const double n[3], const double o[3], double sign) {
+  double v = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const bool hi = (n[k] * sign) > 0.0;
+    v += n[k] * ((hi ? b.hi[k] : b.lo[k]) - o[k]);
+  }
+  return v;
+}
+
 struct BNode {       // binary build node
   Box box;
   int32_t left = -1, right = -1;  // children (build indices) for inner nodes
@@ -159,6 +175,11 @@ constexpr double kCostTri = 1.2;
 constexpr double kSpatialAlpha = 1e-3;
 constexpr double kRefBudget = 0.5;      // at most this many extra references per triangle, in total
 constexpr uint32_t kMaxDepth = kMaxStack - 20;  // SAH below this depth, median splits after
+// A side is exposed when no vertex of the mesh lies more than this (m) in front
+// of its plane.  The kernel skips a re-emitted ray only when it leaves at more
+// than 0.01 from the plane in cos, so a hit it could miss would lie within
+// 1e-10 m, below the shortest hit distance the traversal accepts.
+constexpr double kExposedEps = 1e-12;
 
 }  // namespace
 
@@ -402,6 +423,85 @@ bool build_bvh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t
     bn[ni].right = ri;
     todo.push_back(Task{ri, std::move(rref)});
     todo.push_back(Task{li, std::move(lref)});
+  }
+
+  // ---- exposed sides: bit 0 front (the side n points to), bit 1 back ----
+  // Branch and bound over the build tree: a node whose box lies wholly behind
+  // the plane holds no vertex in front of it.  Every vertex lies in the box of
+  // some leaf that references its triangle, so pruning is exact.
+  if (!bn.empty()) {
+    // The vertices that reach farthest along 26 directions (axes, face and
+    // space diagonals): most sides that are not exposed see one of them in
+    // front, which settles them without a search.
+    std::vector<const double*> probes;
+    for (int dx = -1; dx <= 1; ++dx)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dz = -1; dz <= 1; ++dz) {
+          if (dx == 0 && dy == 0 && dz == 0) continue;
+          const double* best = nullptr;
+          double bv = -INFINITY;
+          for (const Prim& t : prims)
+            for (int j = 0; j < 3; ++j) {
+              const double* v = t.v[j];
+              const double h = dx * v[0] + dy * v[1] + dz * v[2];
+              if (h > bv) { bv = h; best = v; }
+            }
+          if (best) probes.push_back(best);
+        }
+    auto side_clear = [&](const Prim& t, const double n[3], double sign, std::vector<int32_t>& stack) {
+      const double* o = t.v[0];
+      for (const double* v : probes)
+        if (sign * (n[0] * (v[0] - o[0]) + n[1] * (v[1] - o[1]) + n[2] * (v[2] - o[2])) > kExposedEps) return false;
+      stack.assign(1, 0);
+      while (!stack.empty()) {
+        const BNode& nd = bn[stack.back()];
+        stack.pop_back();
+        if (sign * box_extreme(nd.box, n, o, sign) <= kExposedEps) continue;
+        if (nd.left >= 0) {
+          // the child reaching farther in front is searched first
+          const bool l_first = sign * box_extreme(bn[nd.left].box, n, o, sign) >=
+                               sign * box_extreme(bn[nd.right].box, n, o, sign);
+          stack.push_back(l_first ? nd.right : nd.left);
+          stack.push_back(l_first ? nd.left : nd.right);
+          continue;
+        }
+        for (uint32_t k = nd.first; k < nd.first + nd.count; ++k)
+          for (int j = 0; j < 3; ++j) {
+            const double* v = prims[leaf_refs[k]].v[j];
+            const double h = n[0] * (v[0] - o[0]) + n[1] * (v[1] - o[1]) + n[2] * (v[2] - o[2]);
+            if (sign * h > kExposedEps) return false;
+          }
+      }
+      return true;
+    };
+    auto work = [&](size_t begin, size_t end) {
+      std::vector<int32_t> stack;
+      for (size_t k = begin; k < end; ++k) {
+        const Prim& t = prims[k];
+        const double* f = out->frames64 + 8 * (size_t)t.id;
+        const double n[3] = {f[0], f[1], f[2]};
+        uint32_t bits = 0;
+        if (side_clear(t, n, 1.0, stack)) bits |= 1u;
+        if (side_clear(t, n, -1.0, stack)) bits |= 2u;
+        out->frames64[8 * (size_t)t.id + 7] = (double)bits;
+        std::memcpy(out->frames + 8 * (size_t)t.id + 7, &bits, 4);
+      }
+    };
+    const size_t n_prims = prims.size();
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const size_t n_threads = n_prims < 4096 ? 1 : std::min<size_t>(hw, n_prims / 2048);
+    if (n_threads <= 1) {
+      work(0, n_prims);
+    } else {
+      std::vector<std::thread> th;
+      for (size_t w = 0; w < n_threads; ++w)
+        th.emplace_back(work, n_prims * w / n_threads, n_prims * (w + 1) / n_threads);
+      for (auto& t : th) t.join();
+    }
+    for (const Prim& t : prims) {
+      const uint32_t bits = (uint32_t)out->frames64[8 * (size_t)t.id + 7];
+      out->n_exposed += (bits & 1u) + ((bits >> 1) & 1u);
+    }
   }
 
   // ---- GPU layout: inner nodes in breadth-first order, leaves in place ----

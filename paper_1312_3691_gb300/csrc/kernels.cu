@@ -740,18 +740,22 @@ __device__ __forceinline__ bool trav_leaf(const MeshDev& m, const Ray<R>& r, uin
 
 // ------------------------------------------------ re-emission (§II.A)
 template <typename R> struct Frame;
+// A triangle's frame, and its exposed sides (bit 0: the side n points to,
+// bit 1: the other): sides that the whole mesh lies behind.
 template <> struct Frame<float> {
-  static __device__ __forceinline__ void load(const MeshDev& m, uint32_t id, float n[3], float t1[3]) {
+  static __device__ __forceinline__ uint32_t load(const MeshDev& m, uint32_t id, float n[3], float t1[3]) {
     const float4 a = __ldg(&m.frames[2 * id]), b = __ldg(&m.frames[2 * id + 1]);
     n[0] = a.x; n[1] = a.y; n[2] = a.z;
     t1[0] = b.x; t1[1] = b.y; t1[2] = b.z;
+    return __float_as_uint(b.w);
   }
 };
 template <> struct Frame<double> {
-  static __device__ __forceinline__ void load(const MeshDev& m, uint32_t id, double n[3], double t1[3]) {
+  static __device__ __forceinline__ uint32_t load(const MeshDev& m, uint32_t id, double n[3], double t1[3]) {
     const double* f = m.frames64 + 8 * (size_t)id;
     n[0] = __ldg(f); n[1] = __ldg(f + 1); n[2] = __ldg(f + 2);
     t1[0] = __ldg(f + 4); t1[1] = __ldg(f + 5); t1[2] = __ldg(f + 6);
+    return (uint32_t)__ldg(f + 7);
   }
 };
 
@@ -1007,7 +1011,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
       if (tv.best != 0xFFFFFFFFu) {
         const uint32_t hit = tv.best;
         R nrm[3], t1[3], hp[3], v_in[3];
-        Frame<R>::load(a.mesh, hit, nrm, t1);
+        const uint32_t exposed = Frame<R>::load(a.mesh, hit, nrm, t1);
 #pragma unroll
         for (int i = 0; i < 3; ++i) { hp[i] = ray.o[i] + tv.tbest * ray.d[i]; v_in[i] = ray.d[i]; }
         R v[3] = {ray.d[0], ray.d[1], ray.d[2]};
@@ -1041,11 +1045,20 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
         if (bounce >= q.max_bounces) {
           ++acc.truncated;
         } else {
-          const R speed = Fn<R>::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-          make_ray<R>(ray, hp, v, (sizeof(R) == 4 ? (R)1e-6 : (R)1e-9) / speed);
-          trav_begin(tv);
-          tdone = a.mesh.n_nodes == 0;
-          finish = false;
+          // The particle leaves from the side it arrived on.  When the whole
+          // mesh lies behind that side (to 1e-12 m) and it leaves at more than
+          // 0.01 in cos from the plane, nothing lies ahead of it beyond 1e-10 m,
+          // inside the shortest hit distance: it is done, without a traversal.
+          const R vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+          const R vn = v[0] * nrm[0] + v[1] * nrm[1] + v[2] * nrm[2];
+          const bool escapes = (exposed & (vn > (R)0 ? 1u : 2u)) != 0u && vn * vn > (R)1e-4 * vv;
+          if (!escapes) {
+            const R speed = Fn<R>::sqrt(vv);
+            make_ray<R>(ray, hp, v, (sizeof(R) == 4 ? (R)1e-6 : (R)1e-9) / speed);
+            trav_begin(tv);
+            tdone = a.mesh.n_nodes == 0;
+            finish = false;
+          }
         }
       }
       if (finish) {

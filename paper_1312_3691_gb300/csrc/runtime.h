@@ -24,7 +24,7 @@ struct MeshRec {
   void* d_block = nullptr;     // one device allocation holding every mesh array
   size_t bytes = 0;
   double center[3] = {0, 0, 0}, radius = 0;
-  uint32_t depth = 0, leaf_max = 0, n_skipped = 0, n_vert = 0;
+  uint32_t depth = 0, leaf_max = 0, n_skipped = 0, n_vert = 0, n_exposed = 0;
   std::vector<double> h_xyz;   // host copy for the control-volume containment check
   std::vector<uint32_t> h_tri;
   int in_use = 0;              // queries in flight on this mesh (serving)

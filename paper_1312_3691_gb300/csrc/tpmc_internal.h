@@ -43,8 +43,8 @@ struct MeshDev {
   const float4* nodes = nullptr;    // [n_nodes][4]
   const float4* tris = nullptr;     // [n_tri_leaf][3]: (v0, id bits), (v1, 0), (v2, 0)
   const double* tris64 = nullptr;   // [n_tri_leaf][12]: v0, v1, v2, id, 0, 0
-  const float4* frames = nullptr;   // [n_tri][2] by input index: (n, area), (t1, 0)
-  const double* frames64 = nullptr; // [n_tri][8] by input index: n, area, t1, 0
+  const float4* frames = nullptr;   // [n_tri][2] by input index: (n, area), (t1, exposed-side bits)
+  const double* frames64 = nullptr; // [n_tri][8] by input index: n, area, t1, exposed-side bits
   uint32_t n_nodes = 0;
   uint32_t n_tri = 0;               // input numbering (panel arrays use it)
   uint32_t n_tri_leaf = 0;          // triangles referenced by leaves (zero-area ones dropped)
@@ -175,12 +175,13 @@ int trace_max_blocks_per_sm(uint32_t variant, const LaunchCfg& cfg, uint32_t n_n
 struct BvhBuild {
   std::size_t n_nodes = 0;
   uint32_t depth = 0, leaf_max = 0, n_skipped = 0;
+  uint32_t n_exposed = 0;    // triangle sides the whole mesh lies behind
   // host copies ready for upload
   float* nodes = nullptr;    // [n_nodes * 16]
   float* tris = nullptr;     // [n_leaf_tris * 12]
   double* tris64 = nullptr;  // [n_leaf_tris * 12]
-  float* frames = nullptr;   // [n_tri * 8]
-  double* frames64 = nullptr;// [n_tri * 8]
+  float* frames = nullptr;   // [n_tri * 8]: n, area, t1, exposed-side bits (uint32 in word 7)
+  double* frames64 = nullptr;// [n_tri * 8]: n, area, t1, exposed-side bits (as a double in word 7)
   uint32_t n_leaf_tris = 0;
   double center[3] = {0, 0, 0}, radius = 0;
   void release();

@@ -72,7 +72,7 @@ class tpmc_mesh_stats(ctypes.Structure):
         ("n_tri", ctypes.c_uint32), ("n_vert", ctypes.c_uint32), ("n_nodes", ctypes.c_uint32),
         ("depth", ctypes.c_uint32), ("n_skipped", ctypes.c_uint32), ("leaf_max", ctypes.c_uint32),
         ("bound_center", _D3), ("bound_radius", ctypes.c_double), ("device_bytes", ctypes.c_uint64),
-        ("n_refs", ctypes.c_uint32), ("pad_", ctypes.c_uint32),
+        ("n_refs", ctypes.c_uint32), ("n_exposed", ctypes.c_uint32),
     ]
 
 

@@ -8,14 +8,16 @@
 // lower triangle index.  A tree that loses any part of a triangle (a spatial
 // split that drops a piece, a box that does not contain its part) shows up as
 // a ray whose two answers differ.  Also checks that every triangle with
-// nonzero area is referenced by some leaf and that leaves respect the size
+// nonzero area is referenced by some leaf, that leaves respect the size
 // limit (more than max_leaf only where the depth limit stops the build, and
-// never more than 127).
+// never more than 127), and that every triangle side marked exposed has the
+// whole mesh behind its plane.
 //
 // usage: bvh_check MESH RAYS MAX_LEAF
 //   MESH: uint32 n_vert, uint32 n_tri, double xyz[n_vert][3], uint32 tri[n_tri][3]
 //   RAYS: uint32 n_rays, double ray[n_rays][6] (origin, direction)
 // prints one line: rays mismatches hits n_tri n_refs n_nodes depth leaf_max unreferenced oversized
+//                  exposed wrong_exposed
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -121,6 +123,27 @@ int main(int argc, char** argv) {
       if (code < 0 && ((~(uint32_t)code) >> 24) > 127u) ++oversized;
     }
 
+  // exposed sides: a side marked in the frame's word 7 has no vertex more
+  // than 1e-12 m in front of its plane (brute force over all vertices)
+  uint32_t exposed = 0, wrong_exposed = 0;
+  for (uint32_t t = 0; t < nt; ++t) {
+    const double* f = b.frames64 + 8 * (size_t)t;
+    const uint32_t bits = (uint32_t)f[7];
+    uint32_t fbits;
+    std::memcpy(&fbits, b.frames + 8 * (size_t)t + 7, 4);
+    if (fbits != bits) ++wrong_exposed;
+    const double* a = vert(t, 0);
+    for (int side = 0; side < 2; ++side) {
+      if (!((bits >> side) & 1u)) continue;
+      ++exposed;
+      const double sg = side == 0 ? 1.0 : -1.0;
+      for (uint32_t v = 0; v < nv; ++v) {
+        const double* p = xyz.data() + 3 * (size_t)v;
+        if (sg * (f[0] * (p[0] - a[0]) + f[1] * (p[1] - a[1]) + f[2] * (p[2] - a[2])) > 1e-12) { ++wrong_exposed; break; }
+      }
+    }
+  }
+
   uint64_t mismatches = 0, hits = 0;
   for (uint32_t r = 0; r < nr; ++r) {
     const double* o = rays.data() + 6 * (size_t)r;
@@ -167,8 +190,8 @@ int main(int argc, char** argv) {
     if (brute.id != 0xFFFFFFFFu) ++hits;
     if (brute.id != walk.id || !(brute.t == walk.t || (std::isinf(brute.t) && std::isinf(walk.t)))) ++mismatches;
   }
-  std::printf("%u %llu %llu %u %u %zu %u %u %u %u\n", nr, (unsigned long long)mismatches, (unsigned long long)hits, nt,
-              b.n_leaf_tris, b.n_nodes, b.depth, b.leaf_max, unreferenced, oversized);
+  std::printf("%u %llu %llu %u %u %zu %u %u %u %u %u %u\n", nr, (unsigned long long)mismatches, (unsigned long long)hits,
+              nt, b.n_leaf_tris, b.n_nodes, b.depth, b.leaf_max, unreferenced, oversized, exposed, wrong_exposed);
   b.release();
   return 0;
 }

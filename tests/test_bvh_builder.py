@@ -71,7 +71,7 @@ def _check(checker, tmp_path, xyz, tri, rays, leaf=4):
     ray.write_bytes(np.array([len(rays)], np.uint32).tobytes() + np.ascontiguousarray(rays, np.float64).tobytes())
     out = subprocess.check_output([str(checker), str(mesh), str(ray), str(leaf)], text=True).split()
     keys = ["rays", "mismatches", "hits", "n_tri", "n_refs", "n_nodes", "depth", "leaf_max", "unreferenced",
-            "oversized"]
+            "oversized", "exposed", "wrong_exposed"]
     return dict(zip(keys, (int(x) for x in out)))
 
 
@@ -116,6 +116,34 @@ def test_tree_closest_hits_equal_brute_force(checker, tmp_path, name):
     assert r["unreferenced"] == 0 and r["oversized"] == 0, r
     assert r["hits"] > 0.2 * r["rays"], r
     assert len(tri) - 1 <= r["n_refs"] <= 1.5 * len(tri) + 1, r
+    assert r["wrong_exposed"] == 0, r
+    assert r["exposed"] == EXPOSED[name](len(tri)), r
+
+
+# Exposed triangle sides (the whole mesh behind the side's plane): one side of
+# every face of a closed convex body or of the hemisphere's outside, both sides
+# of the flat plate and of the flat fan; of the satellite, the bus faces that
+# neither a panel nor the dish stands in front of; none of the soup.
+EXPOSED = {
+    "cylinder": lambda n: n, "icosphere": lambda n: n, "hemisphere": lambda n: n,
+    "plate": lambda n: 2 * n, "fan": lambda n: 2 * n, "soup": lambda n: 0,
+    "satellite": lambda n: _satellite_exposed(),
+}
+
+
+def _satellite_exposed():
+    """Sides of the satellite(8000) bus faces with nothing in front, counted
+    by brute force in numpy: independent of the builder."""
+    xyz, tri = M.satellite(8_000)
+    xyz, tri = np.asarray(xyz, float), np.asarray(tri)
+    a, b, c = (xyz[tri[:, k]] for k in range(3))
+    n = np.cross(b - a, c - a)
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    count = 0
+    for i in range(len(tri)):
+        d = (xyz - a[i]) @ n[i]
+        count += int(d.max() <= 1e-12) + int(d.min() >= -1e-12)
+    return count
 
 
 def test_spatial_splits_cut_the_fans(checker, tmp_path):
