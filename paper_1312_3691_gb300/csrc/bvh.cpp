@@ -489,7 +489,7 @@ bool build_bvh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t
     };
     const size_t n_prims = prims.size();
     const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    const size_t n_threads = n_prims < 4096 ? 1 : std::min<size_t>(hw, n_prims / 2048);
+    const size_t n_threads = n_prims < 1024 ? 1 : std::min<size_t>(hw, n_prims / 512);
     if (n_threads <= 1) {
       work(0, n_prims);
     } else {
