@@ -374,6 +374,17 @@ tpmc_status tpmc_mesh_load(tpmc_ctx* ctx, const double* xyz, uint32_t n_vert, co
   m.dev.frames = (const float4*)p_fr;
   m.dev.frames64 = (const double*)p_fr64;
   m.dev.n_nodes = (uint32_t)b.n_nodes;
+  for (uint32_t c = 0; c < 2 && b.n_nodes > 0; ++c) {  // the root box: union of the root's child boxes
+    const float* xy = b.nodes + 4 * c;
+    const float* z = b.nodes + 8 + 2 * c;
+    if (xy[0] > 1e29f) continue;  // empty child
+    const float lo[3] = {xy[0], xy[2], z[0]}, hi[3] = {xy[1], xy[3], z[1]};
+    const bool first = m.dev.box_lo[0] > m.dev.box_hi[0];
+    for (int k = 0; k < 3; ++k) {
+      m.dev.box_lo[k] = first ? lo[k] : std::min(m.dev.box_lo[k], lo[k]);
+      m.dev.box_hi[k] = first ? hi[k] : std::max(m.dev.box_hi[k], hi[k]);
+    }
+  }
   m.dev.n_tri = n_tri;
   m.dev.n_tri_leaf = b.n_leaf_tris;
   m.dev.scene_radius = (float)b.radius;

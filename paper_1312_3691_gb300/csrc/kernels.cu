@@ -954,6 +954,21 @@ __device__ __noinline__ void seed_into(const TraceArgs& a, uint32_t qi, uint64_t
 
 constexpr uint32_t kQueue = 64;     // queue slots per warp (two seeding batches)
 
+// Whether the ray meets the mesh's padded root box beyond tlo (the slab
+// arithmetic of the node test, so a ray rejected here misses every node).
+template <typename R>
+__device__ __forceinline__ bool ray_meets_box(const Ray<R>& r, const MeshDev& m) {
+  R tn = r.tlo, tf = (R)CUDART_INF;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    R a, b;
+    slab<R>((R)m.box_lo[i], (R)m.box_hi[i], r.inv[i], r.oi[i], a, b);
+    tn = fmax(tn, a);
+    tf = fmin(tf, b);
+  }
+  return tn <= tf;
+}
+
 // --------------------------------------------------------- trace kernel
 // Persistent kernel.  Each warp keeps a queue of seeded particles in shared
 // memory; when its lanes need particles and the queue runs low, all 32 lanes
@@ -1077,9 +1092,12 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
       }
     }
 
-    // ---- 2. idle lanes take particles from the queue; seed a batch when it runs low
-    const unsigned need = __ballot_sync(kFull, !has);
-    if (need != 0u) {
+    // ---- 2. idle lanes take particles from the queue; seed a batch when it runs low.
+    // A particle whose ray misses the mesh's root box is counted at once (its
+    // sums are zero) and the lane takes another, up to three times.
+    for (int pass = 0; pass < 3; ++pass) {
+      const unsigned need = __ballot_sync(kFull, !has);
+      if (need == 0u) break;
       const uint32_t n_need = __popc(need);
       if (q_count < n_need && !drained && q_count + 32u <= kQueue) {
         if (pool_rem == 0) {
@@ -1133,10 +1151,21 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
         bounce = 0;
         last = 0xFFFFFFFFu;
         dvp[0] = dvp[1] = dvp[2] = (R)0;
+        if (!ray_meets_box<R>(ray, a.mesh)) {
+          ++acc.particles;
+          if (a.rec.n_hits != nullptr) {
+            a.rec.n_hits[pid] = 0;
+            a.rec.truncated[pid] = 0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) a.rec.dv[3 * pid + i] = 0.0;
+          }
+          has = false;
+        }
       }
       q_head = (q_head + take) & (kQueue - 1);
       q_count -= take;
       __syncwarp();
+      if (take == 0) break;
     }
 
     // ---- 3. the warp is done when nothing is in flight and nothing is left to seed

@@ -49,6 +49,7 @@ struct MeshDev {
   uint32_t n_tri = 0;               // input numbering (panel arrays use it)
   uint32_t n_tri_leaf = 0;          // triangles referenced by leaves (zero-area ones dropped)
   float scene_radius = 1.0f;
+  float box_lo[3] = {0.0f, 0.0f, 0.0f}, box_hi[3] = {-1.0f, -1.0f, -1.0f};  // padded root box (empty: no mesh)
 };
 
 // ------------------------------------------------------------- query (device)
