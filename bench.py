@@ -693,6 +693,7 @@ def run_ours(args):
         extras["attitude_sweep"] = measure_attitude_sweep(T, ctx, torch, stream, dev)
         extras["serving"] = measure_serving(T, ctx, rate=100.0)
         extras["serving_high_load"] = measure_serving(T, ctx, rate=200.0)
+        extras["serving_saturated"] = measure_serving(T, ctx, rate=400.0)
     if rank == 0:
         cpu_base, cd_err, cd_other = (None, None, None)
         if not args.no_cpu_baseline:
