@@ -41,12 +41,15 @@ UNIT = "particles/s"
 WORKLOAD = "plate(2 tri)+cylinder(4096 tri) sweep: 32 alpha x S{2,5,10} x {specular,diffuse}, 1e7 particles/case"
 N_EACH = 10_000_000
 FP32_LANES_PER_SM = 128
-# Algorithmic FP32 work per unit (FMA = 2 flops; add, mul, min, max, compare = 1).
-FLOPS_PER_NODE_VISIT = 50    # two child boxes: 6 FMA + 6 min/max + 6 min/max + 1 compare each
-FLOPS_PER_TRI_TEST = 45      # watertight test: 9 sub, 6 FMA, 9 mul/sub, 5 det/T, signs, 1 div
-FLOPS_PER_PARTICLE = 300     # seeding: two inverse-CDF solves, Box-Muller, rotations
-FLOPS_PER_HIT = 60           # re-emission, momentum difference, torque, quantisation
-BYTES_PER_NODE_VISIT = 64    # one BVH node: both child boxes and child codes
+# Algorithmic work per unit of BVH ray casting (FMA = 2 flops; add, mul, min,
+# max, compare = 1).  A node visit tests each of its child boxes (the node's
+# width: 2 for the binary tree, up to 8 for the compressed wide tree) and reads
+# the node once (64 B binary, 80 B compressed wide); the counts of node visits
+# and triangle tests are measured per run.
+FLOPS_PER_CHILD_BOX = 20     # slab test of one child box: 6 FMA + 8 min/max/compare
+FLOPS_PER_TRI_TEST = 35      # watertight test: translate, shear, 3 edge functions, det, T
+FLOPS_PER_PARTICLE = 150     # seeding: two inverse-CDF solves, Box-Muller, two rotations
+FLOPS_PER_HIT = 30           # re-emission, momentum difference, torque, quantisation
 BYTES_PER_TRI_TEST = 48      # three float4 vertices
 # DRAM bytes per trace launch from an ncu capture, valid only for the kernel
 # source and the BVH builder it was taken with (keyed by the SHA-256 of
@@ -150,6 +153,61 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def roofline_of(parts, seconds: float, ceil: dict) -> dict:
+    """The trace kernel's roofline for one measured run: particles/s against
+    min(B_L2 / bytes per particle, P_FP32 / flops per particle), with B_L2 and
+    P_FP32 the ceilings measured on this device (tpmc_measure_ceilings).  The
+    kernel reads nodes and triangles that stay in L1/L2, so L2 bandwidth, not
+    HBM, is the memory ceiling.  `parts` lists (work, node bytes, BVH width) of
+    the launches timed together in `seconds`; `achieved` is in the binding
+    ceiling's unit."""
+    tot = {"particles": 0, "hits": 0, "nodes": 0, "tris": 0}
+    flops = l2_bytes = 0.0
+    widths = set()
+    for work, node_bytes, width in parts:
+        for k in tot:
+            tot[k] += work[k]
+        flops += (FLOPS_PER_CHILD_BOX * width * work["nodes"] + FLOPS_PER_TRI_TEST * work["tris"] +
+                  FLOPS_PER_PARTICLE * work["particles"] + FLOPS_PER_HIT * work["hits"])
+        l2_bytes += node_bytes * work["nodes"] + BYTES_PER_TRI_TEST * work["tris"]
+        widths.add((width, node_bytes))
+    n = max(tot["particles"], 1)
+    fpp, bpp = flops / n, l2_bytes / n
+    rate = tot["particles"] / seconds
+    bound_l2 = ceil["l2_read_gbs"] * 1e9 / max(bpp, 1e-30)
+    bound_fp32 = ceil["fp32_tflops"] * 1e12 / max(fpp, 1e-30)
+    if bound_l2 <= bound_fp32:
+        out = {"bound": "l2", "achieved": rate * bpp / 1e9, "peak": ceil["l2_read_gbs"], "unit": "GB/s"}
+    else:
+        out = {"bound": "fp32", "achieved": rate * fpp / 1e12, "peak": ceil["fp32_tflops"], "unit": "TFLOP/s"}
+    out["frac"] = rate / min(bound_l2, bound_fp32)
+    out.update({
+        "particles_per_s": rate, "flops_per_particle": fpp, "bytes_per_particle": bpp, "work": tot,
+        "node_visits_per_particle": tot["nodes"] / n, "tri_tests_per_particle": tot["tris"] / n,
+        "hits_per_particle": tot["hits"] / n,
+        "bvh": [{"width": w, "node_bytes": b} for w, b in sorted(widths)],
+        "particles_per_s_l2_bound": bound_l2, "particles_per_s_fp32_bound": bound_fp32,
+        "fp32_frac": rate * fpp / (ceil["fp32_tflops"] * 1e12), "l2_frac": rate * bpp / (ceil["l2_read_gbs"] * 1e9),
+        "ceilings": {"l2_read_gbs": ceil["l2_read_gbs"], "fp32_tflops": ceil["fp32_tflops"],
+                     "basis": "measured on this device: L2-resident streaming read (32 MiB, 64 passes, L1 "
+                              "bypassed) and an FP32 FMA loop, best of 5 (tpmc_measure_ceilings)"},
+        "units": {"flops_per_child_box": FLOPS_PER_CHILD_BOX, "flops_per_tri_test": FLOPS_PER_TRI_TEST,
+                  "flops_per_particle": FLOPS_PER_PARTICLE, "flops_per_hit": FLOPS_PER_HIT,
+                  "bytes_per_tri_test": BYTES_PER_TRI_TEST},
+    })
+    return out
+
+
+def work_of(results) -> dict:
+    w = {"particles": 0, "hits": 0, "nodes": 0, "tris": 0}
+    for r in results:
+        w["particles"] += r["n_particles"]
+        w["hits"] += r["n_hits"]
+        w["nodes"] += r["n_node_visits"]
+        w["tris"] += r["n_tri_tests"]
+    return w
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -244,6 +302,64 @@ def other_configs_vs_oracle(T, ctx):
     return out
 
 
+def parity_excused_shares(T, ctx):
+    """Path parity on the same Philox streams for C1-C4 (after the timed region):
+    the share of particles whose hit paths differ from the oracle's after a
+    near-edge or grazing hit (excused), binned by the bounce where they first
+    differ, the count that differ away from edges (must be 0), and the FP32
+    momentum parity of the identical-path particles."""
+    import oracle
+
+    from tests.parity_util import dv_parity, path_stats
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    K = 16
+    c_mp = (2 * W.K_B * 1000.0 / W.M_OXYGEN) ** 0.5
+    cases = []
+    c1 = W.icosphere_case(N=100_000)
+    cases.append(("C1_icosphere_fp64", c1["xyz"], c1["tri"], [(c1["params"], T.TPMC_FP64, 0, 100_000)]))
+    for shape in ("plate", "cylinder"):
+        xyz, tri, cs = W.sweep_cases(shape, N_each=N_EACH, n_alpha=32)
+        runs = [(cs[i]["params"], T.TPMC_FP32, 0, 50_000) for i in (len(cs) - 20, 45)]
+        cases.append((f"C2_{shape}_fp32", xyz, tri, runs))
+    c3 = W.satellite_case(N=1)
+    cases.append(("C3_satellite_fp32", c3["xyz"], c3["tri"], [(c3["params"], T.TPMC_FP32, 0, 100_000)]))
+    grid = W.attitude_grid(32, 32)
+    runs = []
+    for k in (5, 300, 517, 1000):
+        pk = dict(c3["params"], dir=tuple(grid[k]), V=7.5 * c_mp)
+        runs.append((pk, T.TPMC_FP32, (1 << 20) + 1024 + k, 25_000))
+    cases.append(("C4_attitude_items_fp32", c3["xyz"], c3["tri"], runs))
+    out = {}
+    for name, xyz, tri, runs in cases:
+        mesh = T.tpmc_mesh_load(ctx, xyz, tri)
+        om = oracle.Mesh(xyz, tri)
+        agg = {"n": 0, "identical": 0, "excused": 0, "unexplained": 0, "excused_by_bounce": [0] * K}
+        dvs = []
+        try:
+            for params, prec, stream, n in runs:
+                _, rec = T.tpmc_trace_records(ctx, mesh, T.make_params(**params, precision=prec, stream_id=stream),
+                                              n, K=K)
+                _, _, orec = oracle.trace(om, oracle.make_params(**params, stream=stream, threads=threads), n,
+                                          records=True, K=K)
+                st = path_stats(rec, orec, K)
+                for k in ("n", "identical", "excused", "unexplained"):
+                    agg[k] += st[k]
+                agg["excused_by_bounce"] = [a + b for a, b in zip(agg["excused_by_bounce"], st["excused_by_bounce"])]
+                dvs.append(dv_parity(rec, orec, st["_identical_mask"], params["dir"]))
+        finally:
+            T.tpmc_mesh_unload(ctx, mesh)
+        agg["excused_share"] = agg["excused"] / max(agg["n"], 1)
+        last = max([i for i, x in enumerate(agg["excused_by_bounce"]) if x] or [0])
+        agg["excused_by_bounce"] = agg["excused_by_bounce"][:last + 1]
+        agg["dv_identical_paths"] = {"median_rel_max": max(d.get("median_rel", 0.0) for d in dvs),
+                                     "p99_rel_max": max(d.get("p99_rel", 0.0) for d in dvs),
+                                     "drag_rel_max": max(d["drag_rel"] for d in dvs)}
+        out[name] = agg
+    return out
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle timed as it stands on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -294,23 +410,38 @@ def run_reference(args):
 
 
 # ----------------------------------------------------- other configurations
-def measure_satellite(T, ctx):
-    """Concave synthetic satellite (60,656 triangles), 1e8 particles, <= 64 bounces,
-    Maxwell 0.9 diffuse, per-panel pressure and shear (host API, wall clock)."""
-    case = W.satellite_case(N=100_000_000)
+def measure_satellite(T, ctx, torch, stream, ceil, target_triangles=60_000):
+    """Concave synthetic satellite (60,656 or 503,537 triangles), 1e8 particles,
+    <= 64 bounces, Maxwell 0.9 diffuse, per-panel pressure and shear: the host
+    API's wall clock, and CUDA events on the library's stream around the same
+    call for the roofline (work counted in a separate pass of the same query)."""
+    case = W.satellite_case(N=100_000_000, target_triangles=target_triangles)
     mesh = T.tpmc_mesh_load(ctx, case["xyz"], case["tri"])
+    info = T.tpmc_mesh_info(ctx, mesh)
     try:
+        T.tpmc_set_stream(ctx, stream)
         p = T.make_params(**case["params"], want_panels=True)
         T.tpmc_trace(ctx, mesh, T.make_params(**case["params"]), 1_000_000)  # warm-up
+        T.tpmc_set_counters(ctx, True)
+        rc = T.tpmc_trace(ctx, mesh, T.make_params(**case["params"]), case["N"])
+        T.tpmc_set_counters(ctx, False)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
         r = T.tpmc_trace(ctx, mesh, p, case["N"])
+        b.record(stream)
+        torch.cuda.synchronize()
+        gpu_ms = a.elapsed_time(b)
         pres, shear = T.tpmc_panels(ctx, r["query_id"], case["tri"].shape[0])
     finally:
         T.tpmc_mesh_unload(ctx, mesh)
+    assert rc["sum_dv_q"] == r["sum_dv_q"]
     return {"workload": case["name"] + ", 1e8 particles, <=64 bounces, eps 0.9, panels",
-            "particles_per_s": case["N"] / (r["ms"] / 1e3), "ms": r["ms"], "CD": r["CD"], "CD_sigma": r["CD_sigma"],
+            "particles_per_s": case["N"] / (r["ms"] / 1e3), "ms": r["ms"], "gpu_ms": gpu_ms,
+            "CD": r["CD"], "CD_sigma": r["CD_sigma"],
             "torque_Nm": r["torque"], "hits_per_particle": r["n_hits"] / r["n_particles"],
             "truncated": r["n_truncated"], "max_abs_pressure_Pa": float(np.abs(pres).max()),
-            "max_shear_Pa": float(shear.max())}
+            "max_shear_Pa": float(shear.max()),
+            "roofline": roofline_of([(work_of([rc]), info["node_bytes"], info["bvh_width"])], gpu_ms / 1e3, ceil)}
 
 
 def measure_hemisphere(T, ctx):
@@ -416,7 +547,7 @@ def measure_moment_sweep(T, ctx, torch, stream, dev):
             "max_CD_sigma_rel": max(r["CD_sigma"] / r["CD"] for r in res)}
 
 
-def measure_attitude_sweep(T, ctx, torch, stream, dev):
+def measure_attitude_sweep(T, ctx, torch, stream, dev, ceil):
     """32 x 32 yaw/pitch grid x S in {5, 7.5, 10} on the satellite, 2^20 particles per
     item: one persistent launch against 3,072 one-query launches (same N, so equal
     C_D error)."""
@@ -440,6 +571,14 @@ def measure_attitude_sweep(T, ctx, torch, stream, dev):
         torch.cuda.synchronize(dev)
         batched_ms = a.elapsed_time(b)
         res = T.results_from_bytes(out.cpu().numpy().tobytes(), K)
+        T.tpmc_set_counters(ctx, True)
+        T.tpmc_sweep_device(ctx, mesh, base, dd, ds, K, N_each, out)
+        torch.cuda.synchronize(dev)
+        T.tpmc_set_counters(ctx, False)
+        res_c = T.results_from_bytes(out.cpu().numpy().tobytes(), K)
+        assert all(x["sum_dv_q"] == y["sum_dv_q"] for x, y in zip(res, res_c))
+        info = T.tpmc_mesh_info(ctx, mesh)
+        roof = roofline_of([(work_of(res_c), info["node_bytes"], info["bvh_width"])], batched_ms / 1e3, ceil)
         T.tpmc_set_stream(ctx, None)
         c_mp = (2 * W.K_B * case["params"]["T_inf"] / case["params"]["m"]) ** 0.5
         t0 = time.perf_counter()
@@ -480,6 +619,7 @@ def measure_attitude_sweep(T, ctx, torch, stream, dev):
             "batched_particles_per_s": n / (batched_ms / 1e3), "batched_ms": batched_ms,
             "plain_particles_per_s": n / plain_s, "plain_ms": 1e3 * plain_s,
             "speedup_vs_plain": plain_s / (batched_ms / 1e3), "items_bit_identical_to_plain": same, "items": K,
+            "roofline": roof,
             "median_CD_sigma_rel": float(np.median([r["CD_sigma"] / r["CD"] for r in res]))}
 
 
@@ -600,16 +740,16 @@ def run_ours(args):
     step()
     torch.cuda.synchronize(dev)
     T.tpmc_set_counters(ctx, False)
-    work = {"particles": 0, "hits": 0, "nodes": 0, "tris": 0}
+    group_work = []
     for (_, _, _, _, out) in d_in:
-        for r in T.results_from_bytes(out.cpu().numpy().tobytes(), K):
-            assert r["status"] == 0, r
-            work["particles"] += r["n_particles"]
-            work["hits"] += r["n_hits"]
-            work["nodes"] += r["n_node_visits"]
-            work["tris"] += r["n_tri_tests"]
-    flops_per_step = (FLOPS_PER_NODE_VISIT * work["nodes"] + FLOPS_PER_TRI_TEST * work["tris"] +
-                      FLOPS_PER_PARTICLE * work["particles"] + FLOPS_PER_HIT * work["hits"])
+        res = T.results_from_bytes(out.cpu().numpy().tobytes(), K)
+        assert all(r["status"] == 0 for r in res), res
+        group_work.append(work_of(res))
+    work = work_of([])
+    for w in group_work:
+        for k in work:
+            work[k] += w[k]
+    mesh_info = {shape: T.tpmc_mesh_info(ctx, mid) for shape, mid in mesh_ids.items()}
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -666,39 +806,38 @@ def run_ours(args):
 
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    launch_avg_ms = statistics.mean(launch_ms)
-    flops_per_launch = flops_per_step / len(d_in)
-    achieved = flops_per_launch / (launch_avg_ms / 1e3) / 1e12
+    alu_peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     traffic = TRACE_TRAFFIC.get(kernel_source_hash())
-    # measured ceilings: particles/s <= min(FP32 rate / flops per particle, L2 rate / bytes per particle)
+    # measured ceilings: particles/s <= min(L2 rate / bytes per particle, FP32 rate / flops per particle)
     ceil = T.tpmc_measure_ceilings(ctx)
-    fpp = flops_per_step / particles_step
-    bpp = (BYTES_PER_NODE_VISIT * work["nodes"] + BYTES_PER_TRI_TEST * work["tris"]) / particles_step
-    bound_fp32 = ceil["fp32_tflops"] * 1e12 / fpp
-    bound_l2 = ceil["l2_read_gbs"] * 1e9 / bpp
-    rate_gpu = particles_step / (t_step / 1e3)
-    ceilings = {"fp32_tflops_measured": ceil["fp32_tflops"], "l2_read_gbs_measured": ceil["l2_read_gbs"],
-                "flops_per_particle": fpp, "l2_bytes_per_particle": bpp,
-                "particles_per_s_fp32_bound": bound_fp32, "particles_per_s_l2_bound": bound_l2,
-                "binding": "fp32" if bound_fp32 <= bound_l2 else "l2",
-                "frac": rate_gpu / min(bound_fp32, bound_l2)}
-
+    mean_step_s = statistics.mean(step_ms) / 1e3
+    parts = [(w, mesh_info[g["shape"]]["node_bytes"], mesh_info[g["shape"]]["bvh_width"])
+             for w, g in zip(group_work, gs)]
+    roof = roofline_of(parts, mean_step_s, ceil)
+    roof.update({"traffic": traffic, "kernel": "trace_kernel<float>",
+                 "achieved_definition": "algorithmic L2 bytes (node and triangle reads) per launch / mean launch "
+                                        "duration (CUDA events on the launching stream)",
+                 "launch_ms_mean": statistics.mean(launch_ms),
+                 "fp32_alu_derived_tflops": alu_peak_tflops,
+                 "fp32_alu_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 (FMA) x "
+                                   f"{sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"})
     extras = {}
     if rank == 0 and not args.no_extras:
-        extras["satellite"] = measure_satellite(T, ctx)
+        extras["satellite"] = measure_satellite(T, ctx, torch, stream, ceil)
+        extras["satellite_500k"] = measure_satellite(T, ctx, torch, stream, ceil, target_triangles=500_000)
         extras["concave_hemisphere"] = measure_hemisphere(T, ctx)
         extras["box_cv"] = measure_box_cv(T, ctx)
         extras["moment_sweep"] = measure_moment_sweep(T, ctx, torch, stream, dev)
-        extras["attitude_sweep"] = measure_attitude_sweep(T, ctx, torch, stream, dev)
+        extras["attitude_sweep"] = measure_attitude_sweep(T, ctx, torch, stream, dev, ceil)
         extras["serving"] = measure_serving(T, ctx, rate=100.0)
         extras["serving_high_load"] = measure_serving(T, ctx, rate=200.0)
         extras["serving_saturated"] = measure_serving(T, ctx, rate=400.0)
     if rank == 0:
-        cpu_base, cd_err, cd_other = (None, None, None)
+        cpu_base, cd_err, cd_other, parity = (None, None, None, None)
         if not args.no_cpu_baseline:
             cpu_base, cd_err = cpu_baseline_and_cd_error(results_by_group)
             cd_other = other_configs_vs_oracle(T, ctx)
+            parity = parity_excused_shares(T, ctx)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
@@ -710,15 +849,10 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_t, "includes": "mesh upload + BVH build, host inputs, host results"},
             "gpu_launches": args.steps * len(d_in) * 3,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved / peak_tflops, "traffic": traffic,
-                         "kernel": "trace_kernel<float>",
-                         "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
-                                       f"(FMA) x {sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
-                         "work_per_step": work, "ceilings_measured": ceilings},
+            "roofline": roof,
             "clocks": clocks,
             "cpu_baseline": cpu_base,
-            "cd_error": cd_err, "cd_error_other_configs": cd_other,
+            "cd_error": cd_err, "cd_error_other_configs": cd_other, "parity": parity,
             "serve": {k: extras["serving"][k] for k in ("p50_ms", "p99_ms", "throughput_particles_per_s", "plain")}
             if "serving" in extras else None,
             "extras": extras,

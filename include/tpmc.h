@@ -169,6 +169,9 @@ typedef struct {
                                 /* put parts of some triangles in several leaves         */
   uint32_t n_exposed;           /* triangle sides with the whole mesh behind them: a    */
                                 /* particle re-emitted from one is not traced further    */
+  uint32_t bvh_width;           /* children per BVH node: 2 (binary, 64-byte nodes) or  */
+                                /* 4 / 8 (compressed wide nodes of 80 bytes)             */
+  uint32_t node_bytes;          /* bytes the trace kernel reads per node visit           */
 } tpmc_mesh_stats;
 
 /* Launch schedule of the trace kernel (chosen by tpmc_tune or set by hand). */
@@ -197,6 +200,12 @@ tpmc_status tpmc_set_stream(tpmc_ctx* ctx, void* cuda_stream);
 
 /* Thread-local message describing the last failure on this thread. */
 const char* tpmc_last_error(const tpmc_ctx* ctx);
+
+/* Device memory of the context: *used, the bytes it holds through its own
+ * allocations (meshes and their BVHs, scratch, panel buffers, serving slots),
+ * *budget, the limit set at creation, and *n_allocs, the number of device
+ * allocations it has made since creation.  Any pointer may be NULL. */
+tpmc_status tpmc_memory_info(tpmc_ctx* ctx, size_t* used, size_t* budget, uint64_t* n_allocs);
 
 /* Enables (1) or disables (0) the traversal counters n_node_visits and
  * n_tri_tests in later results. */
@@ -271,7 +280,9 @@ tpmc_status tpmc_sweep_device(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_param
  * real-time control loops, code whose device memory belongs to a framework's
  * own pool, or code that must keep a fixed footprint).  Same inputs and
  * results as tpmc_sweep with host buffers (h_dirs [K][3], h_S [K] or NULL,
- * h_out [K]); per-panel loads are not kept.  Its scratch is one fixed device
+ * h_out [K]) and the same behaviour: an item rejected by its set-up reports
+ * that in h_out[k].status, and h_out[k].ms is the call's wall time; per-panel
+ * loads are not kept.  Its scratch is one fixed device
  * array of the library (64 queries, about 100 KB), held by every GPU that
  * loads the library until the process exits.  The first call on a device
  * looks up that array's device address (cudaGetSymbolAddress, which also

@@ -41,6 +41,7 @@ tpmc_status Ctx::alloc(void** p, size_t bytes, const char* what) {
   }
   sizes[*p] = bytes;
   used += bytes;
+  ++n_allocs;
   return TPMC_OK;
 }
 
@@ -98,6 +99,10 @@ tpmc_status fill_query(const MeshRec& m, const tpmc_params* p, uint64_t N, Query
   q->n = p->n; q->T_inf = p->T_inf; q->m = p->m; q->V = p->V;
   for (int i = 0; i < 3; ++i) { q->dir[i] = p->dir[i]; q->ref[i] = p->ref_point[i]; }
   q->T_W = p->T_W; q->eps = p->eps_diffuse; q->A_ref = p->A_ref;
+  // The Maxwell choice u < eps on the uniform u = (k + 1/2) 2^-23 of a draw's
+  // top 23 bits k holds exactly when k < eps 2^23 - 1/2, i.e. k < ceil(eps 2^23 - 1/2)
+  // (eps 2^23 - 1/2 is exact in double), so the kernel decides in integers.
+  q->eps_k = (uint32_t)std::min(8388608.0, std::max(0.0, std::ceil(p->eps_diffuse * 8388608.0 - 0.5)));
   q->l_ref = p->l_ref > 0.0 ? p->l_ref : 1.0;
   q->cv_kind = p->cv_kind;
   q->gsi_model = p->gsi_model;
@@ -318,6 +323,16 @@ tpmc_status tpmc_set_stream(tpmc_ctx* ctx, void* cuda_stream) {
 
 const char* tpmc_last_error(const tpmc_ctx*) { return g_last_error.c_str(); }
 
+tpmc_status tpmc_memory_info(tpmc_ctx* ctx, size_t* used, size_t* budget, uint64_t* n_allocs) {
+  if (!ctx) return fail(TPMC_EINVAL, "ctx is NULL");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  if (used) *used = c->used;
+  if (budget) *budget = c->budget;
+  if (n_allocs) *n_allocs = c->n_allocs;
+  return TPMC_OK;
+}
+
 tpmc_status tpmc_set_counters(tpmc_ctx* ctx, int enable) {
   if (!ctx) return fail(TPMC_EINVAL, "ctx is NULL");
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
@@ -438,6 +453,8 @@ tpmc_status tpmc_mesh_info(tpmc_ctx* ctx, tpmc_mesh_id mesh, tpmc_mesh_stats* ou
   out->device_bytes = m.bytes;
   out->n_refs = m.dev.n_tri_leaf;
   out->n_exposed = m.n_exposed;
+  out->bvh_width = 2;
+  out->node_bytes = 64;
   return TPMC_OK;
 }
 

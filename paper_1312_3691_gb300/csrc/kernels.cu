@@ -522,6 +522,19 @@ __device__ __forceinline__ double edge_fn(double a, double b, double c, double d
   return __dsub_rn(__dmul_rn(a, b), __dmul_rn(c, d));
 }
 
+// a b - c d in float with the sign of the exact value, and exactly 0 when
+// a b = c d: Kahan's algorithm, w = c d, e = w - c d (exact by an FMA),
+// f = round(a b - w), result f + e, whose relative error is at most two units
+// in the last place (Jeannerod, Louvet & Muller, Math. Comp. 2013).  It
+// decides the watertight test's ties in float where the plain edge function
+// rounds to 0.
+__device__ __forceinline__ float edge_fn_exact(float a, float b, float c, float d) {
+  const float w = __fmul_rn(c, d);
+  const float e = __fmaf_rn(-c, d, w);
+  const float f = __fmaf_rn(a, b, -w);
+  return __fadd_rn(f, e);
+}
+
 template <typename R>
 struct Ray {
   R o[3], d[3], inv[3], oi[3];
@@ -577,11 +590,13 @@ __device__ __forceinline__ void test_triangle(const Ray<R>& r, const Shear<R>& s
   R U = edge_fn(Cx, By, Cy, Bx);
   R V = edge_fn(Ax, Cy, Ay, Cx);
   R W = edge_fn(Bx, Ay, By, Ax);
-  if (sizeof(R) == 4 && (U == (R)0 || V == (R)0 || W == (R)0)) {
-    // exact-product fallback in double on the edge itself
-    U = (R)((double)Cx * (double)By - (double)Cy * (double)Bx);
-    V = (R)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
-    W = (R)((double)Bx * (double)Ay - (double)By * (double)Ax);
+  if constexpr (sizeof(R) == 4) {
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+      // the ray meets an edge or a vertex to float rounding: the exact signs decide
+      U = edge_fn_exact(Cx, By, Cy, Bx);
+      V = edge_fn_exact(Ax, Cy, Ay, Cx);
+      W = edge_fn_exact(Bx, Ay, By, Ax);
+    }
   }
   if ((U < (R)0 || V < (R)0 || W < (R)0) && (U > (R)0 || V > (R)0 || W > (R)0)) return;
   R det = U + V + W;
@@ -811,7 +826,7 @@ __device__ __forceinline__ void reemit(const QueryDev& q, R cw, uint64_t pid, ui
       return;
     }
   }
-  if (uniform<double>(w.x) < q.eps) {
+  if ((w.x >> 9) < q.eps_k) {  // u < eps, decided on the integer behind u
     const R sgn = vdn < (R)0 ? (R)1 : (R)-1;
     const R vn = cw * Fn<R>::sqrt(-Fn<R>::log(uniform<R>(w.y)));
     const R vt = cw * Fn<R>::sqrt(-Fn<R>::log(uniform<R>(w.z)));
@@ -832,20 +847,33 @@ __device__ __forceinline__ long long quantize(double x) { return __double2ll_rn(
 // Per-lane partial sums for the query the lane is working on.  They live in
 // shared memory (one slot per thread), which keeps them out of the registers
 // the traversal needs.
+// d2lo and d2hi hold the lane's sum of squared drag contributions as the
+// 96-bit integer d2hi 2^64 + d2lo (units of the query's quantum2).
 struct LaneAcc {
   long long F[3], T[3];
-  double d2;
+  unsigned long long d2lo;
   uint32_t hits, hit_particles, truncated, particles;
   int q;
-  uint32_t pad;
+  uint32_t d2hi;
 };
 
 __device__ __forceinline__ void lane_reset(LaneAcc& a, int q) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) { a.F[i] = 0; a.T[i] = 0; }
   a.hits = a.hit_particles = a.truncated = a.particles = 0;
-  a.d2 = 0.0;
+  a.d2lo = 0;
+  a.d2hi = 0;
   a.q = q;
+}
+
+// Adds one particle's squared drag contribution d^2 (c_mp^2 units), rounded to
+// the query's quantum2; the set-up bounds every particle's term below 2^62.
+__device__ __forceinline__ unsigned long long quantize_sq(float x) { return __float2ull_rn(x); }
+__device__ __forceinline__ unsigned long long quantize_sq(double x) { return __double2ull_rn(x); }
+__device__ __forceinline__ void lane_add_d2(LaneAcc& a, unsigned long long x) {
+  const unsigned long long lo = a.d2lo + x;
+  a.d2hi += lo < x ? 1u : 0u;
+  a.d2lo = lo;
 }
 
 __device__ __forceinline__ void lane_flush(AccDev* acc, LaneAcc& a) {
@@ -860,7 +888,13 @@ __device__ __forceinline__ void lane_flush(AccDev* acc, LaneAcc& a) {
   if (a.hit_particles) atomicAdd(&A.hit_particles, (unsigned long long)a.hit_particles);
   if (a.truncated) atomicAdd(&A.truncated, (unsigned long long)a.truncated);
   atomicAdd(&A.particles, (unsigned long long)a.particles);
-  if (a.d2 != 0.0) atomicAdd(&A.d2, a.d2);
+  if (a.d2lo != 0 || a.d2hi != 0) {
+    // 128-bit add: the low word's carry goes to the high word, so the total
+    // does not depend on the order of the lanes' flushes
+    const unsigned long long old = atomicAdd(&A.d2lo, a.d2lo);
+    const unsigned long long carry = old + a.d2lo < old ? 1ull : 0ull;
+    if (a.d2hi != 0 || carry != 0) atomicAdd(&A.d2hi, (unsigned long long)a.d2hi + carry);
+  }
 }
 
 __device__ __forceinline__ void work_flush(AccDev* acc, int q, uint32_t n_nodes, uint32_t n_tris) {
@@ -886,12 +920,14 @@ template <> struct HitConst<float> {
   static __device__ __forceinline__ float scale(const QueryDev& q) { return q.fc[kFcScale]; }
   static __device__ __forceinline__ float ref(const QueryDev& q, int i) { return q.fc[kFcRef + i]; }
   static __device__ __forceinline__ float vhat(const QueryDev& q, int i) { return q.fc[kFcVhat + i]; }
+  static __device__ __forceinline__ float scale2(const QueryDev& q) { return q.fc[kFcScale2]; }
 };
 template <> struct HitConst<double> {
   static __device__ __forceinline__ double cw(const QueryDev& q) { return q.cw; }
   static __device__ __forceinline__ double scale(const QueryDev& q) { return 1.0 / q.quantum; }
   static __device__ __forceinline__ double ref(const QueryDev& q, int i) { return q.ref[i]; }
   static __device__ __forceinline__ double vhat(const QueryDev& q, int i) { return q.vhat[i]; }
+  static __device__ __forceinline__ double scale2(const QueryDev& q) { return 1.0 / q.quantum2; }
 };
 
 // A seeded particle waiting in its warp's queue (shared memory).
@@ -1080,7 +1116,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
         R d = 0;
 #pragma unroll
         for (int i = 0; i < 3; ++i) d += dvp[i] * HitConst<R>::vhat(q, i);
-        acc.d2 += (double)d * (double)d;
+        if (d != (R)0) lane_add_d2(acc, quantize_sq(d * d * HitConst<R>::scale2(q)));
         ++acc.particles;
         if (a.rec.n_hits != nullptr) {
           a.rec.n_hits[pid] = bounce;
@@ -1305,6 +1341,13 @@ __global__ void setup_kernel(QueryDev* qs, const QueryDev* base, const double* d
       if (shift < 8) st = TPMC_EINVAL;
       q.shift = shift;
       q.quantum = ldexp(1.0, -shift);
+      // squared drag contributions: a particle's |dv . Vhat| <= 2 vmax max_bounces,
+      // so each quantised term stays below 2^62; the sum is a 128-bit integer
+      const double dmax = 2.0 * vmax * (double)q.max_bounces;
+      const int shift2 = max(0, min(32, (int)floor(62.0 - log2(dmax * dmax))));
+      q.shift2 = shift2;
+      q.quantum2 = ldexp(1.0, -shift2);
+      q.fc[kFcScale2] = (float)ldexp(1.0, shift2);
       q.fc[kFcS] = (float)S;
       q.fc[kFcCw] = (float)q.cw;
       q.fc[kFcRcv] = (float)q.r_cv;
@@ -1417,7 +1460,8 @@ __global__ void finalize_kernel(const QueryDev* qs, const AccDev* acc, uint32_t 
       r.CM[k] = r.torque[k] / (q.q_inf * q.A_ref * q.l_ref);
     }
     const double mean = Np > 0 ? (sdv[0] * q.vhat[0] + sdv[1] * q.vhat[1] + sdv[2] * q.vhat[2]) / Np : 0.0;
-    const double var = Np > 1 ? fmax(0.0, (A.d2 - Np * mean * mean) / (Np - 1.0)) : 0.0;
+    const double d2 = ((double)A.d2hi * 18446744073709551616.0 + (double)A.d2lo) * q.quantum2;
+    const double var = Np > 1 ? fmax(0.0, (d2 - Np * mean * mean) / (Np - 1.0)) : 0.0;
     r.CD_sigma = Np > 0 ? q.gamma * q.m * q.c_mp / (q.q_inf * q.A_ref) * sqrt(var / Np) : 0.0;
     r.S = q.S;
     r.S_W = q.S / q.cw;

@@ -16,6 +16,7 @@
 // process exits.  All calls on a device share it: each call clears what must
 // start at zero, and two calls that overlap on the GPU (different streams or
 // threads of different contexts on one device) race on it.
+#include <chrono>
 #include <mutex>
 
 #include "runtime.h"
@@ -74,6 +75,7 @@ extern "C" tpmc_status tpmc_sweep_noalloc(tpmc_ctx* ctx, tpmc_mesh_id mesh, cons
     return fail(TPMC_EINVAL, "tpmc_sweep_noalloc: K must be in [1, 64], the capacity of its fixed scratch");
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   std::lock_guard<std::recursive_mutex> lk(c->mu);
+  const auto t0 = std::chrono::steady_clock::now();
   cudaError_t e = cudaSetDevice(c->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   tpmc_status st = validate_params(base);
@@ -124,7 +126,9 @@ extern "C" tpmc_status tpmc_sweep_noalloc(tpmc_ctx* ctx, tpmc_mesh_id mesh, cons
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "tpmc_sweep_noalloc");
   if (err_word != 0) return fail(TPMC_ECUDA, "trace kernel reported a traversal stack overflow");
-  for (uint32_t k = 0; k < K; ++k)
-    if (h_out[k].status != TPMC_OK) return fail((tpmc_status)h_out[k].status, "a sweep item was rejected by its set-up");
+  // as tpmc_sweep: an item that its set-up rejected reports that in its own
+  // status, and every item carries the call's wall time
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (uint32_t k = 0; k < K; ++k) h_out[k].ms = ms;
   return TPMC_OK;
 }

@@ -59,6 +59,7 @@ struct Ctx {
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
   size_t budget = 0, used = 0;
+  uint64_t n_allocs = 0;       // device allocations made since creation
   std::map<void*, size_t> sizes;
   std::recursive_mutex mu;
   std::map<tpmc_mesh_id, MeshRec> meshes;

@@ -60,6 +60,7 @@ enum : int {
   kFcR = 7,                                           // [9] Rodrigues matrix (Eq. 15), row major
   kFcCenter = 16, kFcVhat = 19, kFcRef = 22,          // [3] each
   kFcPole = 25,                                       // [6] latitude tail-mass cubics at x = +1, then -1
+  kFcScale2 = 31,                                     // fixed-point scale of the squared drag contributions
   kFcCount = 32
 };
 
@@ -76,15 +77,19 @@ struct QueryDev {
   uint32_t cv_kind;       // TPMC_CV_*
   double box_lo[3], box_hi[3];
   uint32_t gsi_model;     // TPMC_GSI_*
-  uint32_t pad1;
+  uint32_t eps_k;         // Maxwell: diffuse iff the top 23 bits k of the draw satisfy k < eps_k, which
+                          // is u = (k + 1/2) 2^-23 < eps exactly (eps_k = ceil(eps 2^23 - 1/2))
   double cll[4];          // CLL: alpha_n, sqrt(1 - alpha_n), alpha_t = sigma_t (2 - sigma_t), sqrt(1 - alpha_t)
   float fcll[4];
   long long* panel;       // [n_tri][3] fixed-point per-triangle sums, or null
   // derived by the set-up kernel
   double S, cw, c_mp, gamma, q_inf, Dnorm, K1, vhat[3], R[9];
   double quantum;         // 2^-shift
+  double quantum2;        // 2^-shift2: unit of the sum of squared drag contributions
   int32_t shift;          // fixed-point scale 2^shift
+  int32_t shift2;         // fixed-point scale of the squared drag contributions
   int32_t status;         // tpmc_status of the set-up
+  int32_t pad2;
   // FP32 copies of the query constants (kFc* indices)
   float fc[kFcCount];
   float htab[kHTable + 1];
@@ -111,8 +116,10 @@ struct AccDev {
   long long F[3];           // sum of (v_in - v_out), units quantum * c_mp
   long long T[3];           // sum of (r - ref) x (v_in - v_out), units quantum * m * c_mp
   unsigned long long hits, hit_particles, truncated, particles, nodes, tris;
-  double d2;                // sum over particles of (their dv . Vhat)^2
-  double pad;
+  // sum over particles of (their dv . Vhat)^2 in units of quantum2, as a
+  // 128-bit integer (d2hi 2^64 + d2lo): exact, so the error estimate does not
+  // depend on the order in which lanes add their sums
+  unsigned long long d2lo, d2hi;
 };
 
 struct RecordsDev {

@@ -73,6 +73,7 @@ class tpmc_mesh_stats(ctypes.Structure):
         ("depth", ctypes.c_uint32), ("n_skipped", ctypes.c_uint32), ("leaf_max", ctypes.c_uint32),
         ("bound_center", _D3), ("bound_radius", ctypes.c_double), ("device_bytes", ctypes.c_uint64),
         ("n_refs", ctypes.c_uint32), ("n_exposed", ctypes.c_uint32),
+        ("bvh_width", ctypes.c_uint32), ("node_bytes", ctypes.c_uint32),
     ]
 
 
@@ -91,6 +92,8 @@ SIGNATURES = {
     "tpmc_set_stream": [_P, _P],
     "tpmc_last_error": [_P],
     "tpmc_set_counters": [_P, ctypes.c_int],
+    "tpmc_memory_info": [_P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                         ctypes.POINTER(ctypes.c_uint64)],
     "tpmc_mesh_load": [_P, _PD, ctypes.c_uint32, _PU32, ctypes.c_uint32, _PU32],
     "tpmc_mesh_unload": [_P, ctypes.c_uint32],
     "tpmc_mesh_info": [_P, ctypes.c_uint32, ctypes.POINTER(tpmc_mesh_stats)],
@@ -182,6 +185,13 @@ def tpmc_set_stream(ctx, stream=None):
 def tpmc_last_error(ctx=None) -> str:
     m = lib().tpmc_last_error(ctx)
     return m.decode() if m else ""
+
+
+def tpmc_memory_info(ctx) -> dict:
+    used, budget, n = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_uint64()
+    _check(lib().tpmc_memory_info(ctx, ctypes.byref(used), ctypes.byref(budget), ctypes.byref(n)),
+           "tpmc_memory_info", ctx)
+    return {"used": used.value, "budget": budget.value, "n_allocs": n.value}
 
 
 def tpmc_set_counters(ctx, enable: bool):

@@ -11,7 +11,7 @@ import math
 import numpy as np
 import pytest
 
-from tests.parity_util import cd_close, compare_paths
+from tests.parity_util import MAX_EXCUSED_SHARE, cd_close, dv_parity, path_stats, report
 from tpmc_inputs import meshes as M
 from tpmc_inputs import workloads as W
 
@@ -59,12 +59,37 @@ def _run_pair(T, orc, ctx, xyz, tri, params, N, precision, pid_sample=None):
     return res, rec, ores, orec
 
 
-def _assert_paths(rec, orec, max_unexplained=0):
-    ident, expl, unexpl = compare_paths(rec, orec, K)
-    n = len(ident)
-    assert unexpl.sum() <= max_unexplained, (
-        f"{int(unexpl.sum())} of {n} particles differ away from edges; first ids {np.nonzero(unexpl)[0][:10]}")
-    assert ident.mean() > 0.99
+# FP32 momentum differences of particles whose paths are identical: each
+# particle's summed dv within FP32_DV_MEDIAN (median) and FP32_DV_P99 (99th
+# percentile) relative, and the drag they sum to within FP32_DRAG of the
+# oracle's.  The float seeding solves (table start + one Newton step) leave
+# the normal speed within ~6e-8 relative in the median and 2e-5 at the 99th
+# percentile; re-emission and the frames add float rounding (~1e-7).
+FP32_DV_MEDIAN = 1e-5
+FP32_DV_P99 = 1e-4
+FP32_DRAG = 1e-5
+
+
+def _assert_paths(rec, orec, vhat=None, fp32=False, max_excused=MAX_EXCUSED_SHARE, max_unexplained=0):
+    """Per-particle path parity: no path may differ away from an edge, and at
+    most max_excused of the particles may differ after a near-edge or grazing
+    hit.  With vhat, the identical-path particles' dv is compared as well
+    (FP32: the relative tolerances above)."""
+    import os
+
+    st = path_stats(rec, orec, K)
+    ident = st["_identical_mask"]
+    if vhat is not None:
+        st["dv"] = dv_parity(rec, orec, ident, vhat)
+    report(os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], st)
+    assert st["unexplained"] <= max_unexplained, (
+        f"{st['unexplained']} of {st['n']} particles differ away from edges; "
+        f"first ids {np.nonzero(~ident)[0][:10]}")
+    assert st["excused_share"] <= max_excused, (st["excused"], st["n"], st["excused_by_bounce"])
+    if vhat is not None and fp32 and st["dv"]["n"] > 0:
+        d = st["dv"]
+        assert d["median_rel"] <= FP32_DV_MEDIAN and d["p99_rel"] <= FP32_DV_P99, d
+        assert d["drag_rel"] <= FP32_DRAG, d
     return ident
 
 
@@ -72,7 +97,7 @@ def _assert_paths(rec, orec, max_unexplained=0):
 def test_icosphere_fp64_matches_oracle(T, orc, ctx):
     case = W.icosphere_case(N=100_000)
     res, rec, ores, orec = _run_pair(T, orc, ctx, case["xyz"], case["tri"], case["params"], case["N"], T.TPMC_FP64)
-    ident = _assert_paths(rec, orec)
+    ident = _assert_paths(rec, orec, vhat=case["params"]["dir"])
     # FP64 throughout: seeded states agree to rounding
     np.testing.assert_allclose(rec["pos"], orec["pos"], rtol=0, atol=1e-11)
     np.testing.assert_allclose(rec["vel"], orec["vel"], rtol=0, atol=1e-10)
@@ -112,7 +137,7 @@ def test_fp32_convex_matches_oracle(T, orc, ctx, shape, N, S, eps, alpha_deg):
     params = dict(**W.base_state(S=S), dir=Vhat, eps_diffuse=eps, A_ref=A_ref, r_cv=1.05 * rb, center=tuple(c),
                   seed=4242, max_bounces=64)
     res, rec, ores, orec = _run_pair(T, orc, ctx, xyz, tri, params, N, T.TPMC_FP32)
-    _assert_paths(rec, orec)
+    _assert_paths(rec, orec, vhat=Vhat, fp32=True)
     # float seeding: positions to a few float ulps of the CV radius, velocities to ~1e-5
     np.testing.assert_allclose(rec["pos"], orec["pos"], rtol=0, atol=2e-5)
     np.testing.assert_allclose(rec["vel"], orec["vel"], rtol=0, atol=2e-4)
@@ -126,7 +151,7 @@ def test_fp32_concave_satellite_matches_oracle(T, orc, ctx):
     case = W.satellite_case(N=40_000)
     p = dict(case["params"])
     res, rec, ores, orec = _run_pair(T, orc, ctx, case["xyz"], case["tri"], p, case["N"], T.TPMC_FP32)
-    ident = _assert_paths(rec, orec)
+    ident = _assert_paths(rec, orec, vhat=p["dir"], fp32=True)
     assert (rec["n_hits"] >= 2).sum() > 50  # multiple reflections are exercised
     assert cd_close(res["CD"], ores["CD"], ores["CD_sigma"])
     for k in range(3):  # torque within the same tolerance, scaled by its magnitude
@@ -142,7 +167,7 @@ def test_concave_hemisphere_matches_oracle(T, orc, ctx, precision, eps):
     p = dict(case["params"], eps_diffuse=eps)
     prec = T.TPMC_FP32 if precision == "fp32" else T.TPMC_FP64
     res, rec, ores, orec = _run_pair(T, orc, ctx, case["xyz"], case["tri"], p, case["N"], prec)
-    ident = _assert_paths(rec, orec)
+    ident = _assert_paths(rec, orec, vhat=p["dir"], fp32=precision == "fp32")
     assert (rec["n_hits"] >= 3).sum() > 0.1 * res["n_hit_particles"]
     if precision == "fp64":
         np.testing.assert_allclose(rec["dv"][ident], orec["dv"][ident], rtol=0, atol=1e-8 * case["params"]["V"])
@@ -219,7 +244,7 @@ def test_tiny_and_ragged_counts(T, orc, ctx, N):
     xyz, tri = M.icosphere(1)
     params = dict(**W.base_state(S=3.0), dir=(1.0, 0, 0), eps_diffuse=1.0, A_ref=math.pi, r_cv=1.2, seed=N)
     res, rec, ores, orec = _run_pair(T, orc, ctx, xyz, tri, params, N, T.TPMC_FP32)
-    _assert_paths(rec, orec)
+    _assert_paths(rec, orec, vhat=params["dir"], fp32=True)
     assert res["n_particles"] == N
     assert res["n_hits"] == ores["n_hits"]
 
@@ -281,6 +306,8 @@ def test_results_are_deterministic_and_schedule_independent(T, ctx):
     for r in (r2, r3):
         assert r["sum_dv_q"] == r1["sum_dv_q"] and r["sum_rdv_q"] == r1["sum_rdv_q"]
         assert r["force"] == r1["force"] and r["CD"] == r1["CD"]
+        # the squared contributions are integer sums too: sigma is schedule-independent bit for bit
+        assert r["CD_sigma"] == r1["CD_sigma"] and r["CD_sigma"] > 0
         assert r["n_hits"] == r1["n_hits"] and r["n_truncated"] == r1["n_truncated"]
 
 
@@ -336,7 +363,7 @@ def test_cll_matches_oracle(T, orc, ctx, precision, shape, alpha_n, sigma_t):
     p = dict(case["params"], gsi_model=1, alpha_n=alpha_n, sigma_t=sigma_t)
     prec = T.TPMC_FP32 if precision == "fp32" else T.TPMC_FP64
     res, rec, ores, orec = _run_pair(T, orc, ctx, case["xyz"], case["tri"], p, case["N"], prec)
-    ident = _assert_paths(rec, orec)
+    ident = _assert_paths(rec, orec, vhat=p["dir"], fp32=precision == "fp32")
     assert (rec["n_hits"] >= 2).sum() > (1000 if shape == "hemisphere" else 30)  # multiple reflections
     if precision == "fp64":
         np.testing.assert_allclose(rec["dv"][ident], orec["dv"][ident], rtol=0, atol=1e-8 * case["params"]["V"])
@@ -399,7 +426,7 @@ def test_box_cv_matches_oracle(T, orc, ctx, precision, kind, alpha_deg):
     finally:
         T.tpmc_mesh_unload(ctx, mesh)
     ores, _, orec = orc.trace(orc.Mesh(xyz, tri), orc.make_params(**params, cv_kind=cv), N, records=True, K=K)
-    _assert_paths(rec, orec)
+    _assert_paths(rec, orec, vhat=params["dir"], fp32=precision == "fp32")
     tol_pos, tol_vel = (2e-5, 2e-4) if precision == "fp32" else (1e-12, 1e-9)
     np.testing.assert_allclose(rec["pos"], orec["pos"], rtol=0, atol=tol_pos)
     np.testing.assert_allclose(rec["vel"], orec["vel"], rtol=0, atol=tol_vel)
@@ -597,7 +624,7 @@ def test_speed_ratio_extremes_on_the_sphere(T, orc, ctx, S):
     params = dict(**W.base_state(S=S), dir=tuple(Vhat), eps_diffuse=1.0, A_ref=math.pi, r_cv=1.2, seed=31,
                   max_bounces=8)
     res, rec, ores, orec = _run_pair(T, orc, ctx, xyz, tri, params, 40_009, T.TPMC_FP32)
-    _assert_paths(rec, orec)
+    _assert_paths(rec, orec, vhat=params["dir"], fp32=True)
     np.testing.assert_allclose(rec["vel"], orec["vel"], rtol=2e-5, atol=2e-4)
     mesh = T.tpmc_mesh_load(ctx, xyz, tri)
     try:
@@ -642,7 +669,7 @@ def test_flow_along_the_stream_axis(T, orc, ctx, sign):
                   max_bounces=8)
     for prec in (T.TPMC_FP32, T.TPMC_FP64):
         res, rec, ores, orec = _run_pair(T, orc, ctx, xyz, tri, params, 20_011, prec)
-        _assert_paths(rec, orec)
+        _assert_paths(rec, orec, vhat=params["dir"], fp32=prec == T.TPMC_FP32)
         np.testing.assert_allclose(rec["pos"], orec["pos"], rtol=0, atol=2e-5)
         assert cd_close(res["CD"], ores["CD"], ores["CD_sigma"])
 
@@ -700,7 +727,7 @@ def test_spatial_splits_keep_the_closest_hit(T, orc, ctx):
         params = dict(**W.base_state(S=40.0), dir=d, eps_diffuse=0.5, A_ref=math.pi * 0.25, r_cv=1.13,
                       seed=31, max_bounces=8)
         res, rec, ores, orec = _run_pair(T, orc, ctx, xyz, tri, params, 30_011, T.TPMC_FP32)
-        _assert_paths(rec, orec)
+        _assert_paths(rec, orec, vhat=params["dir"], fp32=True)
         assert (rec["n_hits"] > 0).sum() > 4_000
         assert cd_close(res["CD"], ores["CD"], ores["CD_sigma"])
 
@@ -724,7 +751,7 @@ def test_full_size_case_sampled_against_oracle(T, orc, ctx, shape):
     for start in (0, 4_999_000, N - 1000):
         _, _, orec = orc.trace(om, op, N, pid_begin=start, count=1000, records=True, K=K)
         sub = {k: v[start:start + 1000] for k, v in rec.items()}
-        _assert_paths(sub, orec)
+        _assert_paths(sub, orec, vhat=case["params"]["dir"], fp32=True)
     Vhat = np.asarray(case["params"]["dir"])
     F = orc.panel_sum(xyz, tri, Vhat, case["S"], case["eps"], math.sqrt(0.3), two_sided=(shape == "plate"))
     A_ref = case["params"]["A_ref"]
