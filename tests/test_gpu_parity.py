@@ -62,11 +62,12 @@ def _run_pair(T, orc, ctx, xyz, tri, params, N, precision, pid_sample=None):
 # FP32 momentum differences of particles whose paths are identical: each
 # particle's summed dv within FP32_DV_MEDIAN (median) and FP32_DV_P99 (99th
 # percentile) relative, and the drag they sum to within FP32_DRAG of the
-# oracle's.  The float seeding solves (table start + one Newton step) leave
-# the normal speed within ~6e-8 relative in the median and 2e-5 at the 99th
-# percentile; re-emission and the frames add float rounding (~1e-7).
-FP32_DV_MEDIAN = 1e-5
-FP32_DV_P99 = 1e-4
+# oracle's.  Float rounding of the seeding solves (table start + one Newton
+# step), the re-emission and the frames leaves ~5e-8 in the median and ~2e-7
+# at the 99th percentile on GB300; near rest (S = 0.05), where the float
+# latitude CDF cancels O(1/S) terms, 5e-7 and 4e-6, and 2e-6 in the drag.
+FP32_DV_MEDIAN = 1e-6
+FP32_DV_P99 = 1e-5
 FP32_DRAG = 1e-5
 
 
