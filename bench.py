@@ -886,9 +886,9 @@ def run_profile_launch(args):
     torch.cuda.set_stream(stream)
     T.tpmc_set_stream(ctx, stream)
     if args.launch:
-        vals = [int(x) for x in args.launch.split(",")] + [0, 0]
+        vals = [int(x) for x in args.launch.split(",")] + [0, 0, 0]
         T.tpmc_set_launch(ctx, block=vals[0], blocks_per_sm=vals[1], chunk=vals[2], smem_nodes=vals[3],
-                          refill_at=vals[4], bvh_leaf=vals[5])
+                          refill_at=vals[4], bvh_leaf=vals[5], bvh_width=vals[6])
     mesh = T.tpmc_mesh_load(ctx, g["xyz"], g["tri"])
     K = len(g["cases"])
     dd = torch.tensor(g["dirs"], dtype=torch.float64, device="cuda")
@@ -925,7 +925,8 @@ def main():
                     help="plate-specular|plate-diffuse|cylinder-specular|cylinder-diffuse|satellite-sweep: one small launch")
     ap.add_argument("--profile-n-each", type=int, default=100_000)
     ap.add_argument("--launch", default=None,
-                    help="block,blocks_per_sm,chunk,smem_nodes[,refill_at,bvh_leaf] for --profile-launch")
+                    help="block,blocks_per_sm,chunk,smem_nodes[,refill_at,bvh_leaf,bvh_width] for --profile-launch "
+                         "(block 0: only the BVH layout)")
     args = ap.parse_args()
     if args.profile_launch:
         return run_profile_launch(args)

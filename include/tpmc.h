@@ -182,6 +182,9 @@ typedef struct {
   uint32_t smem_nodes;          /* BVH nodes staged in shared memory                    */
   uint32_t refill_at;           /* finished lanes that end a traversal round (0: 24)    */
   uint32_t bvh_leaf;            /* largest BVH leaf for later tpmc_mesh_load (0: 4)     */
+  uint32_t bvh_width;           /* children per BVH node for later tpmc_mesh_load: 2, 4  */
+                                /* or 8 (0: the default, or what tpmc_tune chose for     */
+                                /* meshes of that size class)                            */
 } tpmc_launch;
 
 /* ---- context ------------------------------------------------------------ */

@@ -252,6 +252,82 @@ tpmc_status Ctx::check_error_word() {
   return TPMC_OK;
 }
 
+// BVH width of a mesh load: the one set by tpmc_set_launch, else the one
+// tpmc_tune chose for the size class, else the default.
+uint32_t Ctx::width_for(uint32_t n_tri) const {
+  if (bvh_width) return bvh_width;
+  auto it = tuned_width.find(tune_key(n_tri, 0));
+  return it != tuned_width.end() ? it->second : kDefaultBvhWidth;
+}
+
+// Builds the mesh's BVH with `width` children per node and uploads it, its
+// triangles and frames into one device allocation (the host copies of the
+// mesh are not set here).
+tpmc_status Ctx::upload_mesh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t n_tri, uint32_t width,
+                             MeshRec* out) {
+  BvhBuild b;
+  const char* err = nullptr;
+  if (!build_bvh(xyz, n_vert, tri, n_tri, bvh_leaf, width, &b, &err)) {
+    b.release();
+    return fail(TPMC_EINVAL, err);
+  }
+  MeshRec& m = *out;
+  const size_t sz_nodes = b.n_nodes * b.node_bytes;
+  const size_t sz_tris = (size_t)b.n_leaf_tris * 12 * sizeof(float);
+  const size_t sz_tris64 = (size_t)b.n_leaf_tris * 12 * sizeof(double);
+  const size_t sz_fr = (size_t)n_tri * 8 * sizeof(float);
+  const size_t sz_fr64 = (size_t)n_tri * 8 * sizeof(double);
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t total = al(sz_nodes) + al(sz_tris) + al(sz_tris64) + al(sz_fr) + al(sz_fr64);
+  tpmc_status st = alloc(&m.d_block, std::max(total, (size_t)256), "mesh");
+  if (st != TPMC_OK) { b.release(); return st; }
+  char* base = (char*)m.d_block;
+  size_t off = 0;
+  auto place = [&](size_t sz) { char* p = base + off; off += al(sz); return p; };
+  char* p_nodes = place(sz_nodes);
+  char* p_tris = place(sz_tris);
+  char* p_tris64 = place(sz_tris64);
+  char* p_fr = place(sz_fr);
+  char* p_fr64 = place(sz_fr64);
+  cudaError_t e = cudaSuccess;
+  if (sz_nodes) e = cudaMemcpy(p_nodes, b.nodes, sz_nodes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && sz_tris) e = cudaMemcpy(p_tris, b.tris, sz_tris, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && sz_tris64) e = cudaMemcpy(p_tris64, b.tris64, sz_tris64, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && sz_fr) e = cudaMemcpy(p_fr, b.frames, sz_fr, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && sz_fr64) e = cudaMemcpy(p_fr64, b.frames64, sz_fr64, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    release(m.d_block);
+    m.d_block = nullptr;
+    b.release();
+    return cuda_fail(e, "upload mesh");
+  }
+  m.dev.nodes = (const float4*)p_nodes;
+  m.dev.tris = (const float4*)p_tris;
+  m.dev.tris64 = (const double*)p_tris64;
+  m.dev.frames = (const float4*)p_fr;
+  m.dev.frames64 = (const double*)p_fr64;
+  m.dev.n_nodes = (uint32_t)b.n_nodes;
+  m.dev.width = b.width;
+  for (int k = 0; k < 3; ++k) {  // the padded root box (empty when there is no mesh)
+    m.dev.box_lo[k] = b.root_lo[k];
+    m.dev.box_hi[k] = b.root_hi[k];
+  }
+  m.dev.n_tri = n_tri;
+  m.dev.n_tri_leaf = b.n_leaf_tris;
+  m.dev.scene_radius = (float)b.radius;
+  for (int i = 0; i < 3; ++i) m.center[i] = b.center[i];
+  m.radius = b.radius;
+  m.depth = b.depth;
+  m.leaf_max = b.leaf_max;
+  m.n_skipped = b.n_skipped;
+  m.n_exposed = b.n_exposed;
+  m.node_bytes = b.node_bytes;
+  m.n_vert = n_vert;
+  m.bytes = total;
+  b.release();
+  return TPMC_OK;
+}
+
 Ctx::~Ctx() {
   if (serve) stop_serving(this);
   for (auto& kv : panels) release(kv.second.d_panel);
@@ -348,72 +424,11 @@ tpmc_status tpmc_mesh_load(tpmc_ctx* ctx, const double* xyz, uint32_t n_vert, co
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   std::lock_guard<std::recursive_mutex> lk(c->mu);
   cudaSetDevice(c->device);
-  BvhBuild b;
-  const char* err = nullptr;
-  if (!build_bvh(xyz, n_vert, tri, n_tri, c->bvh_leaf, &b, &err)) {
-    b.release();
-    return fail(TPMC_EINVAL, err);
-  }
   MeshRec m;
-  const size_t sz_nodes = b.n_nodes * 16 * sizeof(float);
-  const size_t sz_tris = (size_t)b.n_leaf_tris * 12 * sizeof(float);
-  const size_t sz_tris64 = (size_t)b.n_leaf_tris * 12 * sizeof(double);
-  const size_t sz_fr = (size_t)n_tri * 8 * sizeof(float);
-  const size_t sz_fr64 = (size_t)n_tri * 8 * sizeof(double);
-  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  const size_t total = al(sz_nodes) + al(sz_tris) + al(sz_tris64) + al(sz_fr) + al(sz_fr64);
-  tpmc_status st = c->alloc(&m.d_block, std::max(total, (size_t)256), "mesh");
-  if (st != TPMC_OK) { b.release(); return st; }
-  char* base = (char*)m.d_block;
-  size_t off = 0;
-  auto place = [&](size_t sz) { char* p = base + off; off += al(sz); return p; };
-  char* p_nodes = place(sz_nodes);
-  char* p_tris = place(sz_tris);
-  char* p_tris64 = place(sz_tris64);
-  char* p_fr = place(sz_fr);
-  char* p_fr64 = place(sz_fr64);
-  cudaError_t e = cudaSuccess;
-  if (sz_nodes) e = cudaMemcpy(p_nodes, b.nodes, sz_nodes, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && sz_tris) e = cudaMemcpy(p_tris, b.tris, sz_tris, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && sz_tris64) e = cudaMemcpy(p_tris64, b.tris64, sz_tris64, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && sz_fr) e = cudaMemcpy(p_fr, b.frames, sz_fr, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && sz_fr64) e = cudaMemcpy(p_fr64, b.frames64, sz_fr64, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    c->release(m.d_block);
-    b.release();
-    return cuda_fail(e, "upload mesh");
-  }
-  m.dev.nodes = (const float4*)p_nodes;
-  m.dev.tris = (const float4*)p_tris;
-  m.dev.tris64 = (const double*)p_tris64;
-  m.dev.frames = (const float4*)p_fr;
-  m.dev.frames64 = (const double*)p_fr64;
-  m.dev.n_nodes = (uint32_t)b.n_nodes;
-  for (uint32_t c = 0; c < 2 && b.n_nodes > 0; ++c) {  // the root box: union of the root's child boxes
-    const float* xy = b.nodes + 4 * c;
-    const float* z = b.nodes + 8 + 2 * c;
-    if (xy[0] > 1e29f) continue;  // empty child
-    const float lo[3] = {xy[0], xy[2], z[0]}, hi[3] = {xy[1], xy[3], z[1]};
-    const bool first = m.dev.box_lo[0] > m.dev.box_hi[0];
-    for (int k = 0; k < 3; ++k) {
-      m.dev.box_lo[k] = first ? lo[k] : std::min(m.dev.box_lo[k], lo[k]);
-      m.dev.box_hi[k] = first ? hi[k] : std::max(m.dev.box_hi[k], hi[k]);
-    }
-  }
-  m.dev.n_tri = n_tri;
-  m.dev.n_tri_leaf = b.n_leaf_tris;
-  m.dev.scene_radius = (float)b.radius;
-  for (int i = 0; i < 3; ++i) m.center[i] = b.center[i];
-  m.radius = b.radius;
-  m.depth = b.depth;
-  m.leaf_max = b.leaf_max;
-  m.n_skipped = b.n_skipped;
-  m.n_exposed = b.n_exposed;
-  m.n_vert = n_vert;
-  m.bytes = total;
+  tpmc_status st = c->upload_mesh(xyz, n_vert, tri, n_tri, c->width_for(n_tri), &m);
+  if (st != TPMC_OK) return st;
   m.h_xyz.assign(xyz, xyz + 3 * (size_t)n_vert);
   m.h_tri.assign(tri, tri + 3 * (size_t)n_tri);
-  b.release();
   const tpmc_mesh_id id = c->next_mesh++;
   c->meshes[id] = std::move(m);
   *out = id;
@@ -453,8 +468,8 @@ tpmc_status tpmc_mesh_info(tpmc_ctx* ctx, tpmc_mesh_id mesh, tpmc_mesh_stats* ou
   out->device_bytes = m.bytes;
   out->n_refs = m.dev.n_tri_leaf;
   out->n_exposed = m.n_exposed;
-  out->bvh_width = 2;
-  out->node_bytes = 64;
+  out->bvh_width = m.dev.width;
+  out->node_bytes = m.node_bytes;
   return TPMC_OK;
 }
 
@@ -504,7 +519,7 @@ static tpmc_status trace_common(Ctx* c, tpmc_mesh_id mesh, const tpmc_params* pa
   item.g_begin = 0; item.pid_begin = 0; item.count = N; item.query = 0;
   tpmc_status rs = c->grow(c->s_out, sizeof(tpmc_result), "result");
   if (rs == TPMC_OK)
-    rs = c->run(m, &q, 1, nullptr, nullptr, nullptr, &item, 1, N, trace_variant(params), (tpmc_result*)c->s_out.ptr,
+    rs = c->run(m, &q, 1, nullptr, nullptr, nullptr, &item, 1, N, trace_variant(params, m.dev), (tpmc_result*)c->s_out.ptr,
                 records ? &rec : nullptr);
   cudaError_t e = cudaSuccess;
   if (rs == TPMC_OK) e = cudaMemcpyAsync(out, c->s_out.ptr, sizeof(tpmc_result), cudaMemcpyDeviceToHost, c->stream);
@@ -625,7 +640,7 @@ static tpmc_status sweep_common(Ctx* c, tpmc_mesh_id mesh, const tpmc_params* ba
   const MeshRec& m = it->second;
   QueryDev q;
   if ((st = fill_query(m, base, N_each, &q)) != TPMC_OK) return st;
-  return c->run(m, nullptr, K, &q, d_dirs, d_S, nullptr, 0, (uint64_t)K * N_each, trace_variant(base), d_out, nullptr);
+  return c->run(m, nullptr, K, &q, d_dirs, d_S, nullptr, 0, (uint64_t)K * N_each, trace_variant(base, m.dev), d_out, nullptr);
 }
 
 tpmc_status tpmc_sweep(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* base, const double* h_dirs,
@@ -668,8 +683,21 @@ tpmc_status tpmc_set_launch(tpmc_ctx* ctx, const tpmc_launch* cfg) {
   if (!ctx) return fail(TPMC_EINVAL, "ctx is NULL");
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   std::lock_guard<std::recursive_mutex> lk(c->mu);
-  if (!cfg) { c->manual_launch = false; return TPMC_OK; }
-  if (cfg->block == 0 || cfg->block % 32 != 0 || cfg->block > 256) return fail(TPMC_EINVAL, "block must be 32..256, multiple of 32");
+  if (!cfg) {
+    c->manual_launch = false;
+    c->bvh_leaf = 4;
+    c->bvh_width = 0;
+    return TPMC_OK;
+  }
+  if (cfg->bvh_leaf > 127) return fail(TPMC_EINVAL, "bvh_leaf must be in [0, 127]");
+  if (cfg->bvh_width != 0 && cfg->bvh_width != 2 && cfg->bvh_width != 4 && cfg->bvh_width != 8)
+    return fail(TPMC_EINVAL, "bvh_width must be 0, 2, 4 or 8");
+  if (cfg->block == 0) {  // the BVH layout of later loads only
+    c->bvh_leaf = cfg->bvh_leaf ? cfg->bvh_leaf : 4;
+    c->bvh_width = cfg->bvh_width;
+    return TPMC_OK;
+  }
+  if (cfg->block % 32 != 0 || cfg->block > 256) return fail(TPMC_EINVAL, "block must be 32..256, multiple of 32");
   if (cfg->chunk != 0 && (cfg->chunk % 32 != 0)) return fail(TPMC_EINVAL, "chunk must be a multiple of 32");
   if (cfg->refill_at > 32) return fail(TPMC_EINVAL, "refill_at must be in [0, 32]");
   if (cfg->bvh_leaf > 127) return fail(TPMC_EINVAL, "bvh_leaf must be in [0, 127]");
@@ -680,6 +708,7 @@ tpmc_status tpmc_set_launch(tpmc_ctx* ctx, const tpmc_launch* cfg) {
   c->manual.smem_nodes = cfg->smem_nodes;
   c->manual.refill_at = cfg->refill_at;
   c->bvh_leaf = cfg->bvh_leaf ? cfg->bvh_leaf : 4;
+  c->bvh_width = cfg->bvh_width;
   return TPMC_OK;
 }
 
@@ -689,13 +718,15 @@ tpmc_status tpmc_get_launch(tpmc_ctx* ctx, tpmc_mesh_id mesh, uint32_t precision
   std::lock_guard<std::recursive_mutex> lk(c->mu);
   auto it = c->meshes.find(mesh);
   if (it == c->meshes.end()) return fail(TPMC_ENOTFOUND, "unknown mesh id");
-  const LaunchCfg cfg = c->schedule(it->second, precision, 0);
+  const LaunchCfg cfg = c->schedule(
+      it->second, precision | (it->second.dev.width == 8 ? kVariantWide8 : (it->second.dev.width == 4 ? kVariantWide4 : 0u)), 0);
   out->block = cfg.block;
   out->blocks_per_sm = cfg.blocks_per_sm;
   out->chunk = cfg.chunk;
   out->smem_nodes = cfg.smem_nodes;
   out->refill_at = cfg.refill_at;
   out->bvh_leaf = c->bvh_leaf;
+  out->bvh_width = it->second.dev.width;
   return TPMC_OK;
 }
 

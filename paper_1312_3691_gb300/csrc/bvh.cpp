@@ -155,6 +155,22 @@ double box_extreme(const Box& b, const double n[3], const double o[3], double si
   return v;
 }
 
+// Conservative float box coordinates: pad by a small multiple of the scene
+// scale and of the coordinate, then round outward, so that float slab tests
+// on the GPU never cut off a part of the box that holds a triangle.
+float pad_down(double v, double scale) {
+  const double p = v - (1e-5 * scale + 4e-7 * std::fabs(v));
+  float f = (float)p;
+  if ((double)f > p) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+float pad_up(double v, double scale) {
+  const double p = v + (1e-5 * scale + 4e-7 * std::fabs(v));
+  float f = (float)p;
+  if ((double)f < p) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
 struct BNode {       // binary build node
   Box box;
   int32_t left = -1, right = -1;  // children (build indices) for inner nodes
@@ -181,11 +197,253 @@ constexpr uint32_t kMaxDepth = kMaxStack - 20;  // SAH below this depth, median 
 // 1e-10 m, below the shortest hit distance the traversal accepts.
 constexpr double kExposedEps = 1e-12;
 
+// Corner (bit 0: +x, bit 1: +y, bit 2: +z) that slot s of a W-wide node faces.
+uint32_t slot_corner(uint32_t W, uint32_t s) { return W == 8 ? s : kWide4Corner[s]; }
+
+// Lays the binary tree out as compressed W-wide nodes (W = 4 or 8; the
+// format is described with kWideLeafMax in tpmc_internal.h).  Returns false,
+// leaving `out` untouched, when the wide tree would be deeper than the
+// traversal stack; the caller then keeps the binary layout.
+bool layout_wide(std::vector<BNode>& bn, const std::vector<uint32_t>& leaf_refs, const std::vector<Prim>& prims,
+                 const double* xyz, const uint32_t* tri, uint32_t W, double scale, BvhBuild* out) {
+  // 1. leaves of at most kWideLeafMax references: a larger leaf becomes a
+  //    binary subtree of leaves with the same box
+  for (size_t i = 0; i < bn.size(); ++i) {
+    if (bn[i].left >= 0 || bn[i].count <= (uint32_t)kWideLeafMax) continue;
+    const uint32_t n = bn[i].count;
+    const uint32_t leaves = (n + kWideLeafMax - 1) / kWideLeafMax;
+    const uint32_t h = ((leaves + 1) / 2) * kWideLeafMax;  // whole leaves in the first half
+    BNode a, b;
+    a.box = b.box = bn[i].box;
+    a.depth = b.depth = bn[i].depth + 1;
+    a.first = bn[i].first;
+    a.count = h;
+    b.first = a.first + h;
+    b.count = n - h;
+    const int32_t ia = (int32_t)bn.size();
+    bn.push_back(a);
+    bn.push_back(b);
+    bn[i].left = ia;
+    bn[i].right = ia + 1;
+    bn[i].count = 0;
+  }
+
+  // 2. collapse by the surface-area heuristic (the dynamic programme of
+  //    Ylitie, Karras & Laine, restated): every binary node m can fill one
+  //    slot of its wide parent, as a leaf (when its subtree holds at most
+  //    kWideLeafMax references: the builder emits leaves depth first, so those
+  //    form one range of leaf_refs) or as a wide node of its own; or it can be
+  //    opened into its two children's slots.  With A the surface area,
+  //      leaf(m)  = A(m) c_tri refs(m),   node(m) = A(m) c_node + F(m, W),
+  //      slot(m)  = min(leaf(m), node(m)),
+  //      G(m, j)  = cheapest way to cover m's subtree with at most j slots
+  //               = min(slot(m), F(m, j)) for j >= 2, slot(m) for j = 1,
+  //      F(m, j)  = min over j1 + j2 = j of G(left, j1) + G(right, j2).
+  //    A triangle cut by a spatial split may then appear twice in one merged
+  //    leaf, which only repeats a test.
+  constexpr double kWideCostNode = 1.0, kWideCostTri = 0.3;
+  constexpr double kInf = INFINITY;
+  const size_t nb = bn.size();
+  std::vector<uint32_t> sub_refs(nb, 0), sub_first(nb, 0);
+  std::vector<double> leaf_cost(nb, kInf), node_cost(nb, kInf), Fc(nb * 9, kInf), Gc(nb * 9, kInf);
+  std::vector<int8_t> Fsplit(nb * 9, 0), Gopen(nb * 9, 0);
+  for (size_t i = nb; i-- > 0;) {  // children come after their parents in bn
+    const BNode& b = bn[i];
+    const double A = std::max(b.box.area(), 1e-300);
+    if (b.left < 0) {
+      sub_refs[i] = b.count;
+      sub_first[i] = b.first;
+    } else {
+      const int32_t l = b.left, r = b.right;
+      sub_refs[i] = sub_refs[l] + sub_refs[r];
+      sub_first[i] = std::min(sub_first[l], sub_first[r]);
+      for (uint32_t j = 2; j <= W; ++j)
+        for (uint32_t j1 = 1; j1 < j; ++j1) {
+          const double c = Gc[9 * l + j1] + Gc[9 * r + (j - j1)];
+          if (c < Fc[9 * i + j]) { Fc[9 * i + j] = c; Fsplit[9 * i + j] = (int8_t)j1; }
+        }
+      node_cost[i] = A * kWideCostNode + Fc[9 * i + W];
+    }
+    if (sub_refs[i] <= (uint32_t)kWideLeafMax) leaf_cost[i] = A * kWideCostTri * sub_refs[i];
+    const double slot = std::min(leaf_cost[i], node_cost[i]);
+    for (uint32_t j = 1; j <= W; ++j) {
+      Gc[9 * i + j] = slot;
+      if (j >= 2 && Fc[9 * i + j] < slot) { Gc[9 * i + j] = Fc[9 * i + j]; Gopen[9 * i + j] = 1; }
+      if (j >= 2 && Gc[9 * i + j - 1] < Gc[9 * i + j]) {  // at most j slots
+        Gc[9 * i + j] = Gc[9 * i + j - 1];
+        Gopen[9 * i + j] = Gopen[9 * i + j - 1];
+        if (Gopen[9 * i + j]) { Fc[9 * i + j] = Fc[9 * i + j - 1]; Fsplit[9 * i + j] = Fsplit[9 * i + j - 1]; }
+      }
+    }
+  }
+  // the binary nodes that fill the slots of the wide node made from binary node m
+  std::vector<int32_t> cover;
+  auto collect = [&](auto&& self, int32_t m, uint32_t j) -> void {
+    if (Gopen[9 * m + j]) {
+      const uint32_t j1 = (uint32_t)Fsplit[9 * m + j];
+      self(self, bn[m].left, j1);
+      self(self, bn[m].right, j - j1);
+    } else {
+      cover.push_back(m);
+    }
+  };
+  auto is_leaf_slot = [&](int32_t m) { return leaf_cost[m] <= node_cost[m]; };
+
+  //    The children go to the slots whose corners point most nearly from the
+  //    node's centre to theirs (greedy over all child-slot pairs), and the
+  //    inner ones get consecutive wide indices in slot order.
+  struct WideNode {
+    int32_t b;                  // binary node
+    int32_t kid[8];             // binary node in each slot, or -1
+    uint32_t depth;
+  };
+  std::vector<WideNode> wn;
+  wn.push_back(WideNode{0, {-1, -1, -1, -1, -1, -1, -1, -1}, 1});
+  uint32_t max_depth = 1;
+  std::vector<char> leaf_slot(nb, 0);
+  for (size_t w = 0; w < wn.size(); ++w) {
+    cover.clear();
+    const int32_t b0i = wn[w].b;
+    if (bn[b0i].left < 0) {
+      cover.push_back(b0i);  // a tree that is a single leaf
+    } else {
+      const uint32_t j1 = (uint32_t)Fsplit[9 * b0i + W];
+      collect(collect, bn[b0i].left, j1);
+      collect(collect, bn[b0i].right, W - j1);
+    }
+    const std::vector<int32_t> kids(cover);
+    for (int32_t k : kids) leaf_slot[k] = (bn[k].left < 0 || is_leaf_slot(k)) ? 1 : 0;
+    const BNode& b0 = bn[b0i];
+    double c[3];
+    for (int a = 0; a < 3; ++a) c[a] = 0.5 * (b0.box.lo[a] + b0.box.hi[a]);
+    struct Pair { double score; uint32_t k, s; };
+    std::vector<Pair> pairs;
+    for (uint32_t k = 0; k < kids.size(); ++k)
+      for (uint32_t s = 0; s < W; ++s) {
+        const uint32_t corner = slot_corner(W, s);
+        const Box& kb = bn[kids[k]].box;
+        double score = 0.0;
+        for (int a = 0; a < 3; ++a) score += (0.5 * (kb.lo[a] + kb.hi[a]) - c[a]) * (((corner >> a) & 1u) ? 1.0 : -1.0);
+        pairs.push_back(Pair{score, k, s});
+      }
+    std::stable_sort(pairs.begin(), pairs.end(), [](const Pair& x, const Pair& y) { return x.score > y.score; });
+    std::vector<char> kid_done(kids.size(), 0), slot_done(W, 0);
+    for (const Pair& pr : pairs) {
+      if (kid_done[pr.k] || slot_done[pr.s]) continue;
+      kid_done[pr.k] = slot_done[pr.s] = 1;
+      wn[w].kid[pr.s] = kids[pr.k];
+    }
+    for (uint32_t s = 0; s < W; ++s) {
+      const int32_t k = wn[w].kid[s];
+      if (k >= 0 && !leaf_slot[k]) {
+        wn.push_back(WideNode{k, {-1, -1, -1, -1, -1, -1, -1, -1}, wn[w].depth + 1});
+        max_depth = std::max(max_depth, wn[w].depth + 1);
+      }
+    }
+  }
+  // the traversal stack holds one group per level; child indices take 24 bits
+  if (max_depth + 1 >= (uint32_t)kMaxStackW || wn.size() >= (1u << 24)) return false;
+
+  // 3. nodes and the triangle blocks, in wide-node order
+  const uint32_t F4 = W == 8 ? 5 : 4;
+  size_t n_refs = 0;
+  for (const WideNode& x : wn)
+    for (uint32_t s = 0; s < W; ++s)
+      if (x.kid[s] >= 0 && leaf_slot[x.kid[s]]) n_refs += sub_refs[x.kid[s]];
+  float* nodes = (float*)std::calloc(wn.size() * F4 * 4, sizeof(float));
+  float* tris = (float*)std::calloc(std::max<size_t>(n_refs, 1) * 12, sizeof(float));
+  double* tris64 = (double*)std::calloc(std::max<size_t>(n_refs, 1) * 12, sizeof(double));
+  uint32_t next_inner = 1, leaf_max = 0;
+  size_t ref = 0;
+  for (size_t w = 0; w < wn.size(); ++w) {
+    uint32_t* nd = reinterpret_cast<uint32_t*>(nodes + w * F4 * 4);
+    float lo[8][3], hi[8][3];
+    double p[3], top[3];
+    for (int a = 0; a < 3; ++a) { p[a] = INFINITY; top[a] = -INFINITY; }
+    for (uint32_t s = 0; s < W; ++s) {
+      const int32_t k = wn[w].kid[s];
+      if (k < 0) continue;
+      for (int a = 0; a < 3; ++a) {
+        lo[s][a] = pad_down(bn[k].box.lo[a], scale);
+        hi[s][a] = pad_up(bn[k].box.hi[a], scale);
+        p[a] = std::min(p[a], (double)lo[s][a]);
+        top[a] = std::max(top[a], (double)hi[s][a]);
+      }
+    }
+    // grid: origin p (a float), step 2^e_a with (top - p) <= 255 2^e_a
+    int e[3];
+    for (int a = 0; a < 3; ++a) {
+      const double ext = top[a] - p[a];
+      int ea = ext > 0.0 ? (int)std::ceil(std::log2(ext / 255.0)) : -126;
+      ea = std::min(std::max(ea, -126), 127);
+      while (ea < 127 && ext > 255.0 * std::ldexp(1.0, ea)) ++ea;
+      while (ea > -126 && ext <= 255.0 * std::ldexp(1.0, ea - 1)) --ea;
+      e[a] = ea;
+      const float pf = (float)p[a];  // exact: p is the smallest of the children's float corners
+      std::memcpy(&nd[a], &pf, 4);
+    }
+    uint32_t imask = 0;
+    for (uint32_t s = 0; s < W; ++s)
+      if (wn[w].kid[s] >= 0 && !leaf_slot[wn[w].kid[s]]) imask |= 1u << s;
+    nd[3] = (uint32_t)(e[0] + 127) | ((uint32_t)(e[1] + 127) << 8) | ((uint32_t)(e[2] + 127) << 16) | (imask << 24);
+    nd[4] = imask ? next_inner : 0u;
+    nd[5] = (uint32_t)ref;
+    for (uint32_t s = 0; s < W; ++s)
+      if ((imask >> s) & 1u) ++next_inner;
+    // quantised planes (empty slots: lo 255 > hi 0) and leaf metadata
+    auto put = [&](uint32_t word, uint32_t byte, uint32_t v) { nd[word] = (nd[word] & ~(0xFFu << (8 * byte))) | (v << (8 * byte)); };
+    const uint32_t per_plane = W == 8 ? 2 : 1;
+    for (uint32_t s = 0; s < W; ++s) {
+      const int32_t k = wn[w].kid[s];
+      for (int plane = 0; plane < 6; ++plane) {
+        const int a = plane % 3;
+        uint32_t q = plane < 3 ? 255u : 0u;
+        if (k >= 0) {
+          const double step = std::ldexp(1.0, e[a]);
+          const double v = plane < 3 ? std::floor(((double)lo[s][a] - p[a]) / step)
+                                     : std::ceil(((double)hi[s][a] - p[a]) / step);
+          q = (uint32_t)std::min(255.0, std::max(0.0, v));
+        }
+        put(8 + per_plane * plane + s / 4, s % 4, q);
+      }
+      if (k >= 0 && leaf_slot[k]) {
+        const uint32_t count = sub_refs[k], first = sub_first[k];
+        const uint32_t off = (uint32_t)(ref - nd[5]);
+        put(6 + s / 4, s % 4, ((count - 1) << 5) | off);
+        leaf_max = std::max(leaf_max, count);
+        for (uint32_t j = 0; j < count; ++j, ++ref) {
+          const uint32_t id = prims[leaf_refs[first + j]].id;
+          for (int v = 0; v < 3; ++v) {
+            const double* pv = xyz + 3 * (uint64_t)tri[3 * (size_t)id + v];
+            for (int a = 0; a < 3; ++a) {
+              tris[12 * ref + 4 * v + a] = (float)pv[a];
+              tris64[12 * ref + 3 * v + a] = pv[a];
+            }
+          }
+          std::memcpy(&tris[12 * ref + 3], &id, 4);
+          tris64[12 * ref + 9] = (double)id;
+        }
+      }
+    }
+  }
+  out->nodes = nodes;
+  out->tris = tris;
+  out->tris64 = tris64;
+  out->n_nodes = wn.size();
+  out->n_leaf_tris = (uint32_t)n_refs;
+  out->width = W;
+  out->node_bytes = 16 * F4;
+  out->depth = max_depth;
+  out->leaf_max = leaf_max;
+  return true;
+}
+
 }  // namespace
 
 bool build_bvh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t n_tri, uint32_t max_leaf,
-               BvhBuild* out, const char** err) {
+               uint32_t width, BvhBuild* out, const char** err) {
   *out = BvhBuild();
+  if (width != 2 && width != 4 && width != 8) { *err = "BVH width must be 2, 4 or 8"; return false; }
   max_leaf = std::max(1u, std::min(max_leaf, 127u));
   if (n_tri > (1u << 24)) { *err = "mesh has more than 2^24 triangles"; return false; }
   if (n_tri > 0 && n_vert == 0) { *err = "triangles without vertices"; return false; }
@@ -504,6 +762,15 @@ bool build_bvh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t
     }
   }
 
+  if (!bn.empty())
+    for (int a = 0; a < 3; ++a) {
+      out->root_lo[a] = pad_down(bn[0].box.lo[a], scale);
+      out->root_hi[a] = pad_up(bn[0].box.hi[a], scale);
+    }
+  out->width = 2;
+  out->node_bytes = 64;
+  if (width > 2 && !bn.empty() && layout_wide(bn, leaf_refs, prims, xyz, tri, width, scale, out)) return true;
+
   // ---- GPU layout: inner nodes in breadth-first order, leaves in place ----
   // A tree that is a single leaf gets a root whose second child is empty.
   std::vector<int32_t> inner_order;  // build index of each GPU node
@@ -544,20 +811,8 @@ bool build_bvh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t
     out->tris64[12 * k + 9] = (double)i;
   }
 
-  // conservative float boxes: pad by a small multiple of the scene scale and
-  // of the coordinate, then round outward
-  auto pad_lo = [&](double v) {
-    const double p = v - (1e-5 * scale + 4e-7 * std::fabs(v));
-    float f = (float)p;
-    if ((double)f > p) f = std::nextafter(f, -INFINITY);
-    return f;
-  };
-  auto pad_hi = [&](double v) {
-    const double p = v + (1e-5 * scale + 4e-7 * std::fabs(v));
-    float f = (float)p;
-    if ((double)f < p) f = std::nextafter(f, INFINITY);
-    return f;
-  };
+  auto pad_lo = [&](double v) { return pad_down(v, scale); };
+  auto pad_hi = [&](double v) { return pad_up(v, scale); };
   auto child_code = [&](int32_t b, uint32_t& depth_seen) -> int32_t {
     const BNode& c = bn[b];
     depth_seen = std::max(depth_seen, c.depth);

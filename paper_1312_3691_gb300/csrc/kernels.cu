@@ -3,7 +3,7 @@
 //   setup_kernel     FP64: free-stream set-up per query (Nomenclature; Eq. 10
 //                    flux; particle weight, §II.A), Rodrigues matrix (Eq. 15),
 //                    fixed-point scale, start table of the latitude inverse CDF.
-//   trace_kernel<R, MINB, CLL>
+//   trace_kernel<R, MINB, CLL, W>
 //                    persistent, one warp = 32 particle slots refilled from a
 //                    global work counter by ballot; per slot: Philox draws,
 //                    seeding (Eq. 11, Eq. 14a-c, Eq. 15; or the box CV),
@@ -18,6 +18,7 @@
 // This file shares nothing with the CPU oracle; both follow the paper and the
 // published Philox4x32-10 definition (Salmon et al., SC'11).
 #include <algorithm>
+#include <type_traits>
 
 #include <cuda_runtime.h>
 #include <math_constants.h>
@@ -539,6 +540,9 @@ template <typename R>
 struct Ray {
   R o[3], d[3], inv[3], oi[3];
   R tlo;
+  // wide trees: visit position (0 first) of each child-box corner c (nibble c
+  // of ptab) and the corner at each position (nibble p of stab)
+  uint32_t ptab, stab;
 };
 
 // Woop, Benthin & Wald (JCGT 2013): shear the ray onto +z of a permuted frame.
@@ -751,6 +755,207 @@ __device__ __forceinline__ bool trav_leaf(const MeshDev& m, const Ray<R>& r, uin
     t.cur = trav_pop(t, stack);
   }
   return t.leaf == 0 && t.cur == kDone;
+}
+
+// ------------------------------------- compressed wide BVH traversal
+// The children of a wide node are visited in the order of their slots'
+// corners (bit a of a corner: the child lies towards +a) as seen along the
+// ray: the corner's bits are flipped on the axes where the ray runs towards
+// -a, then read most significant first along the ray's dominant axis, next
+// the second, last the third.  A near child thus comes before a far one
+// along the axis that matters most, with no sort.
+template <typename R>
+__device__ __forceinline__ void ray_order(Ray<R>& r) {
+  const R ax = Fn<R>::fabs(r.d[0]), ay = Fn<R>::fabs(r.d[1]), az = Fn<R>::fabs(r.d[2]);
+  const uint32_t flip = (r.d[0] < (R)0 ? 1u : 0u) | (r.d[1] < (R)0 ? 2u : 0u) | (r.d[2] < (R)0 ? 4u : 0u);
+  // axes by decreasing |d|
+  uint32_t a0 = 0, a1 = 1, a2 = 2;
+  {
+    R v0 = ax, v1 = ay, v2 = az;
+    if (v1 > v0) { const R t = v0; v0 = v1; v1 = t; const uint32_t u = a0; a0 = a1; a1 = u; }
+    if (v2 > v1) { const R t = v1; v1 = v2; v2 = t; const uint32_t u = a1; a1 = a2; a2 = u; }
+    if (v1 > v0) { const uint32_t u = a0; a0 = a1; a1 = u; }
+  }
+  uint32_t ptab = 0, stab = 0;
+#pragma unroll
+  for (uint32_t c = 0; c < 8; ++c) {
+    const uint32_t t = c ^ flip;
+    const uint32_t pos = (((t >> a0) & 1u) << 2) | (((t >> a1) & 1u) << 1) | ((t >> a2) & 1u);
+    ptab |= pos << (4 * c);
+    stab |= c << (4 * pos);
+  }
+  r.ptab = ptab;
+  r.stab = stab;
+}
+
+// Traversal state of one ray in a wide tree.
+//   gx, gy: the current node group, the hit inner children of one node still
+//           to visit: gx = child_base | (hit positions << 24), gy = (lower
+//           bound on their entry distances, low 8 bits cleared) | imask;
+//   tb, tm: triangles to test: tb + k for every bit k of tm.
+template <typename R>
+struct TravW {
+  R tbest;
+  uint32_t best;
+  uint32_t gx, gy, tb, tm;
+  int sp;
+};
+
+template <typename R>
+__device__ __forceinline__ void travw_begin(TravW<R>& t, const Ray<R>& r) {
+  t.tbest = (R)CUDART_INF;
+  t.best = 0xFFFFFFFFu;
+  t.gx = (1u << (r.ptab & 7u)) << 24;  // the root: an inner child in slot 0 (corner 0) of node base 0
+  t.gy = 1u;
+  t.tb = 0;
+  t.tm = 0;
+  t.sp = 0;
+}
+
+// Next stacked group whose entry bound is still within the best hit.
+template <typename R>
+__device__ __forceinline__ bool travw_pop(TravW<R>& t, const uint2* stack) {
+  while (t.sp > 0) {
+    --t.sp;
+    const uint2 e = stack[t.sp];
+    if ((R)__uint_as_float(e.y & ~0xFFu) <= t.tbest) {
+      t.gx = e.x;
+      t.gy = e.y;
+      return true;
+    }
+  }
+  return false;
+}
+
+// Byte k of w as a float, exactly: 2^23 + b built in the bits, then 2^23 taken off.
+__device__ __forceinline__ float byte_float(uint32_t w, uint32_t k) {
+  return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7440u + k)) - 8388608.0f;
+}
+
+// Near and far slab distances of one child along one axis.
+template <typename R>
+__device__ __forceinline__ R slab_w(uint32_t w, uint32_t k, R sa, R oa) {
+  return fma((R)byte_float(w, k), sa, oa);
+}
+
+// Float bound below t (its low 8 bits are cleared to make room for imask).
+__device__ __forceinline__ uint32_t t_bits_down(float t) { return __float_as_uint(t) & ~0xFFu; }
+__device__ __forceinline__ uint32_t t_bits_down(double t) { return __float_as_uint(__double2float_rd(t)) & ~0xFFu; }
+
+// One node of the group: the next hit child in visit order is fetched and its
+// W child boxes tested; the group's other children are stacked; the hit inner
+// children form the new group and the hit leaves' triangles the triangle mask.
+template <typename R, int W, bool STAGE>
+__device__ __forceinline__ void travw_node(const MeshDev& m, const float4* __restrict__ s_nodes, uint32_t n_stage,
+                                           const Ray<R>& r, TravW<R>& t, uint2* stack, uint32_t& n_nodes, int* err) {
+  constexpr int F4 = W == 8 ? 5 : 4;
+  const uint32_t hits = t.gx >> 24;
+  const uint32_t pos = __ffs(hits) - 1;
+  const uint32_t rest = hits & (hits - 1u);
+  const uint32_t corner = (r.stab >> (4 * pos)) & 7u;
+  const uint32_t slot = W == 8 ? corner : corner >> 1;  // 4-wide slots face corners 0, 3, 5, 6
+  const uint32_t node = (t.gx & 0xFFFFFFu) + __popc(t.gy & 0xFFu & ((1u << slot) - 1u));
+  if (rest != 0u) {
+    if (t.sp >= kMaxStackW) {
+      atomicOr(err, 1);
+      t.gx = 0;
+      t.tm = 0;
+      t.sp = 0;
+      return;
+    }
+    stack[t.sp] = make_uint2((t.gx & 0xFFFFFFu) | (rest << 24), t.gy);
+    ++t.sp;
+  }
+  ++n_nodes;
+  float4 v[F4];
+  if (STAGE && node < n_stage) {
+#pragma unroll
+    for (int i = 0; i < F4; ++i) v[i] = s_nodes[F4 * node + i];
+  } else {
+    const float4* g = m.nodes + (size_t)F4 * node;
+#pragma unroll
+    for (int i = 0; i < F4; ++i) v[i] = __ldg(g + i);
+  }
+  const uint32_t ew = __float_as_uint(v[0].w);
+  const uint32_t imask = ew >> 24;
+  // per axis: grid step times 1/d, and the grid origin's distance
+  R sa[3], oa[3];
+  const float p[3] = {v[0].x, v[0].y, v[0].z};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    sa[a] = (R)__uint_as_float(((ew >> (8 * a)) & 0xFFu) << 23) * r.inv[a];
+    oa[a] = fma((R)p[a], r.inv[a], -r.oi[a]);
+  }
+  // plane words (W = 8: two per plane, slots 0-3 then 4-7; W = 4: one per plane)
+  uint32_t q[12];
+  if constexpr (W == 8) {
+    q[0] = __float_as_uint(v[2].x); q[1] = __float_as_uint(v[2].y);
+    q[2] = __float_as_uint(v[2].z); q[3] = __float_as_uint(v[2].w);
+    q[4] = __float_as_uint(v[3].x); q[5] = __float_as_uint(v[3].y);
+    q[6] = __float_as_uint(v[3].z); q[7] = __float_as_uint(v[3].w);
+    q[8] = __float_as_uint(v[4].x); q[9] = __float_as_uint(v[4].y);
+    q[10] = __float_as_uint(v[4].z); q[11] = __float_as_uint(v[4].w);
+  } else {
+    q[0] = __float_as_uint(v[2].x); q[1] = __float_as_uint(v[2].y);
+    q[2] = __float_as_uint(v[2].z); q[3] = __float_as_uint(v[2].w);
+    q[4] = __float_as_uint(v[3].x); q[5] = __float_as_uint(v[3].y);
+  }
+  constexpr int PP = W == 8 ? 2 : 1;  // words per plane
+  // near and far planes along each axis: lo first where the ray runs towards +a
+  uint32_t qn[3][PP], qf[3][PP];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const bool pos_dir = r.inv[a] >= (R)0;
+#pragma unroll
+    for (int h = 0; h < PP; ++h) {
+      const uint32_t lo = q[PP * a + h], hi = q[PP * (a + 3) + h];
+      qn[a][h] = pos_dir ? lo : hi;
+      qf[a][h] = pos_dir ? hi : lo;
+    }
+  }
+  const uint32_t meta0 = __float_as_uint(v[1].z), meta1 = __float_as_uint(v[1].w);
+  uint32_t new_hits = 0, tris = 0;
+  R tmin_in = (R)CUDART_INF;
+#pragma unroll
+  for (int s = 0; s < W; ++s) {
+    const int h = s >> 2, k = s & 3;
+    const R tn = fmax(fmax(slab_w<R>(qn[0][h], k, sa[0], oa[0]), slab_w<R>(qn[1][h], k, sa[1], oa[1])),
+                      fmax(slab_w<R>(qn[2][h], k, sa[2], oa[2]), r.tlo));
+    const R tf = fmin(fmin(slab_w<R>(qf[0][h], k, sa[0], oa[0]), slab_w<R>(qf[1][h], k, sa[1], oa[1])),
+                      fmin(slab_w<R>(qf[2][h], k, sa[2], oa[2]), t.tbest));
+    const bool hit = tn <= tf;
+    // the slot's corner (kWide4Corner for 4-wide nodes)
+    const uint32_t c = W == 8 ? (uint32_t)s : (s == 0 ? 0u : (s == 1 ? 3u : (s == 2 ? 5u : 6u)));
+    if ((imask >> s) & 1u) {
+      if (hit) {
+        new_hits |= 1u << ((r.ptab >> (4 * c)) & 7u);
+        tmin_in = fmin(tmin_in, tn);
+      }
+    } else if (hit) {
+      const uint32_t meta = ((s < 4 ? meta0 : meta1) >> (8 * k)) & 0xFFu;
+      tris |= (0xFu >> (3u - (meta >> 5))) << (meta & 31u);
+    }
+  }
+  t.gx = __float_as_uint(v[1].x) | (new_hits << 24);
+  t.gy = t_bits_down(tmin_in) | imask;
+  t.tb = __float_as_uint(v[1].y);
+  t.tm = tris;
+}
+
+// Triangles of the mask (a node's hit leaves), in any order: nearest t wins.
+template <typename R>
+__device__ __forceinline__ void travw_tris(const MeshDev& m, const Ray<R>& r, uint32_t last, TravW<R>& t,
+                                           uint32_t& n_tris) {
+  const Shear<R> sh = make_shear<R>(r.d);
+  while (t.tm != 0u) {
+    const uint32_t k = __ffs(t.tm) - 1;
+    t.tm &= t.tm - 1u;
+    R V0[3], V1[3], V2[3];
+    const uint32_t id = TriLoad<R>::load(m, t.tb + k, V0, V1, V2);
+    if (id == last) continue;
+    ++n_tris;
+    test_triangle<R>(r, sh, V0, V1, V2, id, t.tbest, t.best);
+  }
 }
 
 // ------------------------------------------------ re-emission (§II.A)
@@ -1016,16 +1221,27 @@ __device__ __forceinline__ bool ray_meets_box(const Ray<R>& r, const MeshDev& m)
 // least MINB resident blocks per SM (more warps to hide latency, at the cost
 // of spills inside the out-of-line seeding).  MINB = 0: 256-thread blocks,
 // two per SM in float (at most 128 registers), one in double.
-template <typename R, int MINB, bool CLL>
+template <int W, typename R, typename TV>
+__device__ __forceinline__ void begin_trav(Ray<R>& r, TV& tv) {
+  if constexpr (W > 2) {
+    ray_order(r);
+    travw_begin(tv, r);
+  } else {
+    trav_begin(tv);
+  }
+}
+
+template <typename R, int MINB, bool CLL, int W>
 __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeof(R) == 4 ? 2 : 1))
     trace_kernel(TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr uint32_t kNodeF4 = W == 8 ? 5 : 4;  // float4 per node
   const uint32_t n_stage = min(a.smem_nodes, a.mesh.n_nodes);
   float4* s_nodes = reinterpret_cast<float4*>(smem);
-  for (uint32_t i = threadIdx.x; i < 4 * n_stage; i += blockDim.x) s_nodes[i] = __ldg(&a.mesh.nodes[i]);
-  Seeded<R>* queue = reinterpret_cast<Seeded<R>*>(smem + (size_t)n_stage * 4 * sizeof(float4)) +
+  for (uint32_t i = threadIdx.x; i < kNodeF4 * n_stage; i += blockDim.x) s_nodes[i] = __ldg(&a.mesh.nodes[i]);
+  Seeded<R>* queue = reinterpret_cast<Seeded<R>*>(smem + (size_t)n_stage * kNodeF4 * sizeof(float4)) +
                      (threadIdx.x >> 5) * kQueue;
-  LaneAcc& acc = reinterpret_cast<LaneAcc*>(smem + (size_t)n_stage * 4 * sizeof(float4) +
+  LaneAcc& acc = reinterpret_cast<LaneAcc*>(smem + (size_t)n_stage * kNodeF4 * sizeof(float4) +
                                             (size_t)(blockDim.x >> 5) * kQueue * sizeof(Seeded<R>))[threadIdx.x];
   lane_reset(acc, -1);
   __syncthreads();
@@ -1049,9 +1265,10 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
   uint32_t bounce = 0, last = 0xFFFFFFFFu;
   R dvp[3] = {0, 0, 0};
   Ray<R> ray;
-  Trav<R> tv;
-  trav_begin(tv);
-  StackE<R> stack[kMaxStack];
+  using TV = std::conditional_t<(W > 2), TravW<R>, Trav<R>>;
+  using SE = std::conditional_t<(W > 2), uint2, StackE<R>>;
+  TV tv{};
+  SE stack[W > 2 ? kMaxStackW : kMaxStack];
   uint32_t n_nodes = 0, n_tris = 0;
 
   for (;;) {
@@ -1106,7 +1323,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
           if (!escapes) {
             const R speed = Fn<R>::sqrt(vv);
             make_ray<R>(ray, hp, v, (sizeof(R) == 4 ? (R)1e-6 : (R)1e-9) / speed);
-            trav_begin(tv);
+            begin_trav<W>(ray, tv);
             tdone = a.mesh.n_nodes == 0;
             finish = false;
           }
@@ -1181,7 +1398,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
         qi = nq;
         const R speed = Fn<R>::sqrt(vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
         make_ray<R>(ray, pos, vel, (sizeof(R) == 4 ? (R)1e-6 : (R)1e-9) / speed);
-        trav_begin(tv);
+        begin_trav<W>(ray, tv);
         tdone = a.mesh.n_nodes == 0;
         has = true;
         bounce = 0;
@@ -1210,8 +1427,35 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
       continue;
     }
 
-    // ---- 4. traversal round: inner nodes until every searching lane holds a
-    // leaf (lanes with a leaf keep descending meanwhile), then the leaves
+    // ---- 4. traversal round
+    if constexpr (W > 2) {
+      // Wide tree: lanes without triangles to test step through nodes until
+      // each holds a triangle mask or has nothing left; then the triangles.
+      for (;;) {
+        for (;;) {
+          const bool want = has && !tdone && tv.tm == 0u && ((tv.gx >> 24) != 0u || tv.sp > 0);
+          if (!__any_sync(kFull, want)) break;
+          if (want) {
+            if ((tv.gx >> 24) != 0u || travw_pop(tv, stack)) {
+              if (n_stage == 0)
+                travw_node<R, W, false>(a.mesh, s_nodes, n_stage, ray, tv, stack, n_nodes, a.error);
+              else
+                travw_node<R, W, true>(a.mesh, s_nodes, n_stage, ray, tv, stack, n_nodes, a.error);
+            }
+          }
+        }
+        if (has && !tdone) {
+          if (tv.tm != 0u) travw_tris<R>(a.mesh, ray, last, tv, n_tris);
+          tdone = (tv.gx >> 24) == 0u && tv.sp == 0;
+        }
+        const unsigned fin = __ballot_sync(kFull, has && tdone);
+        const unsigned run = __ballot_sync(kFull, has && !tdone);
+        if (run == 0u || (uint32_t)__popc(fin) >= a.refill_at) break;
+      }
+      continue;
+    } else
+    // ---- binary tree: inner nodes until every searching lane holds a leaf
+    // (lanes with a leaf keep descending meanwhile), then the leaves
     for (;;) {
       // without staged nodes, the shared-memory check leaves the node loop
       if (n_stage == 0) {
@@ -1522,7 +1766,8 @@ size_t trace_smem_bytes(const LaunchCfg& cfg, uint32_t n_nodes, uint32_t variant
   const uint32_t precision = variant & 1u;
   const size_t queue = (size_t)(cfg.block / 32) * kQueue *
                        (precision == TPMC_FP64 ? sizeof(Seeded<double>) : sizeof(Seeded<float>));
-  return (size_t)std::min(cfg.smem_nodes, n_nodes) * 4 * sizeof(float4) + queue + (size_t)cfg.block * sizeof(LaneAcc);
+  return (size_t)std::min(cfg.smem_nodes, n_nodes) * node_float4s(variant_width(variant)) * sizeof(float4) + queue +
+         (size_t)cfg.block * sizeof(LaneAcc);
 }
 
 namespace {
@@ -1530,19 +1775,28 @@ using TraceFn = void (*)(TraceArgs);
 
 // Kernel instantiation for a schedule: the register-capped float variants
 // serve 128-thread blocks at 5 to 8 blocks per SM.
-template <bool CLL>
+template <bool CLL, int W>
 TraceFn pick_trace_t(uint32_t precision, uint32_t block, uint32_t blocks_per_sm) {
-  if (precision == TPMC_FP64) return trace_kernel<double, 0, CLL>;
-  if (block <= 128 && blocks_per_sm >= 8) return trace_kernel<float, 8, CLL>;
-  if (block <= 128 && blocks_per_sm == 7) return trace_kernel<float, 7, CLL>;
-  if (block <= 128 && blocks_per_sm == 6) return trace_kernel<float, 6, CLL>;
-  if (block <= 128 && blocks_per_sm == 5) return trace_kernel<float, 5, CLL>;
-  return trace_kernel<float, 0, CLL>;
+  if (precision == TPMC_FP64) return trace_kernel<double, 0, CLL, W>;
+  if (block <= 128 && blocks_per_sm >= 8) return trace_kernel<float, 8, CLL, W>;
+  if (block <= 128 && blocks_per_sm == 7) return trace_kernel<float, 7, CLL, W>;
+  if (block <= 128 && blocks_per_sm == 6) return trace_kernel<float, 6, CLL, W>;
+  if (block <= 128 && blocks_per_sm == 5) return trace_kernel<float, 5, CLL, W>;
+  return trace_kernel<float, 0, CLL, W>;
+}
+
+template <int W>
+TraceFn pick_trace_w(uint32_t variant, uint32_t block, uint32_t blocks_per_sm) {
+  return (variant & kVariantCll) ? pick_trace_t<true, W>(variant & 1u, block, blocks_per_sm)
+                                 : pick_trace_t<false, W>(variant & 1u, block, blocks_per_sm);
 }
 
 TraceFn pick_trace(uint32_t variant, uint32_t block, uint32_t blocks_per_sm) {
-  return (variant & kVariantCll) ? pick_trace_t<true>(variant & 1u, block, blocks_per_sm)
-                                 : pick_trace_t<false>(variant & 1u, block, blocks_per_sm);
+  switch (variant_width(variant)) {
+    case 8: return pick_trace_w<8>(variant, block, blocks_per_sm);
+    case 4: return pick_trace_w<4>(variant, block, blocks_per_sm);
+    default: return pick_trace_w<2>(variant, block, blocks_per_sm);
+  }
 }
 
 int occupancy(TraceFn f, uint32_t block, size_t smem) {
@@ -1575,6 +1829,9 @@ int trace_max_blocks_per_sm(uint32_t variant, const LaunchCfg& cfg, uint32_t n_n
 
 cudaError_t launch_trace(const TraceArgs& args, uint32_t variant, const LaunchCfg& cfg, int num_sms,
                          cudaStream_t stream) {
+  // the mesh's own layout decides which traversal reads its nodes
+  variant = (variant & ~(kVariantWide4 | kVariantWide8)) |
+            (args.mesh.width == 8 ? kVariantWide8 : (args.mesh.width == 4 ? kVariantWide4 : 0u));
   const size_t smem = trace_smem_bytes(cfg, args.mesh.n_nodes, variant);
   const uint32_t grid = (uint32_t)num_sms * cfg.blocks_per_sm;
   const TraceFn f = pick_trace(variant, cfg.block, cfg.blocks_per_sm);

@@ -113,11 +113,11 @@ extern "C" tpmc_status tpmc_sweep_noalloc(tpmc_ctx* ctx, tpmc_mesh_id mesh, cons
   a.error = &A->error;
   a.count_work = c->counters ? 1u : 0u;
   a.vn_table = c->vn_table;
-  const LaunchCfg cfg = c->schedule(m, trace_variant(base), a.total);
+  const LaunchCfg cfg = c->schedule(m, trace_variant(base, m.dev), a.total);
   a.chunk = cfg.chunk;
   a.smem_nodes = cfg.smem_nodes;
   a.refill_at = cfg.refill_at;
-  if ((e = launch_trace(a, trace_variant(base), cfg, c->num_sms, s)) != cudaSuccess) return cuda_fail(e, "trace kernel");
+  if ((e = launch_trace(a, trace_variant(base, m.dev), cfg, c->num_sms, s)) != cudaSuccess) return cuda_fail(e, "trace kernel");
   if ((e = launch_finalize(A->queries, A->acc, K, nullptr, A->results, s)) != cudaSuccess)
     return cuda_fail(e, "finalize kernel");
   int err_word = 0;

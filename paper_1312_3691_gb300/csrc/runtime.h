@@ -24,7 +24,7 @@ struct MeshRec {
   void* d_block = nullptr;     // one device allocation holding every mesh array
   size_t bytes = 0;
   double center[3] = {0, 0, 0}, radius = 0;
-  uint32_t depth = 0, leaf_max = 0, n_skipped = 0, n_vert = 0, n_exposed = 0;
+  uint32_t depth = 0, leaf_max = 0, n_skipped = 0, n_vert = 0, n_exposed = 0, node_bytes = 64;
   std::vector<double> h_xyz;   // host copy for the control-volume containment check
   std::vector<uint32_t> h_tri;
   int in_use = 0;              // queries in flight on this mesh (serving)
@@ -43,6 +43,9 @@ struct Scratch {
 };
 
 struct ServeState;  // serve.cpp
+
+// BVH width of mesh loads that neither tpmc_set_launch nor tpmc_tune decided.
+constexpr uint32_t kDefaultBvhWidth = 2;
 
 tpmc_status fill_query(const MeshRec& m, const tpmc_params* p, uint64_t N, QueryDev* q);
 
@@ -69,6 +72,8 @@ struct Ctx {
   bool counters = false;
   bool manual_launch = false;
   uint32_t bvh_leaf = 4;       // largest leaf of the BVHs built by later mesh loads
+  uint32_t bvh_width = 0;      // children per node of later mesh loads (0: tuned or default)
+  std::map<uint64_t, uint32_t> tuned_width;  // BVH width chosen by tpmc_tune per size class
   LaunchCfg manual;
   LaunchCfg last_cfg;
   std::map<uint64_t, LaunchCfg> tuned;
@@ -78,6 +83,9 @@ struct Ctx {
   int* h_err_word = nullptr;
   ServeState* serve = nullptr;
 
+  uint32_t width_for(uint32_t n_tri) const;
+  tpmc_status upload_mesh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t n_tri, uint32_t width,
+                          MeshRec* out);
   tpmc_status alloc(void** p, size_t bytes, const char* what);
   void release(void* p);
   tpmc_status grow(Scratch& s, size_t bytes, const char* what);

@@ -486,12 +486,12 @@ tpmc_status tpmc_submit(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* par
     if (it == c->meshes.end()) return fail(TPMC_ENOTFOUND, "unknown mesh id");
     if ((st = fill_query(it->second, params, N, &r->q)) != TPMC_OK) return st;
     r->n_tri = it->second.dev.n_tri;
+    r->variant = trace_variant(params, it->second.dev);
     if (!c->serve && (st = start_serving(c)) != TPMC_OK) return st;
     ++it->second.in_use;
     r->id = c->next_query++;
   }
   r->mesh = mesh;
-  r->variant = trace_variant(params);
   r->want_panels = params->want_panels != 0;
   r->N = N;
   r->t_submit = Clock::now();

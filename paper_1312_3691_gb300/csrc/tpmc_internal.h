@@ -39,8 +39,34 @@ constexpr int kMaxRecordK = 64;  // hits recorded per particle in verification r
 //        of the leaf-ordered triangle arrays; count <= 127.
 // Nodes are numbered breadth first, so nodes [0, k) are the top of the tree
 // and can be staged in shared memory as a block.
+// Compressed wide BVH node (after Ylitie, Karras & Laine, "Efficient
+// incoherent ray traversal on GPUs through compressed wide BVHs", HPG 2017):
+// the child boxes are 8-bit coordinates on a grid of the node's own, so one
+// node fetch decides up to W children.  W = 8: 80 bytes (5 float4); W = 4:
+// 64 bytes (4 float4).
+//   w0 = (px, py, pz, e)  grid origin p (float); e: bytes ex, ey, ez (biased
+//                         exponents: the grid step along axis a is 2^(ea - 127))
+//                         and imask (bit s: slot s holds an inner node)
+//   w1 = (child_base, tri_base, meta[0..3], meta[4..7] (W = 8 only))
+//   then the planes qlo_x, qlo_y, qlo_z, qhi_x, qhi_y, qhi_z, one byte per
+//   slot: W = 8: two words per plane (slots 0-3, 4-7) in w2.xyzw, w3.xyzw,
+//   w4.xyzw; W = 4: one word per plane in w2.xyzw, w3.xy.
+// Child box of slot s along axis a: [p_a + 2^e_a qlo_a[s], p_a + 2^e_a qhi_a[s]]
+// (rounded outward from the padded float box); an empty slot has qlo = 255 >
+// qhi = 0 on every axis.  Inner slot s: node child_base + (number of inner
+// slots below s); children of a node are consecutive (breadth-first order).
+// Leaf slot s: meta[s] = (count - 1) << 5 | offset, its triangles are
+// tri_base + offset ... + count - 1 in the triangle arrays (count <= 4,
+// offset + count <= 32: a node's leaf triangles form one block).
+// Slot s of an 8-wide node lies towards the box corner s (bit 0: +x, bit 1:
+// +y, bit 2: +z) of its parent; slot s of a 4-wide node towards corner
+// kWide4Corner[s].  The traversal orders children by these corners.
+constexpr int kWideLeafMax = 4;
+constexpr int kMaxStackW = 32;     // wide traversal stack (the builder keeps the depth below)
+constexpr uint32_t kWide4Corner[4] = {0u, 3u, 5u, 6u};
+
 struct MeshDev {
-  const float4* nodes = nullptr;    // [n_nodes][4]
+  const float4* nodes = nullptr;    // binary: [n_nodes][4]; wide: [n_nodes][width == 8 ? 5 : 4]
   const float4* tris = nullptr;     // [n_tri_leaf][3]: (v0, id bits), (v1, 0), (v2, 0)
   const double* tris64 = nullptr;   // [n_tri_leaf][12]: v0, v1, v2, id, 0, 0
   const float4* frames = nullptr;   // [n_tri][2] by input index: (n, area), (t1, exposed-side bits)
@@ -48,6 +74,7 @@ struct MeshDev {
   uint32_t n_nodes = 0;
   uint32_t n_tri = 0;               // input numbering (panel arrays use it)
   uint32_t n_tri_leaf = 0;          // triangles referenced by leaves (zero-area ones dropped)
+  uint32_t width = 2;               // 2: binary nodes; 4 or 8: compressed wide nodes
   float scene_radius = 1.0f;
   float box_lo[3] = {0.0f, 0.0f, 0.0f}, box_hi[3] = {-1.0f, -1.0f, -1.0f};  // padded root box (empty: no mesh)
 };
@@ -158,13 +185,18 @@ struct LaunchCfg {
 };
 
 // ------------------------------------------------------------ host launchers
-// Trace-kernel variant: the precision (TPMC_FP32 / TPMC_FP64) plus
-// kVariantCll when the launch holds a query with the CLL surface model, so
-// that launches without one run code compiled without that branch.
+// Trace-kernel variant: the precision (TPMC_FP32 / TPMC_FP64), plus
+// kVariantCll when the launch holds a query with the CLL surface model (so
+// that launches without one run code compiled without that branch), plus the
+// mesh's BVH layout (kVariantWide4 / kVariantWide8 for compressed wide nodes).
 constexpr uint32_t kVariantCll = 2u;
-inline uint32_t trace_variant(const tpmc_params* p) {
-  return p->precision | (p->gsi_model == TPMC_GSI_CLL ? kVariantCll : 0u);
+constexpr uint32_t kVariantWide4 = 4u, kVariantWide8 = 8u;
+inline uint32_t trace_variant(const tpmc_params* p, const MeshDev& m) {
+  return p->precision | (p->gsi_model == TPMC_GSI_CLL ? kVariantCll : 0u) |
+         (m.width == 8 ? kVariantWide8 : (m.width == 4 ? kVariantWide4 : 0u));
 }
+inline uint32_t variant_width(uint32_t v) { return (v & kVariantWide8) ? 8u : ((v & kVariantWide4) ? 4u : 2u); }
+inline uint32_t node_float4s(uint32_t width) { return width == 8 ? 5u : 4u; }
 
 cudaError_t launch_setup(QueryDev* d_queries, uint32_t nq, const QueryDev* d_base, const double* d_dirs,
                          const double* d_S, ItemDev* d_items, const uint32_t* d_slots, cudaStream_t stream);
@@ -182,10 +214,13 @@ int trace_max_blocks_per_sm(uint32_t variant, const LaunchCfg& cfg, uint32_t n_n
 // ---------------------------------------------------------------- BVH (host)
 struct BvhBuild {
   std::size_t n_nodes = 0;
+  uint32_t width = 2;        // children per node: 2 (binary layout) or 4, 8 (compressed wide layout)
+  uint32_t node_bytes = 64;  // bytes per node in `nodes`
+  float root_lo[3] = {0.0f, 0.0f, 0.0f}, root_hi[3] = {-1.0f, -1.0f, -1.0f};  // padded root box (empty: no mesh)
   uint32_t depth = 0, leaf_max = 0, n_skipped = 0;
   uint32_t n_exposed = 0;    // triangle sides the whole mesh lies behind
   // host copies ready for upload
-  float* nodes = nullptr;    // [n_nodes * 16]
+  float* nodes = nullptr;    // [n_nodes * node_bytes / 4]
   float* tris = nullptr;     // [n_leaf_tris * 12]
   double* tris64 = nullptr;  // [n_leaf_tris * 12]
   float* frames = nullptr;   // [n_tri * 8]: n, area, t1, exposed-side bits (uint32 in word 7)
@@ -196,8 +231,10 @@ struct BvhBuild {
 };
 
 // Builds a BVH over the mesh by the surface-area heuristic with spatial
-// splits.  Returns false (with a message) on invalid input.
+// splits and lays it out with `width` children per node (2: binary nodes;
+// 4 or 8: compressed wide nodes collapsed from the binary tree).  Returns
+// false (with a message) on invalid input.
 bool build_bvh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t n_tri, uint32_t max_leaf,
-               BvhBuild* out, const char** err);
+               uint32_t width, BvhBuild* out, const char** err);
 
 }  // namespace tpmc

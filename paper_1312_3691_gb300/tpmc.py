@@ -79,7 +79,8 @@ class tpmc_mesh_stats(ctypes.Structure):
 
 class tpmc_launch(ctypes.Structure):
     _fields_ = [("block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
-                ("smem_nodes", ctypes.c_uint32), ("refill_at", ctypes.c_uint32), ("bvh_leaf", ctypes.c_uint32)]
+                ("smem_nodes", ctypes.c_uint32), ("refill_at", ctypes.c_uint32), ("bvh_leaf", ctypes.c_uint32),
+                ("bvh_width", ctypes.c_uint32)]
 
 
 # (name, argtypes) of every entry point declared in include/tpmc.h
@@ -329,11 +330,14 @@ def tpmc_tune(ctx, mesh: int, params: tpmc_params, N_trial: int) -> dict:
     return {n: getattr(b, n) for n, _ in b._fields_}
 
 
-def tpmc_set_launch(ctx, block=None, blocks_per_sm=0, chunk=0, smem_nodes=0, refill_at=0, bvh_leaf=0):
+def tpmc_set_launch(ctx, block=None, blocks_per_sm=0, chunk=0, smem_nodes=0, refill_at=0, bvh_leaf=0, bvh_width=0):
+    """block=None returns to automatic schedules (and the default BVH layout);
+    block=0 with bvh_leaf / bvh_width sets only the BVH layout of later loads."""
     if block is None:
         _check(lib().tpmc_set_launch(ctx, None), "tpmc_set_launch", ctx)
         return
-    b = tpmc_launch(int(block), int(blocks_per_sm), int(chunk), int(smem_nodes), int(refill_at), int(bvh_leaf))
+    b = tpmc_launch(int(block), int(blocks_per_sm), int(chunk), int(smem_nodes), int(refill_at), int(bvh_leaf),
+                    int(bvh_width))
     _check(lib().tpmc_set_launch(ctx, ctypes.byref(b)), "tpmc_set_launch", ctx)
 
 

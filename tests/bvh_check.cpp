@@ -13,11 +13,16 @@
 // never more than 127), and that every triangle side marked exposed has the
 // whole mesh behind its plane.
 //
-// usage: bvh_check MESH RAYS MAX_LEAF
+// With WIDTH 4 or 8 the tree is laid out as compressed wide nodes, and the
+// walk decodes each child box from the node's 8-bit grid exactly as the GPU
+// reads it (origin p, step 2^e, bytes qlo / qhi), in double: a quantised box
+// that does not contain its child's triangles shows up the same way.
+//
+// usage: bvh_check MESH RAYS MAX_LEAF [WIDTH]
 //   MESH: uint32 n_vert, uint32 n_tri, double xyz[n_vert][3], uint32 tri[n_tri][3]
 //   RAYS: uint32 n_rays, double ray[n_rays][6] (origin, direction)
 // prints one line: rays mismatches hits n_tri n_refs n_nodes depth leaf_max unreferenced oversized
-//                  exposed wrong_exposed
+//                  exposed wrong_exposed width node_bytes bad_index
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -76,6 +81,7 @@ int main(int argc, char** argv) {
   std::vector<unsigned char> mb, rb;
   if (!read_all(argv[1], mb) || !read_all(argv[2], rb)) return 3;
   const uint32_t max_leaf = (uint32_t)std::atoi(argv[3]);
+  const uint32_t width = argc > 4 ? (uint32_t)std::atoi(argv[4]) : 2u;
   uint32_t nv, nt, nr;
   std::memcpy(&nv, mb.data(), 4);
   std::memcpy(&nt, mb.data() + 4, 4);
@@ -89,7 +95,7 @@ int main(int argc, char** argv) {
 
   tpmc::BvhBuild b;
   const char* err = nullptr;
-  if (!tpmc::build_bvh(xyz.data(), nv, tri.data(), nt, max_leaf, &b, &err)) {
+  if (!tpmc::build_bvh(xyz.data(), nv, tri.data(), nt, max_leaf, width, &b, &err)) {
     std::printf("build failed: %s\n", err ? err : "?");
     return 4;
   }
@@ -116,7 +122,7 @@ int main(int argc, char** argv) {
   // leaves within the size limit
   uint32_t oversized = 0;
   std::vector<int32_t> stack;
-  for (size_t g = 0; g < b.n_nodes; ++g)
+  for (size_t g = 0; g < b.n_nodes && b.width == 2; ++g)
     for (int c = 0; c < 2; ++c) {
       int32_t code;
       std::memcpy(&code, b.nodes + 16 * g + 12 + c, 4);
@@ -144,14 +150,63 @@ int main(int argc, char** argv) {
     }
   }
 
-  uint64_t mismatches = 0, hits = 0;
+  uint64_t mismatches = 0, hits = 0, bad_index = 0;  // bad_index: a child or triangle outside its array
   for (uint32_t r = 0; r < nr; ++r) {
     const double* o = rays.data() + 6 * (size_t)r;
     const double* d = o + 3;
     Best brute;
     for (uint32_t t = 0; t < nt; ++t) brute.offer(hit(o, d, vert(t, 0), vert(t, 1), vert(t, 2)), t);
     Best walk;
-    if (b.n_nodes > 0) {
+    auto slab = [&](const double lo[3], const double hi[3]) {
+      double tn = 0.0, tf = walk.t;
+      for (int i = 0; i < 3; ++i) {
+        if (d[i] == 0.0) {
+          if (o[i] < lo[i] || o[i] > hi[i]) tn = INFINITY;
+          continue;
+        }
+        const double t0 = (lo[i] - o[i]) / d[i], t1 = (hi[i] - o[i]) / d[i];
+        tn = std::fmax(tn, std::fmin(t0, t1));
+        tf = std::fmin(tf, std::fmax(t0, t1));
+      }
+      return tn <= tf;
+    };
+    if (b.n_nodes > 0 && b.width > 2) {
+      const uint32_t W = b.width, F = b.node_bytes / 4, per_plane = W == 8 ? 2 : 1;
+      stack.assign(1, 0);
+      while (!stack.empty()) {
+        const uint32_t* nd = reinterpret_cast<const uint32_t*>(b.nodes) + (size_t)F * stack.back();
+        stack.pop_back();
+        auto byte = [&](uint32_t word, uint32_t k) { return (nd[word] >> (8 * k)) & 0xFFu; };
+        float p[3];
+        std::memcpy(p, nd, 12);
+        const uint32_t imask = nd[3] >> 24;
+        for (uint32_t s = 0; s < W; ++s) {
+          double lo[3], hi[3];
+          bool empty = false;
+          for (int a = 0; a < 3; ++a) {
+            const double step = std::ldexp(1.0, (int)byte(3, a) - 127);
+            const uint32_t ql = byte(8 + per_plane * a + s / 4, s % 4), qh = byte(8 + per_plane * (a + 3) + s / 4, s % 4);
+            empty = empty || ql > qh;
+            lo[a] = (double)p[a] + step * ql;
+            hi[a] = (double)p[a] + step * qh;
+          }
+          if (empty || !slab(lo, hi)) continue;
+          if ((imask >> s) & 1u) {
+            const uint32_t child = nd[4] + __builtin_popcount(imask & ((1u << s) - 1u));
+            if (child >= b.n_nodes || child == 0) { ++bad_index; continue; }
+            stack.push_back((int32_t)child);
+          } else {
+            const uint32_t meta = byte(6 + s / 4, s % 4), first = nd[5] + (meta & 31u), count = (meta >> 5) + 1;
+            if ((meta & 31u) + count > 32u || first + count > b.n_leaf_tris) { ++bad_index; continue; }
+            for (uint32_t k = first; k < first + count; ++k) {
+              uint32_t id;
+              std::memcpy(&id, b.tris + 12 * (size_t)k + 3, 4);
+              walk.offer(hit(o, d, vert(id, 0), vert(id, 1), vert(id, 2)), id);
+            }
+          }
+        }
+      }
+    } else if (b.n_nodes > 0) {
       stack.assign(1, 0);
       while (!stack.empty()) {
         const int32_t node = stack.back();
@@ -190,8 +245,9 @@ int main(int argc, char** argv) {
     if (brute.id != 0xFFFFFFFFu) ++hits;
     if (brute.id != walk.id || !(brute.t == walk.t || (std::isinf(brute.t) && std::isinf(walk.t)))) ++mismatches;
   }
-  std::printf("%u %llu %llu %u %u %zu %u %u %u %u %u %u\n", nr, (unsigned long long)mismatches, (unsigned long long)hits,
-              nt, b.n_leaf_tris, b.n_nodes, b.depth, b.leaf_max, unreferenced, oversized, exposed, wrong_exposed);
+  std::printf("%u %llu %llu %u %u %zu %u %u %u %u %u %u %u %u %llu\n", nr, (unsigned long long)mismatches,
+              (unsigned long long)hits, nt, b.n_leaf_tris, b.n_nodes, b.depth, b.leaf_max, unreferenced, oversized,
+              exposed, wrong_exposed, b.width, b.node_bytes, (unsigned long long)bad_index);
   b.release();
   return 0;
 }

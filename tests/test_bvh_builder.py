@@ -62,16 +62,16 @@ def _rays(xyz, tri, rng, n_random=6000, n_vertex=1500, n_edge=1500, n_axis=1000)
     return np.vstack(out)
 
 
-def _check(checker, tmp_path, xyz, tri, rays, leaf=4):
+def _check(checker, tmp_path, xyz, tri, rays, leaf=4, width=2):
     xyz = np.ascontiguousarray(xyz, np.float64)
     tri = np.ascontiguousarray(tri, np.uint32)
     mesh = tmp_path / "mesh.bin"
     ray = tmp_path / "rays.bin"
     mesh.write_bytes(np.array([len(xyz), len(tri)], np.uint32).tobytes() + xyz.tobytes() + tri.tobytes())
     ray.write_bytes(np.array([len(rays)], np.uint32).tobytes() + np.ascontiguousarray(rays, np.float64).tobytes())
-    out = subprocess.check_output([str(checker), str(mesh), str(ray), str(leaf)], text=True).split()
+    out = subprocess.check_output([str(checker), str(mesh), str(ray), str(leaf), str(width)], text=True).split()
     keys = ["rays", "mismatches", "hits", "n_tri", "n_refs", "n_nodes", "depth", "leaf_max", "unreferenced",
-            "oversized", "exposed", "wrong_exposed"]
+            "oversized", "exposed", "wrong_exposed", "width", "node_bytes", "bad_index"]
     return dict(zip(keys, (int(x) for x in out)))
 
 
@@ -105,14 +105,18 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("width", [2, 4, 8])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_tree_closest_hits_equal_brute_force(checker, tmp_path, name):
+def test_tree_closest_hits_equal_brute_force(checker, tmp_path, name, width):
+    """Binary and compressed wide layouts (the wide walk decodes the 8-bit
+    child boxes as the GPU does)."""
     rng = np.random.default_rng(sorted(CASES).index(name) + 11)
     xyz, tri = CASES[name](rng)
     xyz, tri = np.asarray(xyz, float), np.asarray(tri)
     rays = _rays(xyz, tri, np.random.default_rng(17))
-    r = _check(checker, tmp_path, xyz, tri, rays)
-    assert r["mismatches"] == 0, r
+    r = _check(checker, tmp_path, xyz, tri, rays, width=width)
+    assert r["width"] == width and r["node_bytes"] == {2: 64, 4: 64, 8: 80}[width], r
+    assert r["mismatches"] == 0 and r["bad_index"] == 0, r
     assert r["unreferenced"] == 0 and r["oversized"] == 0, r
     assert r["hits"] > 0.2 * r["rays"], r
     assert len(tri) - 1 <= r["n_refs"] <= 1.5 * len(tri) + 1, r
@@ -157,10 +161,30 @@ def test_spatial_splits_cut_the_fans(checker, tmp_path):
         assert len(tri) < r["n_refs"] <= 1.5 * len(tri) + 1, r
 
 
+@pytest.mark.parametrize("width", [2, 8])
 @pytest.mark.parametrize("leaf", [1, 2, 8])
-def test_leaf_sizes(checker, tmp_path, leaf):
+def test_leaf_sizes(checker, tmp_path, leaf, width):
+    """Wide layouts keep leaves of at most 4 references whatever the binary
+    leaf size: larger binary leaves are split into leaves with the same box,
+    and subtrees of at most 4 references are merged into one leaf."""
     xyz, tri = M.cylinder()
     xyz, tri = np.asarray(xyz, float), np.asarray(tri)
-    r = _check(checker, tmp_path, xyz, tri, _rays(xyz, tri, np.random.default_rng(5), 3000, 500, 500, 500), leaf)
+    r = _check(checker, tmp_path, xyz, tri, _rays(xyz, tri, np.random.default_rng(5), 3000, 500, 500, 500), leaf,
+               width)
     assert r["mismatches"] == 0 and r["unreferenced"] == 0, r
-    assert r["leaf_max"] <= max(leaf, 1) or r["depth"] >= 40, r
+    assert r["leaf_max"] <= (max(leaf, 1) if width == 2 else 4) or r["depth"] >= 40, r
+
+
+def test_wide_trees_are_shallow(checker, tmp_path):
+    """Collapsing the binary tree into 8-wide nodes at least halves its depth
+    and divides its node count by more than five; the 4-wide tree lies between."""
+    xyz, tri = M.satellite(60_000)
+    xyz, tri = np.asarray(xyz, float), np.asarray(tri)
+    rays = _rays(xyz, tri, np.random.default_rng(9), 400, 100, 100, 100)
+    r2, r4, r8 = (_check(checker, tmp_path, xyz, tri, rays, width=w) for w in (2, 4, 8))
+    for r in (r2, r4, r8):
+        assert r["mismatches"] == 0, r
+    assert r8["depth"] < r4["depth"] < r2["depth"] and 2 * r8["depth"] <= r2["depth"] + 1, (r2, r4, r8)
+    assert r8["n_nodes"] * 5 < r2["n_nodes"] and r8["n_nodes"] < r4["n_nodes"] < r2["n_nodes"], (r2, r4, r8)
+    assert r2["n_refs"] == r4["n_refs"] == r8["n_refs"]
+    print({w: (r["depth"], r["n_nodes"]) for w, r in ((2, r2), (4, r4), (8, r8))})

@@ -33,9 +33,12 @@ def T():
     return tpmc
 
 
-@pytest.fixture(scope="module")
-def ctx(T):
+@pytest.fixture(scope="module", params=[2, 4, 8], ids=lambda w: f"w{w}")
+def ctx(T, request):
+    """A context whose meshes are laid out with 2 (binary), 4 or 8 children per
+    BVH node: every parity test runs on each layout."""
     c = T.tpmc_create(0)
+    T.tpmc_set_launch(c, block=0, bvh_width=request.param)
     yield c
     T.tpmc_destroy(c)
 
@@ -295,16 +298,20 @@ def test_memory_budget_is_enforced(T):
 def test_results_are_deterministic_and_schedule_independent(T, ctx):
     case = W.satellite_case(N=300_000)
     mesh = T.tpmc_mesh_load(ctx, case["xyz"], case["tri"])
+    width = T.tpmc_mesh_info(ctx, mesh)["bvh_width"]
     try:
         p = T.make_params(**case["params"])
         r1 = T.tpmc_trace(ctx, mesh, p, case["N"])
-        T.tpmc_set_launch(ctx, block=64, blocks_per_sm=1, chunk=32, smem_nodes=0)
+        T.tpmc_set_launch(ctx, block=64, blocks_per_sm=1, chunk=32, smem_nodes=0, bvh_width=width)
         r2 = T.tpmc_trace(ctx, mesh, p, case["N"])
+        T.tpmc_set_launch(ctx, block=128, blocks_per_sm=4, chunk=64, smem_nodes=200, refill_at=8, bvh_width=width)
+        r4 = T.tpmc_trace(ctx, mesh, p, case["N"])
         T.tpmc_set_launch(ctx, None)
+        T.tpmc_set_launch(ctx, block=0, bvh_width=width)
         r3 = T.tpmc_trace(ctx, mesh, p, case["N"])
     finally:
         T.tpmc_mesh_unload(ctx, mesh)
-    for r in (r2, r3):
+    for r in (r2, r3, r4):
         assert r["sum_dv_q"] == r1["sum_dv_q"] and r["sum_rdv_q"] == r1["sum_rdv_q"]
         assert r["force"] == r1["force"] and r["CD"] == r1["CD"]
         # the squared contributions are integer sums too: sigma is schedule-independent bit for bit
@@ -349,6 +356,32 @@ def test_sweep_equals_separate_queries(T, ctx):
             assert abs(sw[k]["S"] - S[k]) < 1e-12
     finally:
         T.tpmc_mesh_unload(ctx, mesh)
+
+
+def test_bvh_layouts_give_identical_results(T):
+    """The closest hit does not depend on the tree: the binary and both wide
+    layouts give the same integer sums, hit counts and sigma, bit for bit, on a
+    sweep over the concave satellite, the cylinder and the plate."""
+    cases = [(M.satellite(60_000), W.satellite_case(N=1)["params"]), (M.cylinder(), None), (M.plate(), None)]
+    out = {}
+    for w in (2, 4, 8):
+        c = T.tpmc_create(0)
+        try:
+            T.tpmc_set_launch(c, block=0, bvh_width=w)
+            for ci, ((xyz, tri), params) in enumerate(cases):
+                mesh = T.tpmc_mesh_load(c, xyz, tri)
+                assert T.tpmc_mesh_info(c, mesh)["bvh_width"] == w
+                if params is None:
+                    params = dict(**W.base_state(S=5.0), dir=(0.3, -0.2, -0.9), eps_diffuse=0.5, A_ref=1.0,
+                                  max_bounces=64, seed=3)
+                sw = T.tpmc_sweep(c, mesh, T.make_params(**params, stream_id=40), W.attitude_grid(4, 4),
+                                  np.linspace(3.0, 11.0, 16), 60_000)
+                out[w, ci] = [(r["sum_dv_q"], r["sum_rdv_q"], r["n_hits"], r["CD_sigma"]) for r in sw]
+                T.tpmc_mesh_unload(c, mesh)
+        finally:
+            T.tpmc_destroy(c)
+    for ci in range(len(cases)):
+        assert out[2, ci] == out[4, ci] == out[8, ci], ci
 
 
 # ------------------------------------------ Cercignani-Lampis-Lord surfaces
