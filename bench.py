@@ -243,8 +243,24 @@ def cpu_baseline_and_cd_error(results_by_group, budget_s=12.0):
                 n_total += per_case
         rates[shape] = n_total / t_total
         sample_desc.append(f"{shape}: first {per_case} ids of 4 cases")
+    # the oracle's own median-split BVH on the cylinder (intersect=2), beside its
+    # default there (brute force over all triangles for meshes of <= 5,000)
+    t_bvh, n_bvh = 0.0, 0
+    for g in gs:
+        if g["shape"] != "cylinder":
+            continue
+        om = oracle.Mesh(g["xyz"], g["tri"])
+        for ci in (10, 50):
+            c = g["cases"][ci]
+            p = oracle.make_params(**c["params"], threads=threads, intersect=2)
+            t0 = time.perf_counter()
+            oracle.trace(om, p, c["N"], pid_begin=0, count=4 * 60_000)
+            t_bvh += time.perf_counter() - t0
+            n_bvh += 4 * 60_000
+    rate_cyl_bvh = n_bvh / t_bvh
     # the workload traces equal particle counts on both meshes
     rate = 1.0 / (0.5 / rates["plate"] + 0.5 / rates["cylinder"])
+    rate_bvh = 1.0 / (0.5 / rates["plate"] + 0.5 / rate_cyl_bvh)
     cd = None
     if results_by_group is not None:
         zs, rels = [], []
@@ -264,7 +280,12 @@ def cpu_baseline_and_cd_error(results_by_group, budget_s=12.0):
               "max_rel": max(rels), "median_rel": float(np.median(rels))}
     base = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "; ".join(sample_desc) + f"; plate {rates['plate']:.4g}/s, cylinder {rates['cylinder']:.4g}/s,"
-                      " combined for equal particle counts"}
+                      " combined for equal particle counts",
+            "intersection": {"plate": "brute force over its 2 triangles (the oracle's default below 5,000)",
+                             "cylinder": "brute force over its 4,096 triangles (the oracle's default below 5,000)"},
+            "cylinder_oracle_bvh_particles_per_s": rate_cyl_bvh,
+            "value_with_oracle_bvh_on_cylinder": rate_bvh,
+            "bvh_sample": "cylinder: first 240,000 ids of 4 cases with the oracle's median-split BVH (intersect=2)"}
     return base, cd
 
 

@@ -169,7 +169,7 @@ LaunchCfg Ctx::schedule(const MeshRec& m, uint32_t variant, uint64_t total) {
     cfg.blocks_per_sm = 0;
     cfg.chunk = 0;
   }
-  cfg.smem_nodes = std::min<uint32_t>(cfg.smem_nodes, m.dev.n_nodes);
+  cfg.smem_nodes = m.dev.width > 2 ? 0u : std::min<uint32_t>(cfg.smem_nodes, m.dev.n_nodes);  // wide: none staged
   // A traversal round ends once this many lanes have finished their rays.
   // Same-box sweeps after the spatial-split BVH: 24 is 6 % faster than 16 on
   // the cylinder sweep, equal on the plate and the satellite; 32 is slower.
@@ -308,6 +308,7 @@ tpmc_status Ctx::upload_mesh(const double* xyz, uint32_t n_vert, const uint32_t*
   m.dev.frames64 = (const double*)p_fr64;
   m.dev.n_nodes = (uint32_t)b.n_nodes;
   m.dev.width = b.width;
+  m.dev.depth = b.depth;
   for (int k = 0; k < 3; ++k) {  // the padded root box (empty when there is no mesh)
     m.dev.box_lo[k] = b.root_lo[k];
     m.dev.box_hi[k] = b.root_hi[k];
@@ -580,9 +581,7 @@ tpmc_status tpmc_trace_records(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_para
   return trace_common(c, mesh, params, N, records, out);
 }
 
-tpmc_status tpmc_panels(tpmc_ctx* ctx, tpmc_query_id query, double* pressure, double* shear, uint32_t n_tri) {
-  if (!ctx) return fail(TPMC_EINVAL, "ctx is NULL");
-  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+static tpmc_status panels_locked(Ctx* c, tpmc_query_id query, double* pressure, double* shear, uint32_t n_tri) {
   std::lock_guard<std::recursive_mutex> lk(c->mu);
   auto it = c->panels.find(query);
   if (it == c->panels.end()) return fail(TPMC_ENOTFOUND, "no panel loads kept for this query");
@@ -609,6 +608,15 @@ tpmc_status tpmc_panels(tpmc_ctx* ctx, tpmc_query_id query, double* pressure, do
   c->release(pr.d_panel);
   c->panels.erase(it);
   return TPMC_OK;
+}
+
+tpmc_status tpmc_panels(tpmc_ctx* ctx, tpmc_query_id query, double* pressure, double* shear, uint32_t n_tri) {
+  if (!ctx) return fail(TPMC_EINVAL, "ctx is NULL");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  const tpmc_status st = panels_locked(c, query, pressure, shear, n_tri);
+  // after the context lock is dropped (the scheduler takes its own lock first)
+  if (st == TPMC_OK) serve_memory_released(c);
+  return st;
 }
 
 tpmc_status tpmc_panel_sums(tpmc_ctx* ctx, tpmc_query_id query, int64_t* dv_q, uint32_t n_tri) {

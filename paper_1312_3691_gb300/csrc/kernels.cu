@@ -763,8 +763,9 @@ __device__ __forceinline__ bool trav_leaf(const MeshDev& m, const Ray<R>& r, uin
 // ray: the corner's bits are flipped on the axes where the ray runs towards
 // -a, then read most significant first along the ray's dominant axis, next
 // the second, last the third.  A near child thus comes before a far one
-// along the axis that matters most, with no sort.
-template <typename R>
+// along the axis that matters most, with no sort.  ptab holds each slot's
+// visit position (nibble s), stab the slot at each position (nibble p).
+template <int W, typename R>
 __device__ __forceinline__ void ray_order(Ray<R>& r) {
   const R ax = Fn<R>::fabs(r.d[0]), ay = Fn<R>::fabs(r.d[1]), az = Fn<R>::fabs(r.d[2]);
   const uint32_t flip = (r.d[0] < (R)0 ? 1u : 0u) | (r.d[1] < (R)0 ? 2u : 0u) | (r.d[2] < (R)0 ? 4u : 0u);
@@ -778,11 +779,13 @@ __device__ __forceinline__ void ray_order(Ray<R>& r) {
   }
   uint32_t ptab = 0, stab = 0;
 #pragma unroll
-  for (uint32_t c = 0; c < 8; ++c) {
+  for (uint32_t slot = 0; slot < (uint32_t)W; ++slot) {
+    // the slot's corner (kWide4Corner for 4-wide nodes)
+    const uint32_t c = W == 8 ? slot : (slot == 0 ? 0u : (slot == 1 ? 3u : (slot == 2 ? 5u : 6u)));
     const uint32_t t = c ^ flip;
     const uint32_t pos = (((t >> a0) & 1u) << 2) | (((t >> a1) & 1u) << 1) | ((t >> a2) & 1u);
-    ptab |= pos << (4 * c);
-    stab |= c << (4 * pos);
+    ptab |= pos << (4 * slot);
+    stab |= slot << (4 * pos);
   }
   r.ptab = ptab;
   r.stab = stab;
@@ -793,6 +796,8 @@ __device__ __forceinline__ void ray_order(Ray<R>& r) {
 //           to visit: gx = child_base | (hit positions << 24), gy = (lower
 //           bound on their entry distances, low 8 bits cleared) | imask;
 //   tb, tm: triangles to test: tb + k for every bit k of tm.
+// A stack entry is a node group (gx, gy), or a postponed triangle group
+// (tm, tb | 2^31): a node group's gy is a positive float's bits, bit 31 clear.
 template <typename R>
 struct TravW {
   R tbest;
@@ -801,30 +806,38 @@ struct TravW {
   int sp;
 };
 
+constexpr uint32_t kTriEntry = 0x80000000u;
+
 template <typename R>
 __device__ __forceinline__ void travw_begin(TravW<R>& t, const Ray<R>& r) {
   t.tbest = (R)CUDART_INF;
   t.best = 0xFFFFFFFFu;
-  t.gx = (1u << (r.ptab & 7u)) << 24;  // the root: an inner child in slot 0 (corner 0) of node base 0
+  t.gx = (1u << (r.ptab & 7u)) << 24;  // the root: an inner child in slot 0 of node base 0
   t.gy = 1u;
   t.tb = 0;
   t.tm = 0;
   t.sp = 0;
 }
 
-// Next stacked group whose entry bound is still within the best hit.
+// Next stacked work: a node group whose entry bound is still within the best
+// hit becomes the current group; a postponed triangle group becomes the
+// triangle mask (only taken when the mask is empty).
 template <typename R>
-__device__ __forceinline__ bool travw_pop(TravW<R>& t, const uint2* stack) {
+__device__ __forceinline__ void travw_pop(TravW<R>& t, const uint2* stack) {
   while (t.sp > 0) {
     --t.sp;
     const uint2 e = stack[t.sp];
+    if (e.y & kTriEntry) {
+      t.tm = e.x;
+      t.tb = e.y & ~kTriEntry;
+      return;
+    }
     if ((R)__uint_as_float(e.y & ~0xFFu) <= t.tbest) {
       t.gx = e.x;
       t.gy = e.y;
-      return true;
+      return;
     }
   }
-  return false;
 }
 
 // Byte k of w as a float, exactly: 2^23 + b built in the bits, then 2^23 taken off.
@@ -832,28 +845,36 @@ __device__ __forceinline__ float byte_float(uint32_t w, uint32_t k) {
   return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7440u + k)) - 8388608.0f;
 }
 
-// Near and far slab distances of one child along one axis.
-template <typename R>
-__device__ __forceinline__ R slab_w(uint32_t w, uint32_t k, R sa, R oa) {
-  return fma((R)byte_float(w, k), sa, oa);
+__device__ __forceinline__ float max3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
 }
+__device__ __forceinline__ float min3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ double max3(double a, double b, double c) { return fmax(fmax(a, b), c); }
+__device__ __forceinline__ double min3(double a, double b, double c) { return fmin(fmin(a, b), c); }
 
 // Float bound below t (its low 8 bits are cleared to make room for imask).
 __device__ __forceinline__ uint32_t t_bits_down(float t) { return __float_as_uint(t) & ~0xFFu; }
 __device__ __forceinline__ uint32_t t_bits_down(double t) { return __float_as_uint(__double2float_rd(t)) & ~0xFFu; }
 
 // One node of the group: the next hit child in visit order is fetched and its
-// W child boxes tested; the group's other children are stacked; the hit inner
-// children form the new group and the hit leaves' triangles the triangle mask.
-template <typename R, int W, bool STAGE>
-__device__ __forceinline__ void travw_node(const MeshDev& m, const float4* __restrict__ s_nodes, uint32_t n_stage,
-                                           const Ray<R>& r, TravW<R>& t, uint2* stack, uint32_t& n_nodes, int* err) {
+// W child boxes tested; the group's other children are stacked.  The hit
+// inner children form the new group; the hit leaves' triangles become the
+// triangle mask, or, when the lane still holds one (speculative descent),
+// a postponed group on the stack.
+template <typename R, int W>
+__device__ __forceinline__ void travw_node(const MeshDev& m, const Ray<R>& r, TravW<R>& t, uint2* stack,
+                                           uint32_t& n_nodes, int* err) {
   constexpr int F4 = W == 8 ? 5 : 4;
   const uint32_t hits = t.gx >> 24;
   const uint32_t pos = __ffs(hits) - 1;
   const uint32_t rest = hits & (hits - 1u);
-  const uint32_t corner = (r.stab >> (4 * pos)) & 7u;
-  const uint32_t slot = W == 8 ? corner : corner >> 1;  // 4-wide slots face corners 0, 3, 5, 6
+  const uint32_t slot = (r.stab >> (4 * pos)) & 7u;
   const uint32_t node = (t.gx & 0xFFFFFFu) + __popc(t.gy & 0xFFu & ((1u << slot) - 1u));
   if (rest != 0u) {
     if (t.sp >= kMaxStackW) {
@@ -868,14 +889,9 @@ __device__ __forceinline__ void travw_node(const MeshDev& m, const float4* __res
   }
   ++n_nodes;
   float4 v[F4];
-  if (STAGE && node < n_stage) {
+  const float4* g = m.nodes + (size_t)F4 * node;
 #pragma unroll
-    for (int i = 0; i < F4; ++i) v[i] = s_nodes[F4 * node + i];
-  } else {
-    const float4* g = m.nodes + (size_t)F4 * node;
-#pragma unroll
-    for (int i = 0; i < F4; ++i) v[i] = __ldg(g + i);
-  }
+  for (int i = 0; i < F4; ++i) v[i] = __ldg(g + i);
   const uint32_t ew = __float_as_uint(v[0].w);
   const uint32_t imask = ew >> 24;
   // per axis: grid step times 1/d, and the grid origin's distance
@@ -887,20 +903,13 @@ __device__ __forceinline__ void travw_node(const MeshDev& m, const float4* __res
     oa[a] = fma((R)p[a], r.inv[a], -r.oi[a]);
   }
   // plane words (W = 8: two per plane, slots 0-3 then 4-7; W = 4: one per plane)
-  uint32_t q[12];
-  if constexpr (W == 8) {
-    q[0] = __float_as_uint(v[2].x); q[1] = __float_as_uint(v[2].y);
-    q[2] = __float_as_uint(v[2].z); q[3] = __float_as_uint(v[2].w);
-    q[4] = __float_as_uint(v[3].x); q[5] = __float_as_uint(v[3].y);
-    q[6] = __float_as_uint(v[3].z); q[7] = __float_as_uint(v[3].w);
-    q[8] = __float_as_uint(v[4].x); q[9] = __float_as_uint(v[4].y);
-    q[10] = __float_as_uint(v[4].z); q[11] = __float_as_uint(v[4].w);
-  } else {
-    q[0] = __float_as_uint(v[2].x); q[1] = __float_as_uint(v[2].y);
-    q[2] = __float_as_uint(v[2].z); q[3] = __float_as_uint(v[2].w);
-    q[4] = __float_as_uint(v[3].x); q[5] = __float_as_uint(v[3].y);
+  constexpr int PP = W == 8 ? 2 : 1;
+  uint32_t q[6 * PP];
+#pragma unroll
+  for (int i = 0; i < 6 * PP; ++i) {
+    const float4& f = v[2 + i / 4];
+    q[i] = __float_as_uint((i & 3) == 0 ? f.x : ((i & 3) == 1 ? f.y : ((i & 3) == 2 ? f.z : f.w)));
   }
-  constexpr int PP = W == 8 ? 2 : 1;  // words per plane
   // near and far planes along each axis: lo first where the ray runs towards +a
   uint32_t qn[3][PP], qf[3][PP];
 #pragma unroll
@@ -913,33 +922,50 @@ __device__ __forceinline__ void travw_node(const MeshDev& m, const float4* __res
       qf[a][h] = pos_dir ? hi : lo;
     }
   }
-  const uint32_t meta0 = __float_as_uint(v[1].z), meta1 = __float_as_uint(v[1].w);
-  uint32_t new_hits = 0, tris = 0;
-  R tmin_in = (R)CUDART_INF;
+  uint32_t hitbits = 0;
+  R tmin_hit = (R)CUDART_INF;
 #pragma unroll
   for (int s = 0; s < W; ++s) {
     const int h = s >> 2, k = s & 3;
-    const R tn = fmax(fmax(slab_w<R>(qn[0][h], k, sa[0], oa[0]), slab_w<R>(qn[1][h], k, sa[1], oa[1])),
-                      fmax(slab_w<R>(qn[2][h], k, sa[2], oa[2]), r.tlo));
-    const R tf = fmin(fmin(slab_w<R>(qf[0][h], k, sa[0], oa[0]), slab_w<R>(qf[1][h], k, sa[1], oa[1])),
-                      fmin(slab_w<R>(qf[2][h], k, sa[2], oa[2]), t.tbest));
+    const R tn = max3(max3(fma((R)byte_float(qn[0][h], k), sa[0], oa[0]), fma((R)byte_float(qn[1][h], k), sa[1], oa[1]),
+                           fma((R)byte_float(qn[2][h], k), sa[2], oa[2])), r.tlo, r.tlo);
+    const R tf = min3(fma((R)byte_float(qf[0][h], k), sa[0], oa[0]), fma((R)byte_float(qf[1][h], k), sa[1], oa[1]),
+                      min3(fma((R)byte_float(qf[2][h], k), sa[2], oa[2]), t.tbest, t.tbest));
     const bool hit = tn <= tf;
-    // the slot's corner (kWide4Corner for 4-wide nodes)
-    const uint32_t c = W == 8 ? (uint32_t)s : (s == 0 ? 0u : (s == 1 ? 3u : (s == 2 ? 5u : 6u)));
-    if ((imask >> s) & 1u) {
-      if (hit) {
-        new_hits |= 1u << ((r.ptab >> (4 * c)) & 7u);
-        tmin_in = fmin(tmin_in, tn);
-      }
-    } else if (hit) {
-      const uint32_t meta = ((s < 4 ? meta0 : meta1) >> (8 * k)) & 0xFFu;
-      tris |= (0xFu >> (3u - (meta >> 5))) << (meta & 31u);
-    }
+    hitbits |= hit ? (1u << s) : 0u;
+    tmin_hit = fmin(tmin_hit, hit ? tn : (R)CUDART_INF);
+  }
+  // hit inner children by visit position; hit leaves' triangles
+  uint32_t inner = hitbits & imask, new_hits = 0;
+  while (inner != 0u) {
+    const uint32_t s = __ffs(inner) - 1;
+    inner &= inner - 1u;
+    new_hits |= 1u << ((r.ptab >> (4 * s)) & 7u);
+  }
+  uint32_t leaves = hitbits & ~imask, tris = 0;
+  const uint32_t meta0 = __float_as_uint(v[1].z), meta1 = __float_as_uint(v[1].w);
+  while (leaves != 0u) {
+    const uint32_t s = __ffs(leaves) - 1;
+    leaves &= leaves - 1u;
+    const uint32_t meta = ((s < 4 ? meta0 : meta1) >> (8 * (s & 3u))) & 0xFFu;
+    tris |= (0xFu >> (3u - (meta >> 5))) << (meta & 31u);
   }
   t.gx = __float_as_uint(v[1].x) | (new_hits << 24);
-  t.gy = t_bits_down(tmin_in) | imask;
-  t.tb = __float_as_uint(v[1].y);
-  t.tm = tris;
+  t.gy = t_bits_down(tmin_hit) | imask;
+  if (tris != 0u) {
+    if (t.tm == 0u) {
+      t.tb = __float_as_uint(v[1].y);
+      t.tm = tris;
+    } else if (t.sp < kMaxStackW) {  // speculative step: postpone these triangles
+      stack[t.sp] = make_uint2(tris, __float_as_uint(v[1].y) | kTriEntry);
+      ++t.sp;
+    } else {
+      atomicOr(err, 1);
+      t.gx = 0;
+      t.tm = 0;
+      t.sp = 0;
+    }
+  }
 }
 
 // Triangles of the mask (a node's hit leaves), in any order: nearest t wins.
@@ -1224,7 +1250,7 @@ __device__ __forceinline__ bool ray_meets_box(const Ray<R>& r, const MeshDev& m)
 template <int W, typename R, typename TV>
 __device__ __forceinline__ void begin_trav(Ray<R>& r, TV& tv) {
   if constexpr (W > 2) {
-    ray_order(r);
+    ray_order<W>(r);
     travw_begin(tv, r);
   } else {
     trav_begin(tv);
@@ -1235,10 +1261,12 @@ template <typename R, int MINB, bool CLL, int W>
 __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeof(R) == 4 ? 2 : 1))
     trace_kernel(TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr uint32_t kNodeF4 = W == 8 ? 5 : 4;  // float4 per node
-  const uint32_t n_stage = min(a.smem_nodes, a.mesh.n_nodes);
+  constexpr uint32_t kNodeF4 = 4;  // float4 per binary node
+  // only the binary traversal reads staged nodes
+  const uint32_t n_stage = W > 2 ? 0u : min(a.smem_nodes, a.mesh.n_nodes);
   float4* s_nodes = reinterpret_cast<float4*>(smem);
-  for (uint32_t i = threadIdx.x; i < kNodeF4 * n_stage; i += blockDim.x) s_nodes[i] = __ldg(&a.mesh.nodes[i]);
+  if constexpr (W == 2)
+    for (uint32_t i = threadIdx.x; i < kNodeF4 * n_stage; i += blockDim.x) s_nodes[i] = __ldg(&a.mesh.nodes[i]);
   Seeded<R>* queue = reinterpret_cast<Seeded<R>*>(smem + (size_t)n_stage * kNodeF4 * sizeof(float4)) +
                      (threadIdx.x >> 5) * kQueue;
   LaneAcc& acc = reinterpret_cast<LaneAcc*>(smem + (size_t)n_stage * kNodeF4 * sizeof(float4) +
@@ -1429,20 +1457,20 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
 
     // ---- 4. traversal round
     if constexpr (W > 2) {
-      // Wide tree: lanes without triangles to test step through nodes until
-      // each holds a triangle mask or has nothing left; then the triangles.
+      // Wide tree: lanes without triangles to test (searching) step through
+      // nodes until each holds a triangle mask or has nothing left; lanes
+      // that already hold one keep descending meanwhile (speculative), while
+      // their stack has room for a postponed triangle group.  Then the
+      // triangles.
       for (;;) {
         for (;;) {
-          const bool want = has && !tdone && tv.tm == 0u && ((tv.gx >> 24) != 0u || tv.sp > 0);
-          if (!__any_sync(kFull, want)) break;
-          if (want) {
-            if ((tv.gx >> 24) != 0u || travw_pop(tv, stack)) {
-              if (n_stage == 0)
-                travw_node<R, W, false>(a.mesh, s_nodes, n_stage, ray, tv, stack, n_nodes, a.error);
-              else
-                travw_node<R, W, true>(a.mesh, s_nodes, n_stage, ray, tv, stack, n_nodes, a.error);
-            }
-          }
+          const bool work = has && !tdone;
+          const bool search = work && tv.tm == 0u && ((tv.gx >> 24) != 0u || tv.sp > 0);
+          if (!__any_sync(kFull, search)) break;
+          if (search && (tv.gx >> 24) == 0u) travw_pop(tv, stack);
+          const bool step = work && (tv.gx >> 24) != 0u &&
+                            (tv.tm == 0u || tv.sp + (int)a.mesh.depth + 2 < kMaxStackW);
+          if (step && (search || tv.tm != 0u)) travw_node<R, W>(a.mesh, ray, tv, stack, n_nodes, a.error);
         }
         if (has && !tdone) {
           if (tv.tm != 0u) travw_tris<R>(a.mesh, ray, last, tv, n_tris);
@@ -1766,8 +1794,8 @@ size_t trace_smem_bytes(const LaunchCfg& cfg, uint32_t n_nodes, uint32_t variant
   const uint32_t precision = variant & 1u;
   const size_t queue = (size_t)(cfg.block / 32) * kQueue *
                        (precision == TPMC_FP64 ? sizeof(Seeded<double>) : sizeof(Seeded<float>));
-  return (size_t)std::min(cfg.smem_nodes, n_nodes) * node_float4s(variant_width(variant)) * sizeof(float4) + queue +
-         (size_t)cfg.block * sizeof(LaneAcc);
+  const size_t staged = variant_width(variant) > 2 ? 0 : (size_t)std::min(cfg.smem_nodes, n_nodes) * 4 * sizeof(float4);
+  return staged + queue + (size_t)cfg.block * sizeof(LaneAcc);
 }
 
 namespace {

@@ -98,5 +98,8 @@ struct Ctx {
 };
 
 void stop_serving(Ctx* c);
+// Wakes the serving scheduler after device memory was released outside it
+// (panel loads read by tpmc_panels), so that queries waiting for memory retry.
+void serve_memory_released(Ctx* c);
 
 }  // namespace tpmc

@@ -2,10 +2,14 @@
 //
 // tpmc_submit queues a query; one scheduler thread per context repeatedly
 //   1. admits queued queries into free slots while device memory allows
-//      (panel buffers are charged to the context's budget),
-//   2. builds a step: a particle budget handed first to the queries with
-//      little work left, smallest first (they finish in this step), then to
-//      the large ones in arrival order,
+//      (panel buffers are charged to the context's budget); a query whose
+//      panel buffer does not fit yet waits without holding back the queries
+//      behind it,
+//   2. builds a step: when no step is in flight (the GPU is idle) every
+//      admitted query gets all of its remaining particles, so a query that
+//      arrives at an idle GPU runs whole in one launch; otherwise a particle
+//      budget goes first to the queries with little work left, smallest first
+//      (they finish in this step), then to the large ones in arrival order,
 //   3. enqueues the step -- set-up of newly admitted queries, one persistent
 //      trace launch per (mesh, kernel variant) group over work items from all of
 //      the group's queries, the FP64 reduction of the queries that finish,
@@ -86,6 +90,7 @@ struct ServeState {
   std::mutex m;
   std::condition_variable cv_work, cv_done;
   bool stop = false;
+  bool mem_wait = false;       // queued queries wait for device memory to be released
   std::deque<Request*> queue;
   std::map<tpmc_query_id, Request*> all;
   std::vector<Request*> slots;
@@ -100,32 +105,41 @@ struct ServeState {
 
 namespace {
 
-// Admits queued requests into free slots (caller holds s->m).
+// Admits queued requests into free slots (caller holds s->m), in arrival
+// order.  A request whose panel buffer does not fit now stays queued while
+// memory may still be released (queries in flight, or panel loads not yet
+// read by tpmc_panels), and the requests behind it are admitted meanwhile; it
+// fails with ENOMEM only when nothing can free memory.
 void admit(ServeState* s) {
   Ctx* c = s->ctx;
-  while (!s->queue.empty()) {
-    Request* r = s->queue.front();
+  s->mem_wait = false;
+  for (auto qit = s->queue.begin(); qit != s->queue.end();) {
+    Request* r = *qit;
     int slot = -1;
     for (uint32_t i = 0; i < kSlots; ++i) if (!s->slots[i]) { slot = (int)i; break; }
     if (slot < 0) return;
     if (r->want_panels && r->n_tri > 0) {
       std::lock_guard<std::recursive_mutex> ck(c->mu);
       if (c->alloc(&r->d_panel, (size_t)r->n_tri * 3 * sizeof(long long), "serving panel loads") != TPMC_OK) {
-        bool any = false;
-        for (Request* a : s->slots) any = any || a;
-        if (any || !s->inflight.empty()) return;  // wait for memory to free up
+        bool may_free = !s->inflight.empty() || !c->panels.empty();
+        for (Request* a : s->slots) may_free = may_free || a;
+        if (may_free) {  // wait for memory; later queries may still fit
+          s->mem_wait = true;
+          ++qit;
+          continue;
+        }
         r->done = true;  // cannot ever fit
         std::memset(&r->result, 0, sizeof(r->result));
         r->result.status = TPMC_ENOMEM;
         r->result.query_id = r->id;
         auto mit = c->meshes.find(r->mesh);
         if (mit != c->meshes.end()) --mit->second.in_use;
-        s->queue.pop_front();
+        qit = s->queue.erase(qit);
         s->cv_done.notify_all();
         continue;
       }
     }
-    s->queue.pop_front();
+    qit = s->queue.erase(qit);
     r->slot = slot;
     s->slots[slot] = r;
   }
@@ -133,7 +147,7 @@ void admit(ServeState* s) {
 
 // Builds and enqueues one step in buffer b (caller does not hold s->m).
 // Returns false when there was nothing to run.
-bool enqueue_step(ServeState* s, int b, int prev, const std::vector<Request*>& cand, cudaError_t& e) {
+bool enqueue_step(ServeState* s, int b, int prev, bool gpu_idle, const std::vector<Request*>& cand, cudaError_t& e) {
   Ctx* c = s->ctx;
   StepBuf& B = s->buf[b];
   B.members.clear();
@@ -150,7 +164,13 @@ bool enqueue_step(ServeState* s, int b, int prev, const std::vector<Request*>& c
     return x->id < y->id;
   });
   std::map<Request*, uint64_t> take;
+  // An idle GPU takes everything admitted in one step: nothing would be
+  // overtaken, and each query then costs one launch.
   uint64_t budget = kStepParticles;
+  if (gpu_idle) {
+    budget = 0;
+    for (Request* r : order) budget += r->N - r->next_pid;
+  }
   for (Request* r : order) {
     if (budget == 0) break;
     const uint64_t t = std::min<uint64_t>(r->N - r->next_pid, budget);
@@ -317,6 +337,7 @@ void retire_step(ServeState* s, cudaError_t e_enqueue) {
       r->d_panel = nullptr;
     }
   }
+  s->mem_wait = false;  // slots and maybe memory were freed: admission may proceed
   s->cv_done.notify_all();
 }
 
@@ -333,7 +354,7 @@ void loop(ServeState* s) {
         return false;
       };
       s->cv_work.wait(lk, [&] {
-        return s->stop || !s->inflight.empty() || !s->queue.empty() || has_work();
+        return s->stop || !s->inflight.empty() || (!s->queue.empty() && !s->mem_wait) || has_work();
       });
       if (s->stop) break;
       admit(s);
@@ -349,7 +370,7 @@ void loop(ServeState* s) {
     if (free_buf >= 0) {
       // inflight is changed only by this thread, so it can be read here unlocked
       const int prev = s->inflight.empty() ? -1 : s->inflight.back();
-      const bool pushed = enqueue_step(s, free_buf, prev, cand, e);
+      const bool pushed = enqueue_step(s, free_buf, prev, s->inflight.empty(), cand, e);
       if (pushed) {
         std::lock_guard<std::mutex> lk(s->m);
         s->inflight.push_back(free_buf);
@@ -445,6 +466,16 @@ tpmc_status start_serving(Ctx* c) {
 
 }  // namespace
 
+void serve_memory_released(Ctx* c) {
+  ServeState* s = c->serve;
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->m);
+    s->mem_wait = false;
+  }
+  s->cv_work.notify_all();
+}
+
 void stop_serving(Ctx* c) {
   ServeState* s = c->serve;
   if (!s) return;
@@ -498,6 +529,7 @@ tpmc_status tpmc_submit(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* par
   ServeState* s = c->serve;
   {
     std::lock_guard<std::mutex> lk(s->m);
+    s->mem_wait = false;  // the new query may fit
     if (s->queue.size() >= kMaxQueue) {
       std::lock_guard<std::recursive_mutex> ck(c->mu);
       --c->meshes.at(mesh).in_use;

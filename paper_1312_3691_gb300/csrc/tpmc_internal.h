@@ -75,6 +75,7 @@ struct MeshDev {
   uint32_t n_tri = 0;               // input numbering (panel arrays use it)
   uint32_t n_tri_leaf = 0;          // triangles referenced by leaves (zero-area ones dropped)
   uint32_t width = 2;               // 2: binary nodes; 4 or 8: compressed wide nodes
+  uint32_t depth = 0;               // levels below the root (bounds the wide traversal's stack)
   float scene_radius = 1.0f;
   float box_lo[3] = {0.0f, 0.0f, 0.0f}, box_hi[3] = {-1.0f, -1.0f, -1.0f};  // padded root box (empty: no mesh)
 };

@@ -163,6 +163,7 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
   for (uint32_t block : {64u, 128u, 256u})
     for (uint32_t sm_nodes : {0u, 64u, 256u, 1024u}) {
       if (sm_nodes > 0 && sm_nodes >= 2 * nn && sm_nodes != 64u) continue;  // a larger stage of a small tree adds nothing
+      if (sm_nodes > 0 && m.dev.width > 2) continue;  // only the binary traversal stages nodes
       for (uint32_t occ : {0u, 6u, 4u})  // 0: the highest occupancy
         for (uint32_t refill : {8u, 16u, 24u}) {
           LaunchCfg cfg;

@@ -629,6 +629,58 @@ def test_serving_results_equal_alone_and_in_the_mix(T, ctx):
             T.tpmc_mesh_unload(ctx, i)
 
 
+def test_serving_admission_waits_for_memory(T):
+    """A memory budget with room for one panel buffer but not two: the second
+    query that wants panels waits (polling it times out) while a later query
+    without panels is admitted past it and finishes; once the first query's
+    panels are read (and released) the second runs and gives the same bits as
+    alone."""
+    xyz, tri = M.satellite(60_000)
+    panel_bytes = len(tri) * 3 * 8
+    st = W.base_state(S=6.0)
+    small = T.make_params(**st, dir=(-1.0, 0.2, 0.1), eps_diffuse=0.9, A_ref=2.0, seed=1, max_bounces=64)
+    # the memory a context holds once its mesh is loaded and serving has started
+    probe = T.tpmc_create(0)
+    try:
+        m = T.tpmc_mesh_load(probe, xyz, tri)
+        T.tpmc_poll(probe, T.tpmc_submit(probe, m, small, 1000), -1)
+        base_used = T.tpmc_memory_info(probe)["used"]
+    finally:
+        T.tpmc_destroy(probe)
+    # room for one panel buffer (24 B per triangle) and tpmc_panels' output (16 B
+    # per triangle) beside it, not for a second panel buffer
+    c = T.tpmc_create(0, base_used + panel_bytes * 7 // 4)
+    try:
+        m = T.tpmc_mesh_load(c, xyz, tri)
+        T.tpmc_poll(c, T.tpmc_submit(c, m, small, 1000), -1)
+        p1 = T.make_params(**st, dir=(-1.0, 0.0, 0.0), eps_diffuse=0.9, A_ref=2.0, seed=11, max_bounces=64,
+                           want_panels=True)
+        p2 = T.make_params(**st, dir=(-0.6, 0.5, 0.3), eps_diffuse=0.9, A_ref=2.0, seed=12, max_bounces=64,
+                           want_panels=True)
+        q1 = T.tpmc_submit(c, m, p1, 200_000)
+        q2 = T.tpmc_submit(c, m, p2, 200_000)
+        q3 = T.tpmc_submit(c, m, small, 100_000)
+        r1 = T.tpmc_poll(c, q1, -1)
+        r3 = T.tpmc_poll(c, q3, -1)
+        assert r1["status"] == 0 and r3["status"] == 0
+        assert T.tpmc_poll(c, q2, 300) is None  # still waiting for memory
+        T.tpmc_panels(c, r1["query_id"], len(tri))  # releases the first panel buffer
+        r2 = T.tpmc_poll(c, q2, -1)
+        dq2 = T.tpmc_panel_sums(c, r2["query_id"], len(tri))
+    finally:
+        T.tpmc_destroy(c)
+    alone_ctx = T.tpmc_create(0)
+    try:
+        m = T.tpmc_mesh_load(alone_ctx, xyz, tri)
+        alone = T.tpmc_trace(alone_ctx, m, p2, 200_000)
+        dq_alone = T.tpmc_panel_sums(alone_ctx, alone["query_id"], len(tri))
+    finally:
+        T.tpmc_destroy(alone_ctx)
+    assert r2["sum_dv_q"] == alone["sum_dv_q"] and r2["sum_rdv_q"] == alone["sum_rdv_q"]
+    assert r2["CD"] == alone["CD"] and r2["CD_sigma"] == alone["CD_sigma"]
+    assert (dq2 == dq_alone).all()
+
+
 # ---------------------------------------------------------------- edge cases
 def test_particle_ids_beyond_2_to_32(T, orc, ctx):
     """N = 2^32 + 2^22 on the plate: 64-bit particle ids in the Philox counter and
