@@ -644,15 +644,15 @@ def measure_attitude_sweep(T, ctx, torch, stream, dev, ceil):
             "median_CD_sigma_rel": float(np.median([r["CD_sigma"] / r["CD"] for r in res]))}
 
 
-def measure_serving(T, ctx, n_queries=200, rate=100.0):
-    """Poisson stream over four resident meshes (icosphere 1,280, cylinder 4,096,
-    satellites 60k and 500k): continuous batching (submit/poll) against a server
-    that runs one query per launch in arrival order, on the same arrival times."""
+def measure_serving(T, ctx, rates=(100.0, 200.0, 400.0, 800.0), n_queries=1000):
+    """Poisson streams of n_queries over four resident meshes (icosphere 1,280,
+    cylinder 4,096, satellites 60k and 500k) at each arrival rate: continuous
+    batching (submit/poll) against a server that runs one query per launch in
+    arrival order, on the same arrival times and queries."""
     import threading as th
 
     ms = [M.icosphere(3), M.cylinder(), M.satellite(60_000), M.satellite(500_000)]
     ids = [T.tpmc_mesh_load(ctx, x, t) for x, t in ms]
-    stream = W.serving_stream(n_queries, rate, seed=3)
     st = W.base_state()
     c_mp = (2 * W.K_B * st["T_inf"] / st["m"]) ** 0.5
 
@@ -660,47 +660,52 @@ def measure_serving(T, ctx, n_queries=200, rate=100.0):
         return T.make_params(n=st["n"], T_inf=st["T_inf"], m=st["m"], V=q["S"] * c_mp, dir=q["dir"], T_W=st["T_W"],
                              eps_diffuse=0.9, A_ref=1.0, seed=q["seed"], max_bounces=64)
 
+    out = {}
     try:
-        for i in ids:  # warm-up per mesh
-            T.tpmc_trace(ctx, i, params(stream[0]), 100_000)
-        # continuous batching
-        handles = [None] * len(stream)
-        t_start = time.perf_counter() + 0.05
+        warm = W.serving_stream(1, 100.0, seed=3)[0]
+        for i in ids:  # warm-up per mesh, through both paths
+            T.tpmc_trace(ctx, i, params(warm), 100_000)
+            T.tpmc_poll(ctx, T.tpmc_submit(ctx, i, params(warm), 100_000), -1)
+        for rate in rates:
+            stream = W.serving_stream(n_queries, rate, seed=3)
+            # continuous batching
+            handles = [None] * len(stream)
+            t_start = time.perf_counter() + 0.05
 
-        def submitter():
-            for k, q in enumerate(stream):
+            def submitter():
+                for k, q in enumerate(stream):
+                    d = t_start + q["t_arrival"] - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    handles[k] = T.tpmc_submit(ctx, ids[q["mesh"]], params(q), q["N"])
+
+            thr = th.Thread(target=submitter)
+            thr.start()
+            thr.join()
+            lat = [T.tpmc_poll(ctx, h, -1)["ms"] for h in handles]
+            cb_span = time.perf_counter() - t_start
+            # one query per launch, first come first served
+            t_start = time.perf_counter() + 0.05
+            lat_plain = []
+            for q in stream:
                 d = t_start + q["t_arrival"] - time.perf_counter()
                 if d > 0:
                     time.sleep(d)
-                handles[k] = T.tpmc_submit(ctx, ids[q["mesh"]], params(q), q["N"])
-
-        thr = th.Thread(target=submitter)
-        thr.start()
-        thr.join()
-        lat = []
-        for h in handles:
-            lat.append(T.tpmc_poll(ctx, h, -1)["ms"])
-        cb_span = time.perf_counter() - t_start
-        # one query per launch, first come first served
-        t_start = time.perf_counter() + 0.05
-        lat_plain = []
-        for q in stream:
-            d = t_start + q["t_arrival"] - time.perf_counter()
-            if d > 0:
-                time.sleep(d)
-            T.tpmc_trace(ctx, ids[q["mesh"]], params(q), q["N"])
-            lat_plain.append(1e3 * (time.perf_counter() - (t_start + q["t_arrival"])))
-        plain_span = time.perf_counter() - t_start
+                T.tpmc_trace(ctx, ids[q["mesh"]], params(q), q["N"])
+                lat_plain.append(1e3 * (time.perf_counter() - (t_start + q["t_arrival"])))
+            plain_span = time.perf_counter() - t_start
+            n = sum(q["N"] for q in stream)
+            out[f"{rate:g}"] = {
+                "workload": f"{n_queries} Poisson queries at {rate:g}/s, N log-uniform [1e5,1e8], S~U[3,12], "
+                            "4 resident meshes (1,280 / 4,096 / 60,656 / 503,537 tri)",
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "throughput_particles_per_s": n / cb_span,
+                "plain": {"p50_ms": float(np.percentile(lat_plain, 50)), "p99_ms": float(np.percentile(lat_plain, 99)),
+                          "throughput_particles_per_s": n / plain_span}}
     finally:
         for i in ids:
             T.tpmc_mesh_unload(ctx, i)
-    n = sum(q["N"] for q in stream)
-    return {"workload": f"{n_queries} Poisson queries at {rate:g}/s, N log-uniform [1e5,1e8], S~U[3,12], "
-                        "4 resident meshes (1,280 / 4,096 / 60,656 / 503,537 tri)",
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "throughput_particles_per_s": n / cb_span,
-            "plain": {"p50_ms": float(np.percentile(lat_plain, 50)), "p99_ms": float(np.percentile(lat_plain, 99)),
-                      "throughput_particles_per_s": n / plain_span}}
+    return out
 
 
 # ---------------------------------------------------------------- GPU side
@@ -850,9 +855,8 @@ def run_ours(args):
         extras["box_cv"] = measure_box_cv(T, ctx)
         extras["moment_sweep"] = measure_moment_sweep(T, ctx, torch, stream, dev)
         extras["attitude_sweep"] = measure_attitude_sweep(T, ctx, torch, stream, dev, ceil)
-        extras["serving"] = measure_serving(T, ctx, rate=100.0)
-        extras["serving_high_load"] = measure_serving(T, ctx, rate=200.0)
-        extras["serving_saturated"] = measure_serving(T, ctx, rate=400.0)
+        extras["serving_by_rate"] = measure_serving(T, ctx)
+        extras["serving"] = extras["serving_by_rate"]["100"]
     if rank == 0:
         cpu_base, cd_err, cd_other, parity = (None, None, None, None)
         if not args.no_cpu_baseline:

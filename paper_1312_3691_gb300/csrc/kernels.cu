@@ -1128,6 +1128,57 @@ __device__ __forceinline__ void lane_flush(AccDev* acc, LaneAcc& a) {
   }
 }
 
+// Flush at the end of the kernel, where every lane of the warp arrives
+// together (the main loop ends on a warp-uniform test).  When all lanes hold
+// sums of the same query, the warp adds them by a butterfly of shuffles (the
+// 128-bit sum of squares with its carry) and one lane issues the atomics;
+// lanes of mixed queries flush one by one.  Integer sums, so the result is
+// the same either way.
+__device__ __forceinline__ void warp_flush(AccDev* acc, LaneAcc& a) {
+  const unsigned same = __match_any_sync(kFull, a.q);
+  if (same != kFull || a.q < 0) {
+    lane_flush(acc, a);
+    return;
+  }
+  long long F[3], T[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { F[i] = a.F[i]; T[i] = a.T[i]; }
+  unsigned long long lo = a.d2lo, hi = a.d2hi;
+  unsigned long long hits = a.hits, hitp = a.hit_particles, trunc = a.truncated, parts = a.particles;
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      F[i] += __shfl_xor_sync(kFull, F[i], m);
+      T[i] += __shfl_xor_sync(kFull, T[i], m);
+    }
+    const unsigned long long olo = __shfl_xor_sync(kFull, lo, m), ohi = __shfl_xor_sync(kFull, hi, m);
+    const unsigned long long nlo = lo + olo;
+    hi += ohi + (nlo < lo ? 1ull : 0ull);
+    lo = nlo;
+    hits += __shfl_xor_sync(kFull, hits, m);
+    hitp += __shfl_xor_sync(kFull, hitp, m);
+    trunc += __shfl_xor_sync(kFull, trunc, m);
+    parts += __shfl_xor_sync(kFull, parts, m);
+  }
+  if ((threadIdx.x & 31u) != 0u || parts == 0) return;
+  AccDev& A = acc[a.q];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (F[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&A.F[i]), (unsigned long long)F[i]);
+    if (T[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&A.T[i]), (unsigned long long)T[i]);
+  }
+  if (hits) atomicAdd(&A.hits, hits);
+  if (hitp) atomicAdd(&A.hit_particles, hitp);
+  if (trunc) atomicAdd(&A.truncated, trunc);
+  atomicAdd(&A.particles, parts);
+  if (lo != 0 || hi != 0) {
+    const unsigned long long old = atomicAdd(&A.d2lo, lo);
+    const unsigned long long carry = old + lo < old ? 1ull : 0ull;
+    if (hi != 0 || carry != 0) atomicAdd(&A.d2hi, hi + carry);
+  }
+}
+
 __device__ __forceinline__ void work_flush(AccDev* acc, int q, uint32_t n_nodes, uint32_t n_tris) {
   if (q < 0) return;
   if (n_nodes) atomicAdd(&acc[q].nodes, (unsigned long long)n_nodes);
@@ -1507,7 +1558,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
     }
   }
   if (a.count_work) work_flush(a.acc, acc.q, n_nodes, n_tris);
-  lane_flush(a.acc, acc);
+  warp_flush(a.acc, acc);
 }
 
 // ---------------------------------------------------------- set-up kernel
