@@ -311,12 +311,23 @@ tpmc_status tpmc_poll(tpmc_ctx* ctx, tpmc_query_id query, int timeout_ms, tpmc_r
 
 /* ---- schedule ------------------------------------------------------------ */
 
-/* Measures candidate schedules on `mesh` and keeps the fastest for meshes of
- * its size class and this precision.  Each candidate traces N_trial / 4 and
- * then N_trial particles of one query built from `params`; it is scored by the
- * marginal rate between the two, so that fixed per-launch costs do not decide
- * (N_trial of a few million or more keeps the difference above the noise).
- * The kept schedule leaves the chunk automatic. */
+/* Chooses the trace kernel's BVH layout and launch schedule for `mesh` (the
+ * paper's closest-hit ray tracing, §II.A, on this GPU), in three stages:
+ *   1. BVH width 2, 4 or 8 (the mesh is laid out again from the context's
+ *      copy; the fastest layout replaces the mesh's own unless queries in
+ *      flight use it, and later loads of meshes of its size class use it);
+ *   2. threads per block, resident blocks per SM, the traversal-round refill
+ *      threshold and the BVH nodes staged in shared memory (binary trees);
+ *   3. particles per lane: a fixed number of ids a warp takes per fetch.
+ * Each candidate runs a trial sweep of `params` over eight flow directions
+ * (params->dir, the six axes and a diagonal) of N_trial / 4 and then N_trial
+ * particles in all, scored by the marginal rate between the two so that
+ * fixed per-launch costs do not decide (N_trial of a few million or more keeps
+ * the difference above the noise); a candidate must beat the untuned schedule
+ * by 1 %.  The schedule is kept for meshes of the size class and this kernel
+ * variant.  `best` (may be NULL) receives it.
+ * Errors: as tpmc_trace; EINVAL for N_trial = 0 or > 2^30; ENOMEM when a
+ * layout does not fit the memory budget (that width is then skipped). */
 tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* params, uint64_t N_trial,
                       tpmc_launch* best);
 tpmc_status tpmc_set_launch(tpmc_ctx* ctx, const tpmc_launch* cfg);

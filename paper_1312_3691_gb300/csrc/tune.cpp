@@ -1,6 +1,7 @@
 // Autotuner of the trace kernel: BVH layout and launch schedule.
 //
-// Three stages, each timed with CUDA events on runs of the caller's query:
+// Three stages, each timed with CUDA events on a trial sweep of the caller's
+// query over eight flow directions (its own, the six axes and a diagonal):
 //   1. BVH width: the mesh is laid out with 2, 4 and 8 children per node (from
 //      the context's host copy of it) and each layout runs the untuned
 //      schedule; the fastest layout replaces the mesh's own (unless queries
@@ -35,31 +36,39 @@ struct Timer {
   }
 };
 
-// Marginal rate (particles per ms) of schedule `cfg` on mesh `m`: the query
-// traces N_trial / 4 and then N_trial particles, and the rate is the
-// difference in particles over the difference in time, so that the fixed
-// costs of a launch (set-up, reduction, the tail of its last warps) drop out
-// and the choice holds for the long launches of sweeps.  `used` receives the
-// schedule as completed by Ctx::schedule.
-tpmc_status measure(Ctx* c, const MeshRec& m, const tpmc_params* params, uint64_t N_trial, const LaunchCfg& cfg,
-                    bool manual, Timer& tm, double* rate, LaunchCfg* used) {
-  QueryDev q;
-  tpmc_status st = fill_query(m, params, N_trial, &q);
-  if (st != TPMC_OK) return st;
-  ItemDev item;
-  std::memset(&item, 0, sizeof(item));
+// Flow directions of the trial sweep: the caller's and seven fixed ones (the
+// axes and a diagonal), so that a schedule is judged on attitudes around the
+// whole body, as sweeps and served queries see it.
+constexpr int kTrialDirs = 8;
+void trial_dirs(const tpmc_params* p, double out[kTrialDirs * 3]) {
+  const double fixed[7][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+                              {0.57735026918962576, 0.57735026918962576, 0.57735026918962576}};
+  for (int i = 0; i < 3; ++i) out[i] = p->dir[i];
+  for (int k = 0; k < 7; ++k)
+    for (int i = 0; i < 3; ++i) out[3 * (k + 1) + i] = fixed[k][i];
+}
+
+// Marginal rate (particles per ms) of schedule `cfg` on mesh `m`: a sweep of
+// the kTrialDirs directions traces N_trial / 4 and then N_trial particles in
+// all, and the rate is the difference in particles over the difference in
+// time, so that the fixed costs of a launch (set-up, reduction, the tail of
+// its last warps) drop out and the choice holds for the long launches of
+// sweeps.  `used` receives the schedule as completed by Ctx::schedule.
+tpmc_status measure(Ctx* c, const MeshRec& m, const tpmc_params* params, uint64_t N_trial, const double* d_dirs,
+                    const LaunchCfg& cfg, bool manual, Timer& tm, double* rate, LaunchCfg* used) {
   const bool had_manual = c->manual_launch;
   const LaunchCfg old_manual = c->manual;
   c->manual_launch = manual;
   c->manual = cfg;
-  const uint64_t quarter = std::max<uint64_t>(1, N_trial / 4);
+  const uint64_t each[2] = {std::max<uint64_t>(1, N_trial / (4 * kTrialDirs)), std::max<uint64_t>(1, N_trial / kTrialDirs)};
   float ms[2] = {0.0f, 0.0f};
+  tpmc_status st = TPMC_OK;
   for (int k = 0; k < 2 && st == TPMC_OK; ++k) {
-    item.count = k == 0 ? quarter : N_trial;
-    q.N = item.count;
+    QueryDev q;
+    if ((st = fill_query(m, params, each[k], &q)) != TPMC_OK) break;
     cudaEventRecord(tm.e0, c->stream);
-    st = c->run(m, &q, 1, nullptr, nullptr, nullptr, &item, 1, item.count, trace_variant(params, m.dev),
-                (tpmc_result*)c->s_out.ptr, nullptr);
+    st = c->run(m, nullptr, kTrialDirs, &q, d_dirs, nullptr, nullptr, 0, (uint64_t)kTrialDirs * each[k],
+                trace_variant(params, m.dev), (tpmc_result*)c->s_out.ptr, nullptr);
     cudaEventRecord(tm.e1, c->stream);
     if (st != TPMC_OK) break;
     const cudaError_t e = cudaEventSynchronize(tm.e1);
@@ -72,17 +81,17 @@ tpmc_status measure(Ctx* c, const MeshRec& m, const tpmc_params* params, uint64_
   if (st != TPMC_OK) return st;
   if ((st = c->check_error_word()) != TPMC_OK) return st;
   const double dt = (double)ms[1] - (double)ms[0];
-  *rate = (N_trial > quarter && dt > 0.0) ? (double)(N_trial - quarter) / dt
-                                          : (double)N_trial / std::max((double)ms[1], 1e-6);
+  const double dn = (double)kTrialDirs * (double)(each[1] - each[0]);
+  *rate = (dn > 0.0 && dt > 0.0) ? dn / dt : (double)kTrialDirs * (double)each[1] / std::max((double)ms[1], 1e-6);
   return TPMC_OK;
 }
 
 // Best of two passes (the first also warms caches and clocks).
-tpmc_status measure2(Ctx* c, const MeshRec& m, const tpmc_params* params, uint64_t N_trial, const LaunchCfg& cfg,
-                     bool manual, Timer& tm, double* rate, LaunchCfg* used) {
+tpmc_status measure2(Ctx* c, const MeshRec& m, const tpmc_params* params, uint64_t N_trial, const double* d_dirs,
+                     const LaunchCfg& cfg, bool manual, Timer& tm, double* rate, LaunchCfg* used) {
   double r0 = 0.0, r1 = 0.0;
-  tpmc_status st = measure(c, m, params, N_trial, cfg, manual, tm, &r0, used);
-  if (st == TPMC_OK) st = measure(c, m, params, N_trial, cfg, manual, tm, &r1, used);
+  tpmc_status st = measure(c, m, params, N_trial, d_dirs, cfg, manual, tm, &r0, used);
+  if (st == TPMC_OK) st = measure(c, m, params, N_trial, d_dirs, cfg, manual, tm, &r1, used);
   *rate = std::max(r0, r1);
   return st;
 }
@@ -105,7 +114,16 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
     QueryDev q;
     if ((st = fill_query(m, params, N_trial, &q)) != TPMC_OK) return st;
   }
-  if ((st = c->grow(c->s_out, sizeof(tpmc_result), "result")) != TPMC_OK) return st;
+  if ((st = c->grow(c->s_out, kTrialDirs * sizeof(tpmc_result), "results")) != TPMC_OK) return st;
+  if ((st = c->grow(c->s_in, kTrialDirs * 3 * sizeof(double), "trial directions")) != TPMC_OK) return st;
+  {
+    double dirs[kTrialDirs * 3];
+    trial_dirs(params, dirs);
+    const cudaError_t e = cudaMemcpyAsync(c->s_in.ptr, dirs, sizeof(dirs), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tune directions");
+  }
+  const double* d_dirs = (const double*)c->s_in.ptr;
   Timer tm;
   const uint32_t n_tri = m.dev.n_tri;
 
@@ -129,7 +147,7 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
         run_on = &cand;
       }
       double rate = 0.0;
-      st = measure2(c, *run_on, params, N_trial, LaunchCfg(), false, tm, &rate, nullptr);
+      st = measure2(c, *run_on, params, N_trial, d_dirs, LaunchCfg(), false, tm, &rate, nullptr);
       if (st != TPMC_OK) {
         if (run_on == &cand) c->release(cand.d_block);
         return st;
@@ -177,12 +195,24 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
           cands.push_back(cfg);
         }
     }
+  // the untuned schedule is the one to beat, by more than the noise
   double best_rate = -1.0;
   LaunchCfg best_cfg;
+  {
+    const auto had = c->tuned.find(tune_key(n_tri, variant));
+    LaunchCfg kept;
+    const bool had_tuned = had != c->tuned.end();
+    if (had_tuned) { kept = had->second; c->tuned.erase(had); }
+    st = measure2(c, m, params, N_trial, d_dirs, LaunchCfg(), false, tm, &best_rate, &best_cfg);
+    if (had_tuned) c->tuned[tune_key(n_tri, variant)] = kept;
+    if (st != TPMC_OK) return st;
+    best_cfg.chunk = 0;
+    best_rate *= 1.01;
+  }
   for (const LaunchCfg& cfg : cands) {
     double rate = 0.0;
     LaunchCfg used;
-    if ((st = measure2(c, m, params, N_trial, cfg, true, tm, &rate, &used)) != TPMC_OK) return st;
+    if ((st = measure2(c, m, params, N_trial, d_dirs, cfg, true, tm, &rate, &used)) != TPMC_OK) return st;
     if (rate > best_rate) {
       best_rate = rate;
       best_cfg = used;
@@ -196,8 +226,8 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
     cfg.chunk = 32u * per_lane;
     double rate = 0.0;
     LaunchCfg used;
-    if ((st = measure2(c, m, params, N_trial, cfg, true, tm, &rate, &used)) != TPMC_OK) return st;
-    if (rate > best_rate * 1.005) {  // a fixed chunk must beat the automatic one by more than the noise
+    if ((st = measure2(c, m, params, N_trial, d_dirs, cfg, true, tm, &rate, &used)) != TPMC_OK) return st;
+    if (rate > best_rate * 1.01) {  // a fixed chunk must beat the automatic one by more than the noise
       best_rate = rate;
       best_cfg = used;
     }

@@ -37,10 +37,17 @@ def test_tune_picks_a_valid_schedule_that_keeps_results(T, ctx):
         before = T.tpmc_trace(ctx, mesh, p, 500_000)
         best = T.tpmc_tune(ctx, mesh, p, 200_000)
         assert best["block"] in (64, 128, 256) and best["blocks_per_sm"] >= 1
+        assert best["bvh_width"] in (2, 4, 8)
+        # the mesh now has the chosen layout, and later loads of its size class get it too
+        assert T.tpmc_mesh_info(ctx, mesh)["bvh_width"] == best["bvh_width"]
         got = T.tpmc_get_launch(ctx, mesh, T.TPMC_FP32)
         assert got["block"] == best["block"] and got["smem_nodes"] == best["smem_nodes"]
+        assert got["bvh_width"] == best["bvh_width"]
         after = T.tpmc_trace(ctx, mesh, p, 500_000)
         assert after["sum_dv_q"] == before["sum_dv_q"] and after["n_hits"] == before["n_hits"]
+        mesh2 = T.tpmc_mesh_load(ctx, xyz, tri)
+        assert T.tpmc_mesh_info(ctx, mesh2)["bvh_width"] == best["bvh_width"]
+        T.tpmc_mesh_unload(ctx, mesh2)
     finally:
         T.tpmc_mesh_unload(ctx, mesh)
 
