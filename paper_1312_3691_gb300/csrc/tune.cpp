@@ -195,26 +195,41 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
           cands.push_back(cfg);
         }
     }
-  // the untuned schedule is the one to beat, by more than the noise
   double best_rate = -1.0;
   LaunchCfg best_cfg;
-  {
-    const auto had = c->tuned.find(tune_key(n_tri, variant));
-    LaunchCfg kept;
-    const bool had_tuned = had != c->tuned.end();
-    if (had_tuned) { kept = had->second; c->tuned.erase(had); }
-    st = measure2(c, m, params, N_trial, d_dirs, LaunchCfg(), false, tm, &best_rate, &best_cfg);
-    if (had_tuned) c->tuned[tune_key(n_tri, variant)] = kept;
-    if (st != TPMC_OK) return st;
-    best_cfg.chunk = 0;
-    best_rate *= 1.01;
-  }
+  std::vector<std::pair<double, LaunchCfg>> scored;
   for (const LaunchCfg& cfg : cands) {
     double rate = 0.0;
     LaunchCfg used;
     if ((st = measure2(c, m, params, N_trial, d_dirs, cfg, true, tm, &rate, &used)) != TPMC_OK) return st;
-    if (rate > best_rate) {
-      best_rate = rate;
+    used.chunk = 0;
+    scored.push_back({rate, used});
+  }
+  // the three best and the untuned schedule again on a four times longer
+  // trial, so that a short trial's noise does not decide; the untuned
+  // schedule is the one to beat, by 1 %
+  std::sort(scored.begin(), scored.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+  const uint64_t N_long = std::min<uint64_t>(4 * N_trial, 1ull << 30);
+  {
+    double r = 0.0;
+    LaunchCfg used;
+    const auto had = c->tuned.find(tune_key(n_tri, variant));
+    LaunchCfg kept;
+    const bool had_tuned = had != c->tuned.end();
+    if (had_tuned) { kept = had->second; c->tuned.erase(had); }
+    st = measure2(c, m, params, N_long, d_dirs, LaunchCfg(), false, tm, &r, &used);
+    if (had_tuned) c->tuned[tune_key(n_tri, variant)] = kept;
+    if (st != TPMC_OK) return st;
+    best_rate = 1.01 * r;
+    best_cfg = used;
+    best_cfg.chunk = 0;
+  }
+  for (size_t i = 0; i < scored.size() && i < 3; ++i) {
+    double r = 0.0;
+    LaunchCfg used;
+    if ((st = measure2(c, m, params, N_long, d_dirs, scored[i].second, true, tm, &r, &used)) != TPMC_OK) return st;
+    if (r > best_rate) {
+      best_rate = r;
       best_cfg = used;
       best_cfg.chunk = 0;
     }
@@ -226,7 +241,7 @@ extern "C" tpmc_status tpmc_tune(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_pa
     cfg.chunk = 32u * per_lane;
     double rate = 0.0;
     LaunchCfg used;
-    if ((st = measure2(c, m, params, N_trial, d_dirs, cfg, true, tm, &rate, &used)) != TPMC_OK) return st;
+    if ((st = measure2(c, m, params, N_long, d_dirs, cfg, true, tm, &rate, &used)) != TPMC_OK) return st;
     if (rate > best_rate * 1.01) {  // a fixed chunk must beat the automatic one by more than the noise
       best_rate = rate;
       best_cfg = used;
