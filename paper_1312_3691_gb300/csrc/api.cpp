@@ -309,9 +309,13 @@ tpmc_status Ctx::upload_mesh(const double* xyz, uint32_t n_vert, const uint32_t*
   m.dev.n_nodes = (uint32_t)b.n_nodes;
   m.dev.width = b.width;
   m.dev.depth = b.depth;
-  for (int k = 0; k < 3; ++k) {  // the padded root box (empty when there is no mesh)
-    m.dev.box_lo[k] = b.root_lo[k];
-    m.dev.box_hi[k] = b.root_hi[k];
+  for (int k = 0; k < 3; ++k) {
+    // the padded root box (empty when there is no mesh): binary trees test it
+    // in their grid's units, wide trees in metres
+    m.dev.box_lo[k] = b.width == 2 ? b.qroot_lo[k] : b.root_lo[k];
+    m.dev.box_hi[k] = b.width == 2 ? b.qroot_hi[k] : b.root_hi[k];
+    m.dev.qorigin[k] = b.qorigin[k];
+    m.dev.qstep[k] = b.qstep[k];
   }
   m.dev.n_tri = n_tri;
   m.dev.n_tri_leaf = b.n_leaf_tris;

@@ -791,7 +791,8 @@ bool build_bvh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t
   }
   const size_t n_nodes = bn.empty() ? 0 : (single_leaf ? 1 : inner_order.size());
   out->n_nodes = n_nodes;
-  out->nodes = (float*)std::calloc(std::max<size_t>(n_nodes, 1) * 16, sizeof(float));
+  out->node_bytes = 32;
+  out->nodes = (float*)std::calloc(std::max<size_t>(n_nodes, 1) * 8, sizeof(float));
 
   // triangles in leaf order
   out->n_leaf_tris = (uint32_t)leaf_refs.size();
@@ -811,8 +812,24 @@ bool build_bvh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t
     out->tris64[12 * k + 9] = (double)i;
   }
 
-  auto pad_lo = [&](double v) { return pad_down(v, scale); };
-  auto pad_hi = [&](double v) { return pad_up(v, scale); };
+  // The boxes' grid: a step 2^e per axis with the padded root box inside
+  // 65,533 steps, and an origin one step below it, so that every box,
+  // widened by one step each way, keeps its coordinates in [0, 65535].
+  for (int a = 0; a < 3 && !bn.empty(); ++a) {
+    const double ext = std::max((double)out->root_hi[a] - (double)out->root_lo[a], 1e-30);
+    int e = (int)std::ceil(std::log2(ext / 65533.0));
+    while (std::ldexp(65533.0, e) < ext) ++e;
+    const double step = std::ldexp(1.0, e);
+    float origin = (float)((double)out->root_lo[a] - step);
+    if ((double)origin > (double)out->root_lo[a] - step) origin = std::nextafter(origin, -INFINITY);
+    out->qorigin[a] = origin;
+    out->qstep[a] = (float)step;
+  }
+  auto qcoord = [&](double v, int a, bool up) {
+    const double x = (v - (double)out->qorigin[a]) / (double)out->qstep[a];
+    const double q = up ? std::ceil(x) + 1.0 : std::floor(x) - 1.0;
+    return (uint32_t)std::min(65535.0, std::max(0.0, q));
+  };
   auto child_code = [&](int32_t b, uint32_t& depth_seen) -> int32_t {
     const BNode& c = bn[b];
     depth_seen = std::max(depth_seen, c.depth);
@@ -820,37 +837,47 @@ bool build_bvh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t
     out->leaf_max = std::max(out->leaf_max, c.count);
     return ~(int32_t)((c.count << 24) | c.first);
   };
-  auto write_child = [&](float* nd, int slot, const Box* box) {
-    // slot 0 -> n0 and n2.xy ; slot 1 -> n1 and n2.zw
-    float* xy = nd + 4 * slot;
-    float* z = nd + 8 + 2 * slot;
-    if (box == nullptr) {
-      // empty child: a point box far outside any control volume, which no ray reaches
-      xy[0] = xy[1] = xy[2] = xy[3] = z[0] = z[1] = 1e30f;
-      return;
+  uint32_t qlo_root[3] = {65535u, 65535u, 65535u}, qhi_root[3] = {0u, 0u, 0u};
+  // writes a child's box (null: the empty child, a point at the grid's far
+  // corner) into its three words; grows the root's grid box when asked
+  auto write_child = [&](uint32_t* nd, int slot, const Box* box, bool root) {
+    uint32_t qlo[3], qhi[3];
+    for (int a = 0; a < 3; ++a) {
+      qlo[a] = box ? qcoord(pad_down(box->lo[a], scale), a, false) : 65535u;
+      qhi[a] = box ? qcoord(pad_up(box->hi[a], scale), a, true) : 65535u;
+      if (root && box) {
+        qlo_root[a] = std::min(qlo_root[a], qlo[a]);
+        qhi_root[a] = std::max(qhi_root[a], qhi[a]);
+      }
     }
-    xy[0] = pad_lo(box->lo[0]); xy[1] = pad_hi(box->hi[0]);
-    xy[2] = pad_lo(box->lo[1]); xy[3] = pad_hi(box->hi[1]);
-    z[0] = pad_lo(box->lo[2]); z[1] = pad_hi(box->hi[2]);
+    uint32_t* w = nd + 3 * slot;
+    w[0] = qlo[0] | (qlo[1] << 16);
+    w[1] = qlo[2] | (qhi[0] << 16);
+    w[2] = qhi[1] | (qhi[2] << 16);
   };
   uint32_t depth_seen = 0;
+  uint32_t* nodes = reinterpret_cast<uint32_t*>(out->nodes);
   if (single_leaf) {
-    float* nd = out->nodes;
-    write_child(nd, 0, &bn[0].box);
-    write_child(nd, 1, nullptr);
+    write_child(nodes, 0, &bn[0].box, true);
+    write_child(nodes, 1, nullptr, true);
     int32_t c0 = child_code(0, depth_seen), c1 = ~(int32_t)0;  // empty leaf: count 0
-    std::memcpy(nd + 12, &c0, 4);
-    std::memcpy(nd + 13, &c1, 4);
+    std::memcpy(nodes + 6, &c0, 4);
+    std::memcpy(nodes + 7, &c1, 4);
   } else {
     for (size_t g = 0; g < inner_order.size(); ++g) {
       const BNode& b = bn[inner_order[g]];
-      float* nd = out->nodes + 16 * g;
-      write_child(nd, 0, &bn[b.left].box);
-      write_child(nd, 1, &bn[b.right].box);
+      uint32_t* nd = nodes + 8 * g;
+      write_child(nd, 0, &bn[b.left].box, g == 0);
+      write_child(nd, 1, &bn[b.right].box, g == 0);
       int32_t c0 = child_code(b.left, depth_seen), c1 = child_code(b.right, depth_seen);
-      std::memcpy(nd + 12, &c0, 4);
-      std::memcpy(nd + 13, &c1, 4);
+      std::memcpy(nd + 6, &c0, 4);
+      std::memcpy(nd + 7, &c1, 4);
     }
+  }
+  // the root box in the grid units the kernel's slab test reads: 2^23 + q
+  for (int a = 0; a < 3 && n_nodes > 0; ++a) {
+    out->qroot_lo[a] = 8388608.0f + (float)qlo_root[a];
+    out->qroot_hi[a] = 8388608.0f + (float)qhi_root[a];
   }
   out->depth = depth_seen;
   if (out->depth + 1 >= (uint32_t)kMaxStack) {

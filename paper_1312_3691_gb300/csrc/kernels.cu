@@ -614,10 +614,32 @@ __device__ __forceinline__ void test_triangle(const Ray<R>& r, const Shear<R>& s
 
 template <typename R>
 __device__ __forceinline__ void slab(R lo, R hi, R inv, R oi, R& tn, R& tf) {
-  const R a = lo * inv - oi, b = hi * inv - oi;
+  const R a = fma(lo, inv, -oi), b = fma(hi, inv, -oi);
   tn = fmin(a, b);
   tf = fmax(a, b);
 }
+
+// Binary trees keep their boxes on the mesh's grid: plane = qorigin + q qstep.
+// The ray's slab constants are turned into grid units once per segment, so
+// that a node's plane q, read as the float 2^23 + q (exact), gives its
+// distance t = (2^23 + q) inv' - oi' in one FMA: inv' = qstep / d (exact,
+// qstep is a power of two) and oi' = 2^23 inv' - (qorigin - o) / d.  The
+// rounding of oi' is below half a grid step, inside the one step by which
+// the builder widens every box.
+template <typename R>
+__device__ __forceinline__ void ray_to_grid(Ray<R>& r, const MeshDev& m) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const R sa = (R)m.qstep[i] * r.inv[i];
+    const R oa = fma((R)m.qorigin[i], r.inv[i], -r.oi[i]);
+    r.inv[i] = sa;
+    r.oi[i] = fma((R)8388608.0, sa, -oa);
+  }
+}
+
+// The two 16-bit coordinates of word w as floats 2^23 + q (exact).
+__device__ __forceinline__ float grid_lo(uint32_t w) { return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7610u)); }
+__device__ __forceinline__ float grid_hi(uint32_t w) { return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7632u)); }
 
 // Resumable traversal of one ray, organised as in Aila & Laine's
 // "while-while" scheme with speculative traversal: a warp steps through inner
@@ -689,26 +711,29 @@ __device__ __forceinline__ void trav_inner(const MeshDev& m, const float4* __res
                                            const Ray<R>& r, Trav<R>& t, StackE<R>* stack, uint32_t& n_nodes,
                                            int* err) {
   ++n_nodes;
-  float4 n0, n1, n2, n3;
+  float4 n0, n1;
   if (STAGE && (uint32_t)t.cur < n_stage) {
-    n0 = s_nodes[4 * t.cur]; n1 = s_nodes[4 * t.cur + 1]; n2 = s_nodes[4 * t.cur + 2]; n3 = s_nodes[4 * t.cur + 3];
+    n0 = s_nodes[2 * t.cur]; n1 = s_nodes[2 * t.cur + 1];
   } else {
-    const float4* g = m.nodes + 4 * (size_t)t.cur;
-    n0 = __ldg(g); n1 = __ldg(g + 1); n2 = __ldg(g + 2); n3 = __ldg(g + 3);
+    const float4* g = m.nodes + 2 * (size_t)t.cur;
+    n0 = __ldg(g); n1 = __ldg(g + 1);
   }
+  // child 0: words 0-2 of n0; child 1: n0.w, n1.x, n1.y; child codes n1.z, n1.w
+  const uint32_t w0 = __float_as_uint(n0.x), w1 = __float_as_uint(n0.y), w2 = __float_as_uint(n0.z);
+  const uint32_t w3 = __float_as_uint(n0.w), w4 = __float_as_uint(n1.x), w5 = __float_as_uint(n1.y);
   R a0, b0, a1, b1, a2, b2;
-  slab<R>((R)n0.x, (R)n0.y, r.inv[0], r.oi[0], a0, b0);
-  slab<R>((R)n0.z, (R)n0.w, r.inv[1], r.oi[1], a1, b1);
-  slab<R>((R)n2.x, (R)n2.y, r.inv[2], r.oi[2], a2, b2);
+  slab<R>((R)grid_lo(w0), (R)grid_hi(w1), r.inv[0], r.oi[0], a0, b0);
+  slab<R>((R)grid_hi(w0), (R)grid_lo(w2), r.inv[1], r.oi[1], a1, b1);
+  slab<R>((R)grid_lo(w1), (R)grid_hi(w2), r.inv[2], r.oi[2], a2, b2);
   const R tmin0 = fmax(fmax(a0, a1), fmax(a2, r.tlo));
   const R tmax0 = fmin(fmin(b0, b1), fmin(b2, t.tbest));
-  slab<R>((R)n1.x, (R)n1.y, r.inv[0], r.oi[0], a0, b0);
-  slab<R>((R)n1.z, (R)n1.w, r.inv[1], r.oi[1], a1, b1);
-  slab<R>((R)n2.z, (R)n2.w, r.inv[2], r.oi[2], a2, b2);
+  slab<R>((R)grid_lo(w3), (R)grid_hi(w4), r.inv[0], r.oi[0], a0, b0);
+  slab<R>((R)grid_hi(w3), (R)grid_lo(w5), r.inv[1], r.oi[1], a1, b1);
+  slab<R>((R)grid_lo(w4), (R)grid_hi(w5), r.inv[2], r.oi[2], a2, b2);
   const R tmin1 = fmax(fmax(a0, a1), fmax(a2, r.tlo));
   const R tmax1 = fmin(fmin(b0, b1), fmin(b2, t.tbest));
   const bool h0 = tmin0 <= tmax0, h1 = tmin1 <= tmax1;
-  int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+  int c0 = __float_as_int(n1.z), c1 = __float_as_int(n1.w);
   if (h0 && h1) {
     R tfar = tmin1;
     if (tmin1 < tmin0) { const int x = c0; c0 = c1; c1 = x; tfar = tmin0; }
@@ -1299,11 +1324,12 @@ __device__ __forceinline__ bool ray_meets_box(const Ray<R>& r, const MeshDev& m)
 // of spills inside the out-of-line seeding).  MINB = 0: 256-thread blocks,
 // two per SM in float (at most 128 registers), one in double.
 template <int W, typename R, typename TV>
-__device__ __forceinline__ void begin_trav(Ray<R>& r, TV& tv) {
+__device__ __forceinline__ void begin_trav(Ray<R>& r, TV& tv, const MeshDev& m) {
   if constexpr (W > 2) {
     ray_order<W>(r);
     travw_begin(tv, r);
   } else {
+    ray_to_grid<R>(r, m);
     trav_begin(tv);
   }
 }
@@ -1312,7 +1338,7 @@ template <typename R, int MINB, bool CLL, int W>
 __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeof(R) == 4 ? 2 : 1))
     trace_kernel(TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr uint32_t kNodeF4 = 4;  // float4 per binary node
+  constexpr uint32_t kNodeF4 = kBinaryNodeF4;  // float4 per binary node
   // only the binary traversal reads staged nodes
   const uint32_t n_stage = W > 2 ? 0u : min(a.smem_nodes, a.mesh.n_nodes);
   float4* s_nodes = reinterpret_cast<float4*>(smem);
@@ -1402,7 +1428,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
           if (!escapes) {
             const R speed = Fn<R>::sqrt(vv);
             make_ray<R>(ray, hp, v, (sizeof(R) == 4 ? (R)1e-6 : (R)1e-9) / speed);
-            begin_trav<W>(ray, tv);
+            begin_trav<W>(ray, tv, a.mesh);
             tdone = a.mesh.n_nodes == 0;
             finish = false;
           }
@@ -1477,7 +1503,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
         qi = nq;
         const R speed = Fn<R>::sqrt(vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
         make_ray<R>(ray, pos, vel, (sizeof(R) == 4 ? (R)1e-6 : (R)1e-9) / speed);
-        begin_trav<W>(ray, tv);
+        begin_trav<W>(ray, tv, a.mesh);
         tdone = a.mesh.n_nodes == 0;
         has = true;
         bounce = 0;
@@ -1845,7 +1871,8 @@ size_t trace_smem_bytes(const LaunchCfg& cfg, uint32_t n_nodes, uint32_t variant
   const uint32_t precision = variant & 1u;
   const size_t queue = (size_t)(cfg.block / 32) * kQueue *
                        (precision == TPMC_FP64 ? sizeof(Seeded<double>) : sizeof(Seeded<float>));
-  const size_t staged = variant_width(variant) > 2 ? 0 : (size_t)std::min(cfg.smem_nodes, n_nodes) * 4 * sizeof(float4);
+  const size_t staged =
+      variant_width(variant) > 2 ? 0 : (size_t)std::min(cfg.smem_nodes, n_nodes) * kBinaryNodeF4 * sizeof(float4);
   return staged + queue + (size_t)cfg.block * sizeof(LaneAcc);
 }
 

@@ -30,15 +30,19 @@ constexpr int kMaxStack = 64;    // BVH traversal stack (the builder keeps depth
 constexpr int kMaxRecordK = 64;  // hits recorded per particle in verification runs
 
 // ---------------------------------------------------------------- mesh (device)
-// BVH node (64 bytes, both children's boxes in one node):
-//   n0 = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
-//   n1 = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
-//   n2 = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
-//   n3 = (child0, child1, 0, 0) as int bits.  child >= 0: inner node index;
+// Binary BVH node (32 bytes, both children's boxes in one node), boxes as
+// 16-bit coordinates q on one grid over the whole mesh: along axis a the
+// plane is qorigin[a] + q qstep[a] (qstep a power of two; the boxes are
+// rounded outward and widened by one grid step, so float slab tests stay
+// conservative).
+//   words 0-2: child 0's (lo.x | lo.y << 16), (lo.z | hi.x << 16), (hi.y | hi.z << 16)
+//   words 3-5: the same for child 1
+//   words 6-7: child0, child1 as int.  child >= 0: inner node index;
 //        child < 0: leaf ~(count << 24 | first), triangles [first, first+count)
 //        of the leaf-ordered triangle arrays; count <= 127.
 // Nodes are numbered breadth first, so nodes [0, k) are the top of the tree
 // and can be staged in shared memory as a block.
+constexpr int kBinaryNodeF4 = 2;  // float4 per binary node
 // Compressed wide BVH node (after Ylitie, Karras & Laine, "Efficient
 // incoherent ray traversal on GPUs through compressed wide BVHs", HPG 2017):
 // the child boxes are 8-bit coordinates on a grid of the node's own, so one
@@ -77,7 +81,9 @@ struct MeshDev {
   uint32_t width = 2;               // 2: binary nodes; 4 or 8: compressed wide nodes
   uint32_t depth = 0;               // levels below the root (bounds the wide traversal's stack)
   float scene_radius = 1.0f;
-  float box_lo[3] = {0.0f, 0.0f, 0.0f}, box_hi[3] = {-1.0f, -1.0f, -1.0f};  // padded root box (empty: no mesh)
+  // padded root box (empty: no mesh); binary trees: in grid units 2^23 + q
+  float box_lo[3] = {0.0f, 0.0f, 0.0f}, box_hi[3] = {-1.0f, -1.0f, -1.0f};
+  float qorigin[3] = {0.0f, 0.0f, 0.0f}, qstep[3] = {1.0f, 1.0f, 1.0f};  // grid of binary trees' boxes
 };
 
 // ------------------------------------------------------------- query (device)
@@ -197,7 +203,7 @@ inline uint32_t trace_variant(const tpmc_params* p, const MeshDev& m) {
          (m.width == 8 ? kVariantWide8 : (m.width == 4 ? kVariantWide4 : 0u));
 }
 inline uint32_t variant_width(uint32_t v) { return (v & kVariantWide8) ? 8u : ((v & kVariantWide4) ? 4u : 2u); }
-inline uint32_t node_float4s(uint32_t width) { return width == 8 ? 5u : 4u; }
+inline uint32_t node_float4s(uint32_t width) { return width == 8 ? 5u : (width == 4 ? 4u : 2u); }
 
 cudaError_t launch_setup(QueryDev* d_queries, uint32_t nq, const QueryDev* d_base, const double* d_dirs,
                          const double* d_S, ItemDev* d_items, const uint32_t* d_slots, cudaStream_t stream);
@@ -218,6 +224,9 @@ struct BvhBuild {
   uint32_t width = 2;        // children per node: 2 (binary layout) or 4, 8 (compressed wide layout)
   uint32_t node_bytes = 64;  // bytes per node in `nodes`
   float root_lo[3] = {0.0f, 0.0f, 0.0f}, root_hi[3] = {-1.0f, -1.0f, -1.0f};  // padded root box (empty: no mesh)
+  // binary layout: the boxes' grid, and the root box in grid units 2^23 + q
+  float qorigin[3] = {0.0f, 0.0f, 0.0f}, qstep[3] = {1.0f, 1.0f, 1.0f};
+  float qroot_lo[3] = {0.0f, 0.0f, 0.0f}, qroot_hi[3] = {-1.0f, -1.0f, -1.0f};
   uint32_t depth = 0, leaf_max = 0, n_skipped = 0;
   uint32_t n_exposed = 0;    // triangle sides the whole mesh lies behind
   // host copies ready for upload

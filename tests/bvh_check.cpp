@@ -125,7 +125,7 @@ int main(int argc, char** argv) {
   for (size_t g = 0; g < b.n_nodes && b.width == 2; ++g)
     for (int c = 0; c < 2; ++c) {
       int32_t code;
-      std::memcpy(&code, b.nodes + 16 * g + 12 + c, 4);
+      std::memcpy(&code, b.nodes + 8 * g + 6 + c, 4);
       if (code < 0 && ((~(uint32_t)code) >> 24) > 127u) ++oversized;
     }
 
@@ -207,32 +207,30 @@ int main(int argc, char** argv) {
         }
       }
     } else if (b.n_nodes > 0) {
+      // binary nodes: 16-bit boxes on the mesh's grid, decoded exactly in double
       stack.assign(1, 0);
       while (!stack.empty()) {
         const int32_t node = stack.back();
         stack.pop_back();
-        const float* nd = b.nodes + 16 * (size_t)node;
+        if (node < 0 || (size_t)node >= b.n_nodes) { ++bad_index; continue; }
+        const uint32_t* nd = reinterpret_cast<const uint32_t*>(b.nodes) + 8 * (size_t)node;
         for (int c = 0; c < 2; ++c) {
-          const float* xy = nd + 4 * c;
-          const float* z = nd + 8 + 2 * c;
-          const double lo[3] = {xy[0], xy[2], z[0]}, hi[3] = {xy[1], xy[3], z[1]};
-          double tn = 0.0, tf = walk.t;
-          for (int i = 0; i < 3; ++i) {
-            if (d[i] == 0.0) {
-              if (o[i] < lo[i] || o[i] > hi[i]) tn = INFINITY;
-              continue;
-            }
-            const double t0 = (lo[i] - o[i]) / d[i], t1 = (hi[i] - o[i]) / d[i];
-            tn = std::fmax(tn, std::fmin(t0, t1));
-            tf = std::fmin(tf, std::fmax(t0, t1));
+          const uint32_t* w = nd + 3 * c;
+          const uint32_t ql[3] = {w[0] & 0xFFFFu, w[0] >> 16, w[1] & 0xFFFFu};
+          const uint32_t qh[3] = {w[1] >> 16, w[2] & 0xFFFFu, w[2] >> 16};
+          double lo[3], hi[3];
+          for (int a = 0; a < 3; ++a) {
+            lo[a] = (double)b.qorigin[a] + (double)b.qstep[a] * ql[a];
+            hi[a] = (double)b.qorigin[a] + (double)b.qstep[a] * qh[a];
           }
-          if (!(tn <= tf)) continue;
+          if (!slab(lo, hi)) continue;
           int32_t code;
-          std::memcpy(&code, nd + 12 + c, 4);
+          std::memcpy(&code, nd + 6 + c, 4);
           if (code >= 0) {
             stack.push_back(code);
           } else {
             const uint32_t u = ~(uint32_t)code, first = u & 0xFFFFFFu, count = u >> 24;
+            if (first + count > b.n_leaf_tris) { ++bad_index; continue; }
             for (uint32_t k = first; k < first + count; ++k) {
               uint32_t id;
               std::memcpy(&id, b.tris + 12 * (size_t)k + 3, 4);

@@ -115,7 +115,7 @@ def test_tree_closest_hits_equal_brute_force(checker, tmp_path, name, width):
     xyz, tri = np.asarray(xyz, float), np.asarray(tri)
     rays = _rays(xyz, tri, np.random.default_rng(17))
     r = _check(checker, tmp_path, xyz, tri, rays, width=width)
-    assert r["width"] == width and r["node_bytes"] == {2: 64, 4: 64, 8: 80}[width], r
+    assert r["width"] == width and r["node_bytes"] == {2: 32, 4: 64, 8: 80}[width], r
     assert r["mismatches"] == 0 and r["bad_index"] == 0, r
     assert r["unreferenced"] == 0 and r["oversized"] == 0, r
     assert r["hits"] > 0.2 * r["rays"], r
