@@ -898,8 +898,8 @@ def run_profile_launch(args):
     from paper_1312_3691_gb300.build import build
 
     build()
-    if args.profile_launch == "satellite-sweep":
-        case = W.satellite_case(N=1)
+    if args.profile_launch in ("satellite-sweep", "satellite500k-sweep"):
+        case = W.satellite_case(N=1, target_triangles=500_000 if "500k" in args.profile_launch else 60_000)
         grid = W.attitude_grid(8, 12)
         g = {"xyz": case["xyz"], "tri": case["tri"], "base": case["params"], "dirs": grid,
              "S": np.full(len(grid), 7.0), "cases": list(range(len(grid)))}
@@ -947,7 +947,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the satellite, attitude-sweep and serving runs")
     ap.add_argument("--profile-launch", default=None,
-                    help="plate-specular|plate-diffuse|cylinder-specular|cylinder-diffuse|satellite-sweep: one small launch")
+                    help="plate-specular|plate-diffuse|cylinder-specular|cylinder-diffuse|satellite-sweep|"
+                         "satellite500k-sweep: one small launch")
     ap.add_argument("--profile-n-each", type=int, default=100_000)
     ap.add_argument("--launch", default=None,
                     help="block,blocks_per_sm,chunk,smem_nodes[,refill_at,bvh_leaf,bvh_width] for --profile-launch "
