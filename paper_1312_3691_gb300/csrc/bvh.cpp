@@ -851,9 +851,7 @@ bool build_bvh(const double* xyz, uint32_t n_vert, const uint32_t* tri, uint32_t
       }
     }
     uint32_t* w = nd + 3 * slot;
-    w[0] = qlo[0] | (qlo[1] << 16);
-    w[1] = qlo[2] | (qhi[0] << 16);
-    w[2] = qhi[1] | (qhi[2] << 16);
+    for (int a = 0; a < 3; ++a) w[a] = qlo[a] | (qhi[a] << 16);
   };
   uint32_t depth_seen = 0;
   uint32_t* nodes = reinterpret_cast<uint32_t*>(out->nodes);

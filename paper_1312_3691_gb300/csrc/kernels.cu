@@ -543,6 +543,7 @@ struct Ray {
   // wide trees: visit position (0 first) of each child-box corner c (nibble c
   // of ptab) and the corner at each position (nibble p of stab)
   uint32_t ptab, stab;
+  uint32_t nsel[3];  // binary trees: selectors of the near box planes (ray_to_grid)
 };
 
 // Woop, Benthin & Wald (JCGT 2013): shear the ray onto +z of a permuted frame.
@@ -612,6 +613,20 @@ __device__ __forceinline__ void test_triangle(const Ray<R>& r, const Shear<R>& s
   if (t < tbest || (t == tbest && id < best)) { tbest = t; best = id; }
 }
 
+// Three-input min and max (one instruction each for float on sm_100 and later).
+__device__ __forceinline__ float max3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float min3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ double max3(double a, double b, double c) { return fmax(fmax(a, b), c); }
+__device__ __forceinline__ double min3(double a, double b, double c) { return fmin(fmin(a, b), c); }
+
 template <typename R>
 __device__ __forceinline__ void slab(R lo, R hi, R inv, R oi, R& tn, R& tf) {
   const R a = fma(lo, inv, -oi), b = fma(hi, inv, -oi);
@@ -625,7 +640,10 @@ __device__ __forceinline__ void slab(R lo, R hi, R inv, R oi, R& tn, R& tf) {
 // distance t = (2^23 + q) inv' - oi' in one FMA: inv' = qstep / d (exact,
 // qstep is a power of two) and oi' = 2^23 inv' - (qorigin - o) / d.  The
 // rounding of oi' is below half a grid step, inside the one step by which
-// the builder widens every box.
+// the builder widens every box.  A box's lo and hi along an axis share a
+// word, and nsel[a] is the byte selector that reads the plane the ray meets
+// first along a (lo where it runs towards +a); the other plane's selector is
+// nsel[a] ^ 0x22.  The near and far distances then need no min and max.
 template <typename R>
 __device__ __forceinline__ void ray_to_grid(Ray<R>& r, const MeshDev& m) {
 #pragma unroll
@@ -634,12 +652,14 @@ __device__ __forceinline__ void ray_to_grid(Ray<R>& r, const MeshDev& m) {
     const R oa = fma((R)m.qorigin[i], r.inv[i], -r.oi[i]);
     r.inv[i] = sa;
     r.oi[i] = fma((R)8388608.0, sa, -oa);
+    r.nsel[i] = sa >= (R)0 ? 0x7610u : 0x7632u;
   }
 }
 
-// The two 16-bit coordinates of word w as floats 2^23 + q (exact).
-__device__ __forceinline__ float grid_lo(uint32_t w) { return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7610u)); }
-__device__ __forceinline__ float grid_hi(uint32_t w) { return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7632u)); }
+// A 16-bit coordinate of word w (the half that selector sel picks) as the float 2^23 + q (exact).
+__device__ __forceinline__ float grid_q(uint32_t w, uint32_t sel) {
+  return __int_as_float((int)__byte_perm(w, 0x4B000000u, sel));
+}
 
 // Resumable traversal of one ray, organised as in Aila & Laine's
 // "while-while" scheme with speculative traversal: a warp steps through inner
@@ -718,20 +738,21 @@ __device__ __forceinline__ void trav_inner(const MeshDev& m, const float4* __res
     const float4* g = m.nodes + 2 * (size_t)t.cur;
     n0 = __ldg(g); n1 = __ldg(g + 1);
   }
-  // child 0: words 0-2 of n0; child 1: n0.w, n1.x, n1.y; child codes n1.z, n1.w
-  const uint32_t w0 = __float_as_uint(n0.x), w1 = __float_as_uint(n0.y), w2 = __float_as_uint(n0.z);
-  const uint32_t w3 = __float_as_uint(n0.w), w4 = __float_as_uint(n1.x), w5 = __float_as_uint(n1.y);
-  R a0, b0, a1, b1, a2, b2;
-  slab<R>((R)grid_lo(w0), (R)grid_hi(w1), r.inv[0], r.oi[0], a0, b0);
-  slab<R>((R)grid_hi(w0), (R)grid_lo(w2), r.inv[1], r.oi[1], a1, b1);
-  slab<R>((R)grid_lo(w1), (R)grid_hi(w2), r.inv[2], r.oi[2], a2, b2);
-  const R tmin0 = fmax(fmax(a0, a1), fmax(a2, r.tlo));
-  const R tmax0 = fmin(fmin(b0, b1), fmin(b2, t.tbest));
-  slab<R>((R)grid_lo(w3), (R)grid_hi(w4), r.inv[0], r.oi[0], a0, b0);
-  slab<R>((R)grid_hi(w3), (R)grid_lo(w5), r.inv[1], r.oi[1], a1, b1);
-  slab<R>((R)grid_lo(w4), (R)grid_hi(w5), r.inv[2], r.oi[2], a2, b2);
-  const R tmin1 = fmax(fmax(a0, a1), fmax(a2, r.tlo));
-  const R tmax1 = fmin(fmin(b0, b1), fmin(b2, t.tbest));
+  // child 0: x, y, z words n0.x, n0.y, n0.z; child 1: n0.w, n1.x, n1.y; child codes n1.z, n1.w
+  const uint32_t w[6] = {__float_as_uint(n0.x), __float_as_uint(n0.y), __float_as_uint(n0.z),
+                         __float_as_uint(n0.w), __float_as_uint(n1.x), __float_as_uint(n1.y)};
+  R tn[2][3], tf[2][3];
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      tn[c][a] = fma((R)grid_q(w[3 * c + a], r.nsel[a]), r.inv[a], -r.oi[a]);
+      tf[c][a] = fma((R)grid_q(w[3 * c + a], r.nsel[a] ^ 0x22u), r.inv[a], -r.oi[a]);
+    }
+  const R tmin0 = max3(tn[0][0], tn[0][1], fmax(tn[0][2], r.tlo));
+  const R tmax0 = min3(tf[0][0], tf[0][1], fmin(tf[0][2], t.tbest));
+  const R tmin1 = max3(tn[1][0], tn[1][1], fmax(tn[1][2], r.tlo));
+  const R tmax1 = min3(tf[1][0], tf[1][1], fmin(tf[1][2], t.tbest));
   const bool h0 = tmin0 <= tmax0, h1 = tmin1 <= tmax1;
   int c0 = __float_as_int(n1.z), c1 = __float_as_int(n1.w);
   if (h0 && h1) {
@@ -870,18 +891,6 @@ __device__ __forceinline__ float byte_float(uint32_t w, uint32_t k) {
   return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7440u + k)) - 8388608.0f;
 }
 
-__device__ __forceinline__ float max3(float a, float b, float c) {
-  float r;
-  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
-}
-__device__ __forceinline__ float min3(float a, float b, float c) {
-  float r;
-  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
-}
-__device__ __forceinline__ double max3(double a, double b, double c) { return fmax(fmax(a, b), c); }
-__device__ __forceinline__ double min3(double a, double b, double c) { return fmin(fmin(a, b), c); }
 
 // Float bound below t (its low 8 bits are cleared to make room for imask).
 __device__ __forceinline__ uint32_t t_bits_down(float t) { return __float_as_uint(t) & ~0xFFu; }

@@ -35,7 +35,7 @@ constexpr int kMaxRecordK = 64;  // hits recorded per particle in verification r
 // plane is qorigin[a] + q qstep[a] (qstep a power of two; the boxes are
 // rounded outward and widened by one grid step, so float slab tests stay
 // conservative).
-//   words 0-2: child 0's (lo.x | lo.y << 16), (lo.z | hi.x << 16), (hi.y | hi.z << 16)
+//   words 0-2: child 0's (lo.x | hi.x << 16), (lo.y | hi.y << 16), (lo.z | hi.z << 16)
 //   words 3-5: the same for child 1
 //   words 6-7: child0, child1 as int.  child >= 0: inner node index;
 //        child < 0: leaf ~(count << 24 | first), triangles [first, first+count)

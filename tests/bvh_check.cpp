@@ -216,8 +216,8 @@ int main(int argc, char** argv) {
         const uint32_t* nd = reinterpret_cast<const uint32_t*>(b.nodes) + 8 * (size_t)node;
         for (int c = 0; c < 2; ++c) {
           const uint32_t* w = nd + 3 * c;
-          const uint32_t ql[3] = {w[0] & 0xFFFFu, w[0] >> 16, w[1] & 0xFFFFu};
-          const uint32_t qh[3] = {w[1] >> 16, w[2] & 0xFFFFu, w[2] >> 16};
+          const uint32_t ql[3] = {w[0] & 0xFFFFu, w[1] & 0xFFFFu, w[2] & 0xFFFFu};
+          const uint32_t qh[3] = {w[0] >> 16, w[1] >> 16, w[2] >> 16};
           double lo[3], hi[3];
           for (int a = 0; a < 3; ++a) {
             lo[a] = (double)b.qorigin[a] + (double)b.qstep[a] * ql[a];
