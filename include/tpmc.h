@@ -180,7 +180,7 @@ typedef struct {
   uint32_t blocks_per_sm;       /* resident blocks per SM (grid = SMs x this)           */
   uint32_t chunk;               /* particle ids a warp takes per fetch (0: automatic)   */
   uint32_t smem_nodes;          /* BVH nodes staged in shared memory                    */
-  uint32_t refill_at;           /* finished lanes that end a traversal round (0: 24)    */
+  uint32_t refill_at;           /* finished lanes that end a traversal round (0: 16)    */
   uint32_t bvh_leaf;            /* largest BVH leaf for later tpmc_mesh_load (0: 4)     */
   uint32_t bvh_width;           /* children per BVH node for later tpmc_mesh_load: 2, 4  */
                                 /* or 8 (0: the default, or what tpmc_tune chose for     */

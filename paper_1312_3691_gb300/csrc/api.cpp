@@ -160,20 +160,20 @@ LaunchCfg Ctx::schedule(const MeshRec& m, uint32_t variant, uint64_t total) {
   if (manual_launch) cfg = manual;
   else if (it != tuned.end()) cfg = it->second;
   else {
-    // Untuned default, from same-box sweeps on GB300: on a tree of a few
-    // nodes the time goes to seeding, which prefers registers (256 threads,
-    // no register cap); on larger trees the traversal's dependent loads prefer
-    // more resident warps (128 threads at the highest occupancy, 8 blocks).
-    cfg.block = m.dev.n_nodes <= 8 ? 256 : 128;
+    // Untuned default, from same-box sweeps on GB300 with the current kernel:
+    // 128 threads at the highest occupancy (8 blocks per SM) for every tree;
+    // on the 2-triangle plate 3-4 % faster than 256 threads without a register
+    // cap, on the cylinder 6 %, on the satellite 7-15 % faster than 5-7 blocks.
+    cfg.block = 128;
     cfg.smem_nodes = 0;  // the hot top of the tree stays in L1; shared-memory staging costs bank conflicts
     cfg.blocks_per_sm = 0;
     cfg.chunk = 0;
   }
   cfg.smem_nodes = m.dev.width > 2 ? 0u : std::min<uint32_t>(cfg.smem_nodes, m.dev.n_nodes);  // wide: none staged
   // A traversal round ends once this many lanes have finished their rays.
-  // Same-box sweeps after the spatial-split BVH: 24 is 6 % faster than 16 on
-  // the cylinder sweep, equal on the plate and the satellite; 32 is slower.
-  if (cfg.refill_at == 0 || cfg.refill_at > 32) cfg.refill_at = 24;
+  // Same-box sweeps with the current kernel: 16 to 28 are equal on the plate
+  // and the cylinder; on the satellite 16 is 3 % faster than 24 and 2 % than 20.
+  if (cfg.refill_at == 0 || cfg.refill_at > 32) cfg.refill_at = 16;
   const int maxb = trace_max_blocks_per_sm(variant, cfg, m.dev.n_nodes);
   if (cfg.blocks_per_sm == 0 || (int)cfg.blocks_per_sm > maxb) cfg.blocks_per_sm = std::max(1, maxb);
   if (cfg.chunk == 0) {
