@@ -160,11 +160,14 @@ LaunchCfg Ctx::schedule(const MeshRec& m, uint32_t variant, uint64_t total) {
   if (manual_launch) cfg = manual;
   else if (it != tuned.end()) cfg = it->second;
   else {
-    // Untuned default, from same-box sweeps on GB300 with the current kernel:
-    // 128 threads at the highest occupancy (8 blocks per SM) for every tree;
-    // on the 2-triangle plate 3-4 % faster than 256 threads without a register
-    // cap, on the cylinder 6 %, on the satellite 7-15 % faster than 5-7 blocks.
-    cfg.block = 128;
+    // Untuned default, from same-box sweeps on GB300 with the current kernel
+    // at the benchmark's launch size (96 cases x 1e7 particles): a tree of a
+    // few nodes (the 2-triangle plate) takes 256 threads with no register cap,
+    // 20 % faster there than 128 threads at 8 blocks per SM (in launches of
+    // 2e6 particles per case the order reverses, by 3-4 %); larger trees take
+    // 128 threads at the highest occupancy (8 blocks): the cylinder 12 %
+    // faster than 256 x 2, the satellite 7-15 % faster than 5-7 blocks.
+    cfg.block = m.dev.n_nodes <= 8 ? 256 : 128;
     cfg.smem_nodes = 0;  // the hot top of the tree stays in L1; shared-memory staging costs bank conflicts
     cfg.blocks_per_sm = 0;
     cfg.chunk = 0;
