@@ -286,7 +286,7 @@ tpmc_status tpmc_sweep_device(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_param
  * h_out [K]) and the same behaviour: an item rejected by its set-up reports
  * that in h_out[k].status, and h_out[k].ms is the call's wall time; per-panel
  * loads are not kept.  Its scratch is one fixed device
- * array of the library (64 queries, about 100 KB), held by every GPU that
+ * array of the library (64 queries, about 170 KB), held by every GPU that
  * loads the library until the process exits.  The first call on a device
  * looks up that array's device address (cudaGetSymbolAddress, which also
  * loads the library's device code there), so make that first call before any

@@ -1141,9 +1141,28 @@ __device__ __forceinline__ void lane_add_d2(LaneAcc& a, unsigned long long x) {
   a.d2lo = lo;
 }
 
-__device__ __forceinline__ void lane_flush(AccDev* acc, LaneAcc& a) {
+// Adds the 96-bit sum hi 2^64 + lo of one flush to the three limbs of the
+// stripe's squared-drag sum: bits 0-29, bits 30-59, and hi 2^4 + (lo >> 60).
+// Every flush carries at least one particle and a query has at most 2^34, so
+// each low limb stays below 2^34 2^30 = 2^64; the top limb stays below the
+// exact total over 2^60, which is below 2^36 (each particle's term is below
+// 2^62).
+__device__ __forceinline__ void add_d2(AccStripe& A, unsigned long long lo, unsigned long long hi) {
+  constexpr unsigned long long kM30 = (1ull << 30) - 1ull;
+  const unsigned long long l0 = lo & kM30, l1 = (lo >> 30) & kM30, l2 = (hi << 4) | (lo >> 60);
+  if (l0) atomicAdd(&A.d2[0], l0);
+  if (l1) atomicAdd(&A.d2[1], l1);
+  if (l2) atomicAdd(&A.d2[2], l2);
+}
+
+// The stripe of a query's sums that this warp adds to.
+__device__ __forceinline__ int acc_stripe() {
+  return (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) & (unsigned)(kAccStripes - 1));
+}
+
+__device__ __forceinline__ void lane_flush(AccDev* acc, LaneAcc& a, int stripe) {
   if (a.q < 0 || a.particles == 0) return;
-  AccDev& A = acc[a.q];
+  AccStripe& A = acc[a.q].s[stripe];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (a.F[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&A.F[i]), (unsigned long long)a.F[i]);
@@ -1153,13 +1172,7 @@ __device__ __forceinline__ void lane_flush(AccDev* acc, LaneAcc& a) {
   if (a.hit_particles) atomicAdd(&A.hit_particles, (unsigned long long)a.hit_particles);
   if (a.truncated) atomicAdd(&A.truncated, (unsigned long long)a.truncated);
   atomicAdd(&A.particles, (unsigned long long)a.particles);
-  if (a.d2lo != 0 || a.d2hi != 0) {
-    // 128-bit add: the low word's carry goes to the high word, so the total
-    // does not depend on the order of the lanes' flushes
-    const unsigned long long old = atomicAdd(&A.d2lo, a.d2lo);
-    const unsigned long long carry = old + a.d2lo < old ? 1ull : 0ull;
-    if (a.d2hi != 0 || carry != 0) atomicAdd(&A.d2hi, (unsigned long long)a.d2hi + carry);
-  }
+  add_d2(A, a.d2lo, a.d2hi);
 }
 
 // Flush at the end of the kernel, where every lane of the warp arrives
@@ -1168,10 +1181,10 @@ __device__ __forceinline__ void lane_flush(AccDev* acc, LaneAcc& a) {
 // 128-bit sum of squares with its carry) and one lane issues the atomics;
 // lanes of mixed queries flush one by one.  Integer sums, so the result is
 // the same either way.
-__device__ __forceinline__ void warp_flush(AccDev* acc, LaneAcc& a) {
+__device__ __forceinline__ void warp_flush(AccDev* acc, LaneAcc& a, int stripe) {
   const unsigned same = __match_any_sync(kFull, a.q);
   if (same != kFull || a.q < 0) {
-    lane_flush(acc, a);
+    lane_flush(acc, a, stripe);
     return;
   }
   long long F[3], T[3];
@@ -1196,7 +1209,7 @@ __device__ __forceinline__ void warp_flush(AccDev* acc, LaneAcc& a) {
     parts += __shfl_xor_sync(kFull, parts, m);
   }
   if ((threadIdx.x & 31u) != 0u || parts == 0) return;
-  AccDev& A = acc[a.q];
+  AccStripe& A = acc[a.q].s[stripe];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (F[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&A.F[i]), (unsigned long long)F[i]);
@@ -1206,17 +1219,13 @@ __device__ __forceinline__ void warp_flush(AccDev* acc, LaneAcc& a) {
   if (hitp) atomicAdd(&A.hit_particles, hitp);
   if (trunc) atomicAdd(&A.truncated, trunc);
   atomicAdd(&A.particles, parts);
-  if (lo != 0 || hi != 0) {
-    const unsigned long long old = atomicAdd(&A.d2lo, lo);
-    const unsigned long long carry = old + lo < old ? 1ull : 0ull;
-    if (hi != 0 || carry != 0) atomicAdd(&A.d2hi, hi + carry);
-  }
+  add_d2(A, lo, hi);
 }
 
-__device__ __forceinline__ void work_flush(AccDev* acc, int q, uint32_t n_nodes, uint32_t n_tris) {
+__device__ __forceinline__ void work_flush(AccDev* acc, int q, uint32_t n_nodes, uint32_t n_tris, int stripe) {
   if (q < 0) return;
-  if (n_nodes) atomicAdd(&acc[q].nodes, (unsigned long long)n_nodes);
-  if (n_tris) atomicAdd(&acc[q].tris, (unsigned long long)n_tris);
+  if (n_nodes) atomicAdd(&acc[q].s[stripe].nodes, (unsigned long long)n_nodes);
+  if (n_tris) atomicAdd(&acc[q].s[stripe].tris, (unsigned long long)n_tris);
 }
 
 // Work index g -> item (binary search over item starts).
@@ -1505,8 +1514,8 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
         pid = pq & ((1ull << kSlotPidBits) - 1);
         const int nq = (int)(pq >> kSlotPidBits);
         if (nq != acc.q) {
-          if (a.count_work) { work_flush(a.acc, acc.q, n_nodes, n_tris); n_nodes = n_tris = 0; }
-          lane_flush(a.acc, acc);
+          if (a.count_work) { work_flush(a.acc, acc.q, n_nodes, n_tris, acc_stripe()); n_nodes = n_tris = 0; }
+          lane_flush(a.acc, acc, acc_stripe());
           lane_reset(acc, nq);
         }
         qi = nq;
@@ -1592,8 +1601,8 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
       if (run == 0u || (uint32_t)__popc(fin) >= a.refill_at) break;
     }
   }
-  if (a.count_work) work_flush(a.acc, acc.q, n_nodes, n_tris);
-  warp_flush(a.acc, acc);
+  if (a.count_work) work_flush(a.acc, acc.q, n_nodes, n_tris, acc_stripe());
+  warp_flush(a.acc, acc, acc_stripe());
 }
 
 // ---------------------------------------------------------- set-up kernel
@@ -1795,18 +1804,38 @@ __global__ void finalize_kernel(const QueryDev* qs, const AccDev* acc, uint32_t 
   if (i >= nq) return;
   const uint32_t qi = slots != nullptr ? slots[i] : i;
   const QueryDev& q = qs[qi];
-  const AccDev& A = acc[qi];
+  // the stripes' sums; the squared-drag limbs as one exact 128-bit integer
+  const AccDev& AD = acc[qi];
+  long long F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+  unsigned long long hits = 0, hitp = 0, trunc = 0, parts = 0, nodes = 0, tris = 0, d2lo = 0, d2hi = 0;
+  for (int j = 0; j < kAccStripes; ++j) {
+    const AccStripe& A = AD.s[j];
+    for (int k = 0; k < 3; ++k) { F[k] += A.F[k]; T[k] += A.T[k]; }
+    hits += A.hits;
+    hitp += A.hit_particles;
+    trunc += A.truncated;
+    parts += A.particles;
+    nodes += A.nodes;
+    tris += A.tris;
+    const unsigned long long add_lo[3] = {A.d2[0], A.d2[1] << 30, A.d2[2] << 60};
+    const unsigned long long add_hi[3] = {0ull, A.d2[1] >> 34, A.d2[2] >> 4};
+    for (int k = 0; k < 3; ++k) {
+      const unsigned long long nlo = d2lo + add_lo[k];
+      d2hi += add_hi[k] + (nlo < d2lo ? 1ull : 0ull);
+      d2lo = nlo;
+    }
+  }
   tpmc_result r;
   memset(&r, 0, sizeof(r));
   r.status = q.status;
   if (q.status == TPMC_OK) {
-    const double Np = (double)A.particles;
+    const double Np = (double)parts;
     double sdv[3], srdv[3];
     for (int k = 0; k < 3; ++k) {
-      sdv[k] = (double)A.F[k] * q.quantum;
-      srdv[k] = (double)A.T[k] * q.quantum;
-      r.sum_dv_q[k] = A.F[k];
-      r.sum_rdv_q[k] = A.T[k];
+      sdv[k] = (double)F[k] * q.quantum;
+      srdv[k] = (double)T[k] * q.quantum;
+      r.sum_dv_q[k] = F[k];
+      r.sum_rdv_q[k] = T[k];
     }
     // force = (Gamma/N) m c sum(dv) (§II.A); C_D = F . Vhat / (q_inf A_ref) (Eq. 1)
     const double scale = Np > 0 ? q.gamma / Np * q.m * q.c_mp : 0.0;
@@ -1818,7 +1847,7 @@ __global__ void finalize_kernel(const QueryDev* qs, const AccDev* acc, uint32_t 
       r.CM[k] = r.torque[k] / (q.q_inf * q.A_ref * q.l_ref);
     }
     const double mean = Np > 0 ? (sdv[0] * q.vhat[0] + sdv[1] * q.vhat[1] + sdv[2] * q.vhat[2]) / Np : 0.0;
-    const double d2 = ((double)A.d2hi * 18446744073709551616.0 + (double)A.d2lo) * q.quantum2;
+    const double d2 = ((double)d2hi * 18446744073709551616.0 + (double)d2lo) * q.quantum2;
     const double var = Np > 1 ? fmax(0.0, (d2 - Np * mean * mean) / (Np - 1.0)) : 0.0;
     r.CD_sigma = Np > 0 ? q.gamma * q.m * q.c_mp / (q.q_inf * q.A_ref) * sqrt(var / Np) : 0.0;
     r.S = q.S;
@@ -1830,13 +1859,13 @@ __global__ void finalize_kernel(const QueryDev* qs, const AccDev* acc, uint32_t 
     r.r_cv = q.r_cv;
     for (int k = 0; k < 3; ++k) r.center[k] = q.center[k];
     r.fixed_quantum = q.quantum;
-    r.n_particles = A.particles;
-    r.n_hits = A.hits;
-    r.n_hit_particles = A.hit_particles;
-    r.n_truncated = A.truncated;
-    r.n_node_visits = A.nodes;
-    r.n_tri_tests = A.tris;
-    if (A.particles != q.N) r.status = TPMC_ECUDA;
+    r.n_particles = parts;
+    r.n_hits = hits;
+    r.n_hit_particles = hitp;
+    r.n_truncated = trunc;
+    r.n_node_visits = nodes;
+    r.n_tri_tests = tris;
+    if (parts != q.N) r.status = TPMC_ECUDA;
   }
   out[i] = r;
 }

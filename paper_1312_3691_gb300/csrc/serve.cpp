@@ -440,8 +440,9 @@ tpmc_status start_serving(Ctx* c) {
     return st;
   }
   char* p = (char*)s->d_block;
-  s->d_q = (QueryDev*)p; p += kSlots * sizeof(QueryDev);
+  // the accumulators first: cudaMalloc's alignment keeps each stripe on its own line
   s->d_acc = (AccDev*)p; p += kSlots * sizeof(AccDev);
+  s->d_q = (QueryDev*)p; p += kSlots * sizeof(QueryDev);
   const size_t per_buf_host = kSlots * (sizeof(ItemDev) + 2 * sizeof(uint32_t) + sizeof(tpmc_result)) + 64;
   if ((e = cudaMallocHost(&s->h_block, kInFlight * per_buf_host)) != cudaSuccess) {
     c->release(s->d_block);

@@ -146,14 +146,27 @@ struct ItemDev {
 };
 
 // Per-query accumulators (device, zeroed before a launch).
-struct AccDev {
+// One query's integer sums.  They are split into kAccStripes copies, each on
+// its own 128-byte line: a warp adds to the copy its index selects, so when a
+// whole grid moves on to the next query its atomics spread over several L2
+// slices instead of queueing on one line.  The final reduction adds the
+// copies (integer sums, so the split changes no result).
+constexpr int kAccStripes = 8;
+struct alignas(128) AccStripe {
   long long F[3];           // sum of (v_in - v_out), units quantum * c_mp
   long long T[3];           // sum of (r - ref) x (v_in - v_out), units quantum * m * c_mp
   unsigned long long hits, hit_particles, truncated, particles, nodes, tris;
-  // sum over particles of (their dv . Vhat)^2 in units of quantum2, as a
-  // 128-bit integer (d2hi 2^64 + d2lo): exact, so the error estimate does not
-  // depend on the order in which lanes add their sums
-  unsigned long long d2lo, d2hi;
+  // sum over particles of (their dv . Vhat)^2 in units of quantum2, as three
+  // limbs of one 128-bit integer, d2[0] + d2[1] 2^30 + d2[2] 2^60: each flush
+  // adds bits 0-29 and 30-59 of its sum to the first two and the rest to the
+  // third, with atomics that return nothing.  The total is exact and does not
+  // depend on the order of the flushes; the limbs alone do.
+  unsigned long long d2[3];
+  unsigned long long pad;
+};
+static_assert(sizeof(AccStripe) == 128, "one stripe per 128-byte line");
+struct AccDev {
+  AccStripe s[kAccStripes];
 };
 
 struct RecordsDev {
