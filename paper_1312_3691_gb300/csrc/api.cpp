@@ -161,13 +161,12 @@ LaunchCfg Ctx::schedule(const MeshRec& m, uint32_t variant, uint64_t total) {
   else if (it != tuned.end()) cfg = it->second;
   else {
     // Untuned default, from same-box sweeps on GB300 with the current kernel
-    // at the benchmark's launch size (96 cases x 1e7 particles): a tree of a
-    // few nodes (the 2-triangle plate) takes 256 threads with no register cap,
-    // 20 % faster there than 128 threads at 8 blocks per SM (in launches of
-    // 2e6 particles per case the order reverses, by 3-4 %); larger trees take
-    // 128 threads at the highest occupancy (8 blocks): the cylinder 12 %
-    // faster than 256 x 2, the satellite 7-15 % faster than 5-7 blocks.
-    cfg.block = m.dev.n_nodes <= 8 ? 256 : 128;
+    // at 96 cases x 2e6 and x 1e7 particles per launch: 128 threads at the
+    // highest occupancy (8 blocks per SM) for every tree.  Against 256 x 2
+    // (no register cap) the plate is 4-8 % faster, the cylinder 25 %, the
+    // satellite 23 %; against 6 blocks per SM the cylinder 9 % and the
+    // satellite 10 % faster, the diffuse plate 0.6 % slower.
+    cfg.block = 128;
     cfg.smem_nodes = 0;  // the hot top of the tree stays in L1; shared-memory staging costs bank conflicts
     cfg.blocks_per_sm = 0;
     cfg.chunk = 0;
@@ -195,12 +194,12 @@ tpmc_status Ctx::run(const MeshRec& m, const QueryDev* h_queries, uint32_t nq, c
                      uint32_t variant, tpmc_result* d_out, const RecordsDev* rec) {
   tpmc_status st;
   if ((st = grow(s_queries, sizeof(QueryDev) * (size_t)nq, "queries")) != TPMC_OK) return st;
-  if ((st = grow(s_acc, sizeof(AccDev) * (size_t)nq, "accumulators")) != TPMC_OK) return st;
+  if ((st = grow(s_acc, sizeof(AccStripe) * kAccStripes * (size_t)nq, "accumulators")) != TPMC_OK) return st;
   if ((st = grow(s_items, sizeof(ItemDev) * (size_t)std::max(nq, n_items), "work items")) != TPMC_OK) return st;
   if ((st = grow(s_misc, 256, "counters")) != TPMC_OK) return st;
   if ((st = grow(s_base, sizeof(QueryDev), "base query")) != TPMC_OK) return st;
   QueryDev* d_queries = (QueryDev*)s_queries.ptr;
-  AccDev* d_acc = (AccDev*)s_acc.ptr;
+  AccStripe* d_acc = (AccStripe*)s_acc.ptr;
   ItemDev* d_items = (ItemDev*)s_items.ptr;
   unsigned long long* d_counter = (unsigned long long*)s_misc.ptr;
   int* d_err = (int*)((char*)s_misc.ptr + 64);
@@ -216,7 +215,8 @@ tpmc_status Ctx::run(const MeshRec& m, const QueryDev* h_queries, uint32_t nq, c
     if ((e = cudaMemcpyAsync(d_items, h_items, sizeof(ItemDev) * n_items, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
       return cuda_fail(e, "upload items");
   }
-  if ((e = cudaMemsetAsync(d_acc, 0, sizeof(AccDev) * nq, stream)) != cudaSuccess) return cuda_fail(e, "clear acc");
+  if ((e = cudaMemsetAsync(d_acc, 0, sizeof(AccStripe) * kAccStripes * nq, stream)) != cudaSuccess)
+    return cuda_fail(e, "clear acc");
   if ((e = cudaMemsetAsync(s_misc.ptr, 0, 128, stream)) != cudaSuccess) return cuda_fail(e, "clear counter");
   if ((e = launch_setup(d_queries, nq, h_base ? (const QueryDev*)s_base.ptr : nullptr, d_dirs, d_S,
                         h_base ? d_items : nullptr, nullptr, stream)) != cudaSuccess)
@@ -225,6 +225,7 @@ tpmc_status Ctx::run(const MeshRec& m, const QueryDev* h_queries, uint32_t nq, c
   a.mesh = m.dev;
   a.queries = d_queries;
   a.acc = d_acc;
+  a.acc_stride = nq;
   a.items = d_items;
   a.n_items = h_base ? nq : n_items;
   a.total = total;
@@ -239,7 +240,7 @@ tpmc_status Ctx::run(const MeshRec& m, const QueryDev* h_queries, uint32_t nq, c
   a.refill_at = cfg.refill_at;
   last_cfg = cfg;
   if (total > 0 && (e = launch_trace(a, variant, cfg, num_sms, stream)) != cudaSuccess) return cuda_fail(e, "trace kernel");
-  if ((e = launch_finalize(d_queries, d_acc, nq, nullptr, d_out, stream)) != cudaSuccess)
+  if ((e = launch_finalize(d_queries, d_acc, nq, nq, nullptr, d_out, stream)) != cudaSuccess)
     return cuda_fail(e, "finalize kernel");
   if ((e = cudaMemcpyAsync(h_err_word, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
     return cuda_fail(e, "read error word");

@@ -1160,9 +1160,9 @@ __device__ __forceinline__ int acc_stripe() {
   return (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) & (unsigned)(kAccStripes - 1));
 }
 
-__device__ __forceinline__ void lane_flush(AccDev* acc, LaneAcc& a, int stripe) {
+__device__ __forceinline__ void lane_flush(AccStripe* acc, uint32_t stride, LaneAcc& a, int stripe) {
   if (a.q < 0 || a.particles == 0) return;
-  AccStripe& A = acc[a.q].s[stripe];
+  AccStripe& A = acc[(size_t)stripe * stride + a.q];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (a.F[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&A.F[i]), (unsigned long long)a.F[i]);
@@ -1181,10 +1181,10 @@ __device__ __forceinline__ void lane_flush(AccDev* acc, LaneAcc& a, int stripe) 
 // 128-bit sum of squares with its carry) and one lane issues the atomics;
 // lanes of mixed queries flush one by one.  Integer sums, so the result is
 // the same either way.
-__device__ __forceinline__ void warp_flush(AccDev* acc, LaneAcc& a, int stripe) {
+__device__ __forceinline__ void warp_flush(AccStripe* acc, uint32_t stride, LaneAcc& a, int stripe) {
   const unsigned same = __match_any_sync(kFull, a.q);
   if (same != kFull || a.q < 0) {
-    lane_flush(acc, a, stripe);
+    lane_flush(acc, stride, a, stripe);
     return;
   }
   long long F[3], T[3];
@@ -1209,7 +1209,7 @@ __device__ __forceinline__ void warp_flush(AccDev* acc, LaneAcc& a, int stripe) 
     parts += __shfl_xor_sync(kFull, parts, m);
   }
   if ((threadIdx.x & 31u) != 0u || parts == 0) return;
-  AccStripe& A = acc[a.q].s[stripe];
+  AccStripe& A = acc[(size_t)stripe * stride + a.q];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (F[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&A.F[i]), (unsigned long long)F[i]);
@@ -1222,10 +1222,12 @@ __device__ __forceinline__ void warp_flush(AccDev* acc, LaneAcc& a, int stripe) 
   add_d2(A, lo, hi);
 }
 
-__device__ __forceinline__ void work_flush(AccDev* acc, int q, uint32_t n_nodes, uint32_t n_tris, int stripe) {
+__device__ __forceinline__ void work_flush(AccStripe* acc, uint32_t stride, int q, uint32_t n_nodes, uint32_t n_tris,
+                                           int stripe) {
   if (q < 0) return;
-  if (n_nodes) atomicAdd(&acc[q].s[stripe].nodes, (unsigned long long)n_nodes);
-  if (n_tris) atomicAdd(&acc[q].s[stripe].tris, (unsigned long long)n_tris);
+  AccStripe& A = acc[(size_t)stripe * stride + q];
+  if (n_nodes) atomicAdd(&A.nodes, (unsigned long long)n_nodes);
+  if (n_tris) atomicAdd(&A.tris, (unsigned long long)n_tris);
 }
 
 // Work index g -> item (binary search over item starts).
@@ -1514,8 +1516,11 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
         pid = pq & ((1ull << kSlotPidBits) - 1);
         const int nq = (int)(pq >> kSlotPidBits);
         if (nq != acc.q) {
-          if (a.count_work) { work_flush(a.acc, acc.q, n_nodes, n_tris, acc_stripe()); n_nodes = n_tris = 0; }
-          lane_flush(a.acc, acc, acc_stripe());
+          if (a.count_work) {
+            work_flush(a.acc, a.acc_stride, acc.q, n_nodes, n_tris, acc_stripe());
+            n_nodes = n_tris = 0;
+          }
+          lane_flush(a.acc, a.acc_stride, acc, acc_stripe());
           lane_reset(acc, nq);
         }
         qi = nq;
@@ -1601,8 +1606,8 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
       if (run == 0u || (uint32_t)__popc(fin) >= a.refill_at) break;
     }
   }
-  if (a.count_work) work_flush(a.acc, acc.q, n_nodes, n_tris, acc_stripe());
-  warp_flush(a.acc, acc, acc_stripe());
+  if (a.count_work) work_flush(a.acc, a.acc_stride, acc.q, n_nodes, n_tris, acc_stripe());
+  warp_flush(a.acc, a.acc_stride, acc, acc_stripe());
 }
 
 // ---------------------------------------------------------- set-up kernel
@@ -1798,18 +1803,17 @@ __global__ void vn_table_kernel(float* tab) {
 
 // -------------------------------------------------------- final reduction
 // Thread i reduces query slots[i] (or i) into out[i].
-__global__ void finalize_kernel(const QueryDev* qs, const AccDev* acc, uint32_t nq, const uint32_t* slots,
-                                tpmc_result* out) {
+__global__ void finalize_kernel(const QueryDev* qs, const AccStripe* acc, uint32_t stride, uint32_t nq,
+                                const uint32_t* slots, tpmc_result* out) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nq) return;
   const uint32_t qi = slots != nullptr ? slots[i] : i;
   const QueryDev& q = qs[qi];
   // the stripes' sums; the squared-drag limbs as one exact 128-bit integer
-  const AccDev& AD = acc[qi];
   long long F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
   unsigned long long hits = 0, hitp = 0, trunc = 0, parts = 0, nodes = 0, tris = 0, d2lo = 0, d2hi = 0;
   for (int j = 0; j < kAccStripes; ++j) {
-    const AccStripe& A = AD.s[j];
+    const AccStripe& A = acc[(size_t)j * stride + qi];
     for (int k = 0; k < 3; ++k) { F[k] += A.F[k]; T[k] += A.T[k]; }
     hits += A.hits;
     hitp += A.hit_particles;
@@ -1985,10 +1989,10 @@ cudaError_t launch_trace(const TraceArgs& args, uint32_t variant, const LaunchCf
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const QueryDev* d_queries, const AccDev* d_acc, uint32_t nq, const uint32_t* d_slots,
-                            tpmc_result* d_out, cudaStream_t stream) {
+cudaError_t launch_finalize(const QueryDev* d_queries, const AccStripe* d_acc, uint32_t acc_stride, uint32_t nq,
+                            const uint32_t* d_slots, tpmc_result* d_out, cudaStream_t stream) {
   if (nq == 0) return cudaSuccess;
-  finalize_kernel<<<(nq + 127) / 128, 128, 0, stream>>>(d_queries, d_acc, nq, d_slots, d_out);
+  finalize_kernel<<<(nq + 127) / 128, 128, 0, stream>>>(d_queries, d_acc, acc_stride, nq, d_slots, d_out);
   return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ constexpr uint32_t kNoAllocMaxQueries = 64;
 struct NoAllocArea {
   QueryDev base;
   QueryDev queries[kNoAllocMaxQueries];
-  AccDev acc[kNoAllocMaxQueries];
+  AccStripe acc[kAccStripes * kNoAllocMaxQueries];  // stripe-major, kNoAllocMaxQueries slots per stripe
   ItemDev items[kNoAllocMaxQueries];
   double dirs[3 * kNoAllocMaxQueries];
   double S[kNoAllocMaxQueries];
@@ -96,7 +96,7 @@ extern "C" tpmc_status tpmc_sweep_noalloc(tpmc_ctx* ctx, tpmc_mesh_id mesh, cons
     e = cudaMemcpyAsync(A->dirs, h_dirs, (size_t)K * 3 * sizeof(double), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && h_S) e = cudaMemcpyAsync(A->S, h_S, (size_t)K * sizeof(double), cudaMemcpyHostToDevice, s);
   // the array keeps the previous call's contents: clear the sums, the work counter and the error word
-  if (e == cudaSuccess) e = cudaMemsetAsync(A->acc, 0, (size_t)K * sizeof(AccDev), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A->acc, 0, sizeof(A->acc), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(&A->counter, 0, sizeof(unsigned long long) + 2 * sizeof(int), s);
   if (e != cudaSuccess) return cuda_fail(e, "tpmc_sweep_noalloc inputs");
   if ((e = launch_setup(A->queries, K, &A->base, h_dirs ? A->dirs : nullptr, h_S ? A->S : nullptr, A->items, nullptr,
@@ -106,6 +106,7 @@ extern "C" tpmc_status tpmc_sweep_noalloc(tpmc_ctx* ctx, tpmc_mesh_id mesh, cons
   a.mesh = m.dev;
   a.queries = A->queries;
   a.acc = A->acc;
+  a.acc_stride = kNoAllocMaxQueries;
   a.items = A->items;
   a.n_items = K;
   a.total = (uint64_t)K * N_each;
@@ -118,7 +119,7 @@ extern "C" tpmc_status tpmc_sweep_noalloc(tpmc_ctx* ctx, tpmc_mesh_id mesh, cons
   a.smem_nodes = cfg.smem_nodes;
   a.refill_at = cfg.refill_at;
   if ((e = launch_trace(a, trace_variant(base, m.dev), cfg, c->num_sms, s)) != cudaSuccess) return cuda_fail(e, "trace kernel");
-  if ((e = launch_finalize(A->queries, A->acc, K, nullptr, A->results, s)) != cudaSuccess)
+  if ((e = launch_finalize(A->queries, A->acc, kNoAllocMaxQueries, K, nullptr, A->results, s)) != cudaSuccess)
     return cuda_fail(e, "finalize kernel");
   int err_word = 0;
   e = cudaMemcpyAsync(h_out, A->results, (size_t)K * sizeof(tpmc_result), cudaMemcpyDeviceToHost, s);

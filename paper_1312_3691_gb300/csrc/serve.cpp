@@ -102,7 +102,7 @@ struct ServeState {
   std::map<tpmc_query_id, Request*> all;
   std::vector<Request*> slots;
   QueryDev* d_q = nullptr;
-  AccDev* d_acc = nullptr;
+  AccStripe* d_acc = nullptr;  // stripe-major, kSlots query slots per stripe
   StepBuf buf[kInFlight];
   std::deque<int> inflight;    // buffer indices, oldest first
   void* d_block = nullptr;
@@ -207,7 +207,8 @@ bool enqueue_step(ServeState* s, int b, int prev, const std::vector<Request*>& c
       r->q.panel = (long long*)r->d_panel;
       B.h_fresh[n_fresh++] = (uint32_t)r->slot;
       if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_q + r->slot, &r->q, sizeof(QueryDev), cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess) e = cudaMemsetAsync(s->d_acc + r->slot, 0, sizeof(AccDev), st);
+      for (int j = 0; j < kAccStripes && e == cudaSuccess; ++j)
+        e = cudaMemsetAsync(s->d_acc + (size_t)j * kSlots + r->slot, 0, sizeof(AccStripe), st);
       if (e == cudaSuccess && r->d_panel)
         e = cudaMemsetAsync(r->d_panel, 0, (size_t)r->n_tri * 3 * sizeof(long long), st);
       r->set_up = true;
@@ -256,6 +257,7 @@ bool enqueue_step(ServeState* s, int b, int prev, const std::vector<Request*>& c
     a.mesh = md;
     a.queries = s->d_q;
     a.acc = s->d_acc;
+    a.acc_stride = kSlots;
     a.items = B.d_items + first_item;
     a.n_items = n_items - first_item;
     a.total = g;
@@ -280,7 +282,7 @@ bool enqueue_step(ServeState* s, int b, int prev, const std::vector<Request*>& c
   if (!B.finishing.empty() && e == cudaSuccess) {
     e = cudaMemcpyAsync(B.d_fin, B.h_fin, B.finishing.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-      e = launch_finalize(s->d_q, s->d_acc, (uint32_t)B.finishing.size(), B.d_fin, B.d_res, st);
+      e = launch_finalize(s->d_q, s->d_acc, kSlots, (uint32_t)B.finishing.size(), B.d_fin, B.d_res, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(B.h_res, B.d_res, B.finishing.size() * sizeof(tpmc_result), cudaMemcpyDeviceToHost, st);
   }
@@ -432,7 +434,7 @@ tpmc_status start_serving(Ctx* c) {
   }
   const size_t per_buf_dev = kSlots * (sizeof(ItemDev) + 2 * sizeof(uint32_t) + sizeof(tpmc_result)) +
                              kMaxGroups * sizeof(unsigned long long) + 256;
-  const size_t dev_bytes = kSlots * (sizeof(QueryDev) + sizeof(AccDev)) + kInFlight * per_buf_dev + 256;
+  const size_t dev_bytes = kSlots * (sizeof(QueryDev) + kAccStripes * sizeof(AccStripe)) + kInFlight * per_buf_dev + 256;
   tpmc_status st = c->alloc(&s->d_block, dev_bytes, "serving slots");
   if (st != TPMC_OK) {
     destroy_streams(s);
@@ -441,7 +443,7 @@ tpmc_status start_serving(Ctx* c) {
   }
   char* p = (char*)s->d_block;
   // the accumulators first: cudaMalloc's alignment keeps each stripe on its own line
-  s->d_acc = (AccDev*)p; p += kSlots * sizeof(AccDev);
+  s->d_acc = (AccStripe*)p; p += kSlots * kAccStripes * sizeof(AccStripe);
   s->d_q = (QueryDev*)p; p += kSlots * sizeof(QueryDev);
   const size_t per_buf_host = kSlots * (sizeof(ItemDev) + 2 * sizeof(uint32_t) + sizeof(tpmc_result)) + 64;
   if ((e = cudaMallocHost(&s->h_block, kInFlight * per_buf_host)) != cudaSuccess) {

@@ -146,11 +146,15 @@ struct ItemDev {
 };
 
 // Per-query accumulators (device, zeroed before a launch).
-// One query's integer sums.  They are split into kAccStripes copies, each on
-// its own 128-byte line: a warp adds to the copy its index selects, so when a
+// One query's integer sums, kept as kAccStripes copies ("stripes") of one
+// 128-byte line each: a warp adds to the stripe its index selects, so when a
 // whole grid moves on to the next query its atomics spread over several L2
-// slices instead of queueing on one line.  The final reduction adds the
-// copies (integer sums, so the split changes no result).
+// slices instead of queueing on one line.  The array is stripe-major: stripe
+// j of query q is acc[j * stride + q], stride being the array's number of
+// query slots, so a query's stripes lie stride * 128 bytes apart wherever the
+// array starts (with a query's stripes in one 1 KB block the launches ran
+// 15-35 % slower at one alignment of the block than at the other).  The final
+// reduction adds the stripes (integer sums, so the split changes no result).
 constexpr int kAccStripes = 8;
 struct alignas(128) AccStripe {
   long long F[3];           // sum of (v_in - v_out), units quantum * c_mp
@@ -165,9 +169,6 @@ struct alignas(128) AccStripe {
   unsigned long long pad;
 };
 static_assert(sizeof(AccStripe) == 128, "one stripe per 128-byte line");
-struct AccDev {
-  AccStripe s[kAccStripes];
-};
 
 struct RecordsDev {
   double* pos = nullptr;
@@ -182,7 +183,8 @@ struct RecordsDev {
 struct TraceArgs {
   MeshDev mesh;
   const QueryDev* queries;
-  AccDev* acc;
+  AccStripe* acc;             // stripe-major: stripe j of query q at acc[j * acc_stride + q]
+  uint32_t acc_stride;
   const ItemDev* items;
   uint32_t n_items;
   uint32_t chunk;             // ids a warp takes per fetch
@@ -223,8 +225,8 @@ cudaError_t launch_setup(QueryDev* d_queries, uint32_t nq, const QueryDev* d_bas
 cudaError_t launch_vn_table(float* d_table, cudaStream_t stream);
 cudaError_t launch_trace(const TraceArgs& args, uint32_t variant, const LaunchCfg& cfg, int num_sms,
                          cudaStream_t stream);
-cudaError_t launch_finalize(const QueryDev* d_queries, const AccDev* d_acc, uint32_t nq, const uint32_t* d_slots,
-                            tpmc_result* d_out, cudaStream_t stream);
+cudaError_t launch_finalize(const QueryDev* d_queries, const AccStripe* d_acc, uint32_t acc_stride, uint32_t nq,
+                            const uint32_t* d_slots, tpmc_result* d_out, cudaStream_t stream);
 cudaError_t launch_panels(const QueryDev* d_query, const long long* d_panel, const float4* frames,
                           const double* frames64, uint32_t n_tri, double* d_pressure, double* d_shear,
                           cudaStream_t stream);
