@@ -215,11 +215,10 @@ tpmc_status Ctx::run(const MeshRec& m, const QueryDev* h_queries, uint32_t nq, c
     if ((e = cudaMemcpyAsync(d_items, h_items, sizeof(ItemDev) * n_items, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
       return cuda_fail(e, "upload items");
   }
-  if ((e = cudaMemsetAsync(d_acc, 0, sizeof(AccStripe) * kAccStripes * nq, stream)) != cudaSuccess)
-    return cuda_fail(e, "clear acc");
   if ((e = cudaMemsetAsync(s_misc.ptr, 0, 128, stream)) != cudaSuccess) return cuda_fail(e, "clear counter");
+  // the set-up also clears the queries' accumulators
   if ((e = launch_setup(d_queries, nq, h_base ? (const QueryDev*)s_base.ptr : nullptr, d_dirs, d_S,
-                        h_base ? d_items : nullptr, nullptr, stream)) != cudaSuccess)
+                        h_base ? d_items : nullptr, nullptr, d_acc, nq, stream)) != cudaSuccess)
     return cuda_fail(e, "setup kernel");
   TraceArgs a{};
   a.mesh = m.dev;

@@ -1625,8 +1625,12 @@ __device__ double latitude_pdf_d(double x, double S, double D) {
 // Philox stream is base->stream_id + b; with `items` set, it also writes work
 // item b = particles [0, N) of query b at work indices [b N, (b+1) N).
 __global__ void setup_kernel(QueryDev* qs, const QueryDev* base, const double* dirs, const double* Svals,
-                             ItemDev* items, const uint32_t* slots) {
-  QueryDev& q = qs[slots != nullptr ? slots[blockIdx.x] : blockIdx.x];
+                             ItemDev* items, const uint32_t* slots, AccStripe* acc, uint32_t acc_stride) {
+  const uint32_t slot = slots != nullptr ? slots[blockIdx.x] : blockIdx.x;
+  QueryDev& q = qs[slot];
+  // the query's sums start at zero: its kAccStripes stripes of 16 words each
+  for (uint32_t i = threadIdx.x; i < (uint32_t)kAccStripes * 16u; i += blockDim.x)
+    reinterpret_cast<unsigned long long*>(&acc[(size_t)(i >> 4) * acc_stride + slot])[i & 15u] = 0ull;
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     int st = TPMC_OK;
@@ -1898,9 +1902,10 @@ __global__ void panels_kernel(const QueryDev* q, const long long* panel, const d
 
 // ------------------------------------------------------------- launchers
 cudaError_t launch_setup(QueryDev* d_queries, uint32_t nq, const QueryDev* d_base, const double* d_dirs,
-                         const double* d_S, ItemDev* d_items, const uint32_t* d_slots, cudaStream_t stream) {
+                         const double* d_S, ItemDev* d_items, const uint32_t* d_slots, AccStripe* d_acc,
+                         uint32_t acc_stride, cudaStream_t stream) {
   if (nq == 0) return cudaSuccess;
-  setup_kernel<<<nq, 160, 0, stream>>>(d_queries, d_base, d_dirs, d_S, d_items, d_slots);
+  setup_kernel<<<nq, 160, 0, stream>>>(d_queries, d_base, d_dirs, d_S, d_items, d_slots, d_acc, acc_stride);
   return cudaGetLastError();
 }
 

@@ -95,12 +95,12 @@ extern "C" tpmc_status tpmc_sweep_noalloc(tpmc_ctx* ctx, tpmc_mesh_id mesh, cons
   if (e == cudaSuccess && h_dirs)
     e = cudaMemcpyAsync(A->dirs, h_dirs, (size_t)K * 3 * sizeof(double), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && h_S) e = cudaMemcpyAsync(A->S, h_S, (size_t)K * sizeof(double), cudaMemcpyHostToDevice, s);
-  // the array keeps the previous call's contents: clear the sums, the work counter and the error word
-  if (e == cudaSuccess) e = cudaMemsetAsync(A->acc, 0, sizeof(A->acc), s);
+  // the array keeps the previous call's contents: clear the work counter and the error word (the
+  // set-up clears the sums)
   if (e == cudaSuccess) e = cudaMemsetAsync(&A->counter, 0, sizeof(unsigned long long) + 2 * sizeof(int), s);
   if (e != cudaSuccess) return cuda_fail(e, "tpmc_sweep_noalloc inputs");
   if ((e = launch_setup(A->queries, K, &A->base, h_dirs ? A->dirs : nullptr, h_S ? A->S : nullptr, A->items, nullptr,
-                        s)) != cudaSuccess)
+                        A->acc, kNoAllocMaxQueries, s)) != cudaSuccess)
     return cuda_fail(e, "setup kernel");
   TraceArgs a{};
   a.mesh = m.dev;

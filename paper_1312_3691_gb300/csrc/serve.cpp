@@ -27,6 +27,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <thread>
 #include <vector>
 
 #include "runtime.h"
@@ -207,15 +208,15 @@ bool enqueue_step(ServeState* s, int b, int prev, const std::vector<Request*>& c
       r->q.panel = (long long*)r->d_panel;
       B.h_fresh[n_fresh++] = (uint32_t)r->slot;
       if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_q + r->slot, &r->q, sizeof(QueryDev), cudaMemcpyHostToDevice, st);
-      for (int j = 0; j < kAccStripes && e == cudaSuccess; ++j)
-        e = cudaMemsetAsync(s->d_acc + (size_t)j * kSlots + r->slot, 0, sizeof(AccStripe), st);
       if (e == cudaSuccess && r->d_panel)
         e = cudaMemsetAsync(r->d_panel, 0, (size_t)r->n_tri * 3 * sizeof(long long), st);
       r->set_up = true;
     }
   if (n_fresh > 0 && e == cudaSuccess) {
     e = cudaMemcpyAsync(B.d_fresh, B.h_fresh, n_fresh * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_setup(s->d_q, n_fresh, nullptr, nullptr, nullptr, nullptr, B.d_fresh, st);
+    // the set-up also clears the fresh slots' accumulators
+    if (e == cudaSuccess)
+      e = launch_setup(s->d_q, n_fresh, nullptr, nullptr, nullptr, nullptr, B.d_fresh, s->d_acc, kSlots, st);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(B.d_counters, 0, kMaxGroups * sizeof(unsigned long long), st);
   // the groups run on their own streams once the set-up is done, so that one
@@ -297,7 +298,12 @@ void retire_step(ServeState* s, cudaError_t e_enqueue) {
   const int b = s->inflight.front();
   StepBuf& B = s->buf[b];
   cudaError_t e = e_enqueue;
-  if (e == cudaSuccess) e = cudaEventSynchronize(B.ev);
+  // Poll rather than sleep on the event: a blocking wait wakes through an
+  // interrupt, tens of microseconds after the step ends, and that delay lands
+  // on every query's latency.  The loop thread has a core to itself.
+  if (e == cudaSuccess) {
+    while ((e = cudaEventQuery(B.ev)) == cudaErrorNotReady) std::this_thread::yield();
+  }
   ++s->steps;
   const Clock::time_point now = Clock::now();
   std::unique_lock<std::mutex> lk(s->m);
@@ -418,7 +424,7 @@ tpmc_status start_serving(Ctx* c) {
   cudaError_t e = cudaSuccess;
   for (int b = 0; b < kInFlight && e == cudaSuccess; ++b) {
     StepBuf& B = s->buf[b];
-    e = cudaEventCreateWithFlags(&B.ev, cudaEventBlockingSync | cudaEventDisableTiming);
+    e = cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B.ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B.traces_done, cudaEventDisableTiming);

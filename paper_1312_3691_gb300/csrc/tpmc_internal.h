@@ -220,8 +220,11 @@ inline uint32_t trace_variant(const tpmc_params* p, const MeshDev& m) {
 inline uint32_t variant_width(uint32_t v) { return (v & kVariantWide8) ? 8u : ((v & kVariantWide4) ? 4u : 2u); }
 inline uint32_t node_float4s(uint32_t width) { return width == 8 ? 5u : (width == 4 ? 4u : 2u); }
 
+// Set-up of nq queries (block i: slot slots[i], or i), which also clears
+// their accumulator stripes in acc (stripe-major, acc_stride slots per stripe).
 cudaError_t launch_setup(QueryDev* d_queries, uint32_t nq, const QueryDev* d_base, const double* d_dirs,
-                         const double* d_S, ItemDev* d_items, const uint32_t* d_slots, cudaStream_t stream);
+                         const double* d_S, ItemDev* d_items, const uint32_t* d_slots, AccStripe* d_acc,
+                         uint32_t acc_stride, cudaStream_t stream);
 cudaError_t launch_vn_table(float* d_table, cudaStream_t stream);
 cudaError_t launch_trace(const TraceArgs& args, uint32_t variant, const LaunchCfg& cfg, int num_sms,
                          cudaStream_t stream);
