@@ -266,7 +266,8 @@ tpmc_status tpmc_trace_records(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_para
 
 /* Batched sweep: K queries that differ from `base` only in flow direction and
  * speed ratio, in one persistent launch.  h_dirs: host [K][3]; h_S: host [K]
- * speed ratios (V = S c_mp); item k uses stream_id = base->stream_id + k.
+ * speed ratios (V = S c_mp); either may be NULL, and then every item takes
+ * base's direction or speed.  Item k uses stream_id = base->stream_id + k.
  * Per-panel loads are not kept.  Results in h_out[K].
  * Errors as tpmc_trace; EINVAL for K = 0 or K > 2^24. */
 tpmc_status tpmc_sweep(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* base, const double* h_dirs,

@@ -7,7 +7,7 @@ grown by an earlier allocating call could hide an allocation of theirs; the
 context's allocation count and bytes must not move across them.  They run
 twice in a row (the second must not inherit the first's sums from the shared
 scratch), with speed ratios given and with speed ratios taken from the base
-query (h_S = NULL).
+query (h_S = NULL), and once with the directions taken from it (h_dirs = NULL).
 
 This file is collected last on purpose: a failure here leaves every other
 test already run."""
@@ -54,15 +54,20 @@ def test_noalloc_sweep_matches_the_allocating_sweep_twice():
         before = T.tpmc_memory_info(ctx)
         got = [T.tpmc_sweep_noalloc(ctx, mesh, base, dirs, S, N_each) for _ in range(2)]
         got_noS = [T.tpmc_sweep_noalloc(ctx, mesh, base, dirs[:5], None, N_each) for _ in range(2)]
+        got_nodir = T.tpmc_sweep_noalloc(ctx, mesh, base, None, S[:4], N_each)
         after = T.tpmc_memory_info(ctx)
         assert after["n_allocs"] == before["n_allocs"] and after["used"] == before["used"], (before, after)
         ref = T.tpmc_sweep(ctx, mesh, base, dirs, S, N_each)
         ref_noS = T.tpmc_sweep(ctx, mesh, base, dirs[:5], None, N_each)
+        ref_nodir = T.tpmc_sweep(ctx, mesh, base, None, S[:4], N_each)
         for g in got:
             _same(g, ref, N_each)
         for g in got_noS:
             _same(g, ref_noS, N_each)
             assert all(abs(r["S"] - 7.0) < 1e-12 for r in g)
+        # without directions every item flies along the base query's direction
+        _same(got_nodir, ref_nodir, N_each)
+        assert all(abs(r["S"] - x) < 1e-12 for r, x in zip(got_nodir, S[:4]))
         with pytest.raises(T.TpmcError) as e:
             T.tpmc_sweep_noalloc(ctx, mesh, base, W.attitude_grid(9, 8), np.full(72, 5.0), 10)
         assert e.value.status == T.TPMC_EINVAL
