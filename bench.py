@@ -283,7 +283,8 @@ def cpu_baseline_and_cd_error(results_by_group, budget_s=12.0):
                 err = abs(r["CD"] - ref)
                 if r["CD_sigma"] > 0:
                     zs.append(err / r["CD_sigma"])
-                within.append(err <= 1e-4 * abs(ref) + 3.0 * r["CD_sigma"])
+                # 1e-12: the flow edge-on to the specular plate, where drag and sigma both vanish
+                within.append(err <= 1e-4 * abs(ref) + 3.0 * r["CD_sigma"] + 1e-12)
                 rels.append(err / max(abs(ref), 1e-12))
         cd = {"reference": "oracle panel-sum expectation (exact for these convex meshes)",
               "n_cases": len(rels), "max_abs_z": max(zs) if zs else None,
