@@ -3,7 +3,7 @@
 //   setup_kernel     FP64: free-stream set-up per query (Nomenclature; Eq. 10
 //                    flux; particle weight, §II.A), Rodrigues matrix (Eq. 15),
 //                    fixed-point scale, start table of the latitude inverse CDF.
-//   trace_kernel<R, MINB, CLL, W>
+//   trace_kernel<R, MINB, CLL, W, COUNT>
 //                    persistent, one warp = 32 particle slots refilled from a
 //                    global work counter by ballot; per slot: Philox draws,
 //                    seeding (Eq. 11, Eq. 14a-c, Eq. 15; or the box CV),
@@ -11,7 +11,9 @@
 //                    (§II.A), Maxwell (or, with CLL, Cercignani-Lampis-Lord)
 //                    re-emission, int64 fixed-point momentum sums, until the
 //                    particle misses or reaches max_bounces.  R = float (FP32
-//                    path) or double; MINB = register-capped occupancy.
+//                    path) or double; MINB = register-capped occupancy; CLL:
+//                    with the CLL branch; W: BVH width; COUNT: with the
+//                    node-visit and triangle-test counters.
 //   finalize_kernel  FP64 reduction to force, torque, C_D and its error.
 //   panels_kernel    FP64 per-triangle pressure and shear.
 //
@@ -1368,7 +1370,7 @@ __device__ __forceinline__ void begin_trav(Ray<R>& r, TV& tv, const MeshDev& m) 
   }
 }
 
-template <typename R, int MINB, bool CLL, int W>
+template <typename R, int MINB, bool CLL, int W, bool COUNT>
 __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeof(R) == 4 ? 2 : 1))
     trace_kernel(TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1530,7 +1532,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
         pid = pq & ((1ull << kSlotPidBits) - 1);
         const int nq = (int)(pq >> kSlotPidBits);
         if (nq != acc.q) {
-          if (a.count_work) {
+          if constexpr (COUNT) {
             work_flush(a.acc, a.acc_stride, acc.q, n_nodes, n_tris, acc_stripe());
             n_nodes = n_tris = 0;
           }
@@ -1621,7 +1623,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
       if (run == 0u || (uint32_t)__popc(fin) >= a.refill_at) break;
     }
   }
-  if (a.count_work) work_flush(a.acc, a.acc_stride, acc.q, n_nodes, n_tris, acc_stripe());
+  if constexpr (COUNT) work_flush(a.acc, a.acc_stride, acc.q, n_nodes, n_tris, acc_stripe());
   warp_flush(a.acc, a.acc_stride, acc, acc_stripe());
 }
 
@@ -1943,20 +1945,26 @@ using TraceFn = void (*)(TraceArgs);
 
 // Kernel instantiation for a schedule: the register-capped float variants
 // serve 128-thread blocks at 5 to 8 blocks per SM.
-template <bool CLL, int W>
+template <bool CLL, int W, bool COUNT>
 TraceFn pick_trace_t(uint32_t precision, uint32_t block, uint32_t blocks_per_sm) {
-  if (precision == TPMC_FP64) return trace_kernel<double, 0, CLL, W>;
-  if (block <= 128 && blocks_per_sm >= 8) return trace_kernel<float, 8, CLL, W>;
-  if (block <= 128 && blocks_per_sm == 7) return trace_kernel<float, 7, CLL, W>;
-  if (block <= 128 && blocks_per_sm == 6) return trace_kernel<float, 6, CLL, W>;
-  if (block <= 128 && blocks_per_sm == 5) return trace_kernel<float, 5, CLL, W>;
-  return trace_kernel<float, 0, CLL, W>;
+  if (precision == TPMC_FP64) return trace_kernel<double, 0, CLL, W, COUNT>;
+  if (block <= 128 && blocks_per_sm >= 8) return trace_kernel<float, 8, CLL, W, COUNT>;
+  if (block <= 128 && blocks_per_sm == 7) return trace_kernel<float, 7, CLL, W, COUNT>;
+  if (block <= 128 && blocks_per_sm == 6) return trace_kernel<float, 6, CLL, W, COUNT>;
+  if (block <= 128 && blocks_per_sm == 5) return trace_kernel<float, 5, CLL, W, COUNT>;
+  return trace_kernel<float, 0, CLL, W, COUNT>;
+}
+
+template <int W, bool COUNT>
+TraceFn pick_trace_c(uint32_t variant, uint32_t block, uint32_t blocks_per_sm) {
+  return (variant & kVariantCll) ? pick_trace_t<true, W, COUNT>(variant & 1u, block, blocks_per_sm)
+                                 : pick_trace_t<false, W, COUNT>(variant & 1u, block, blocks_per_sm);
 }
 
 template <int W>
 TraceFn pick_trace_w(uint32_t variant, uint32_t block, uint32_t blocks_per_sm) {
-  return (variant & kVariantCll) ? pick_trace_t<true, W>(variant & 1u, block, blocks_per_sm)
-                                 : pick_trace_t<false, W>(variant & 1u, block, blocks_per_sm);
+  return (variant & kVariantCount) ? pick_trace_c<W, true>(variant, block, blocks_per_sm)
+                                   : pick_trace_c<W, false>(variant, block, blocks_per_sm);
 }
 
 TraceFn pick_trace(uint32_t variant, uint32_t block, uint32_t blocks_per_sm) {
@@ -1997,9 +2005,11 @@ int trace_max_blocks_per_sm(uint32_t variant, const LaunchCfg& cfg, uint32_t n_n
 
 cudaError_t launch_trace(const TraceArgs& args, uint32_t variant, const LaunchCfg& cfg, int num_sms,
                          cudaStream_t stream) {
-  // the mesh's own layout decides which traversal reads its nodes
-  variant = (variant & ~(kVariantWide4 | kVariantWide8)) |
-            (args.mesh.width == 8 ? kVariantWide8 : (args.mesh.width == 4 ? kVariantWide4 : 0u));
+  // the mesh's own layout decides which traversal reads its nodes, and the
+  // launch's counting flag whether the counters are compiled in
+  variant = (variant & ~(kVariantWide4 | kVariantWide8 | kVariantCount)) |
+            (args.mesh.width == 8 ? kVariantWide8 : (args.mesh.width == 4 ? kVariantWide4 : 0u)) |
+            (args.count_work ? kVariantCount : 0u);
   const size_t smem = trace_smem_bytes(cfg, args.mesh.n_nodes, variant);
   const uint32_t grid = (uint32_t)num_sms * cfg.blocks_per_sm;
   const TraceFn f = pick_trace(variant, cfg.block, cfg.blocks_per_sm);

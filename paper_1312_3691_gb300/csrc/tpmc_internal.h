@@ -203,16 +203,20 @@ struct LaunchCfg {
   uint32_t blocks_per_sm = 4;
   uint32_t chunk = 0;
   uint32_t smem_nodes = 0;
-  uint32_t refill_at = 0;      // 0: the default (24)
+  uint32_t refill_at = 0;      // 0: the default (16)
 };
 
 // ------------------------------------------------------------ host launchers
 // Trace-kernel variant: the precision (TPMC_FP32 / TPMC_FP64), plus
 // kVariantCll when the launch holds a query with the CLL surface model (so
 // that launches without one run code compiled without that branch), plus the
-// mesh's BVH layout (kVariantWide4 / kVariantWide8 for compressed wide nodes).
+// mesh's BVH layout (kVariantWide4 / kVariantWide8 for compressed wide nodes),
+// plus kVariantCount when the launch counts node visits and triangle tests
+// (launches that do not count run code without the two counters, which the
+// 64-register build otherwise keeps live through the traversal loop).
 constexpr uint32_t kVariantCll = 2u;
 constexpr uint32_t kVariantWide4 = 4u, kVariantWide8 = 8u;
+constexpr uint32_t kVariantCount = 16u;
 inline uint32_t trace_variant(const tpmc_params* p, const MeshDev& m) {
   return p->precision | (p->gsi_model == TPMC_GSI_CLL ? kVariantCll : 0u) |
          (m.width == 8 ? kVariantWide8 : (m.width == 4 ? kVariantWide4 : 0u));
