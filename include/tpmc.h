@@ -105,7 +105,7 @@ typedef struct {
   double ref_point[3];  /* torque reference point, m                                    */
   double r_cv;          /* CV radius, m; <= 0: 1.05 x the mesh's bounding radius       */
   double center[3];     /* CV centre, m (ignored when r_cv <= 0: bounding-sphere centre) */
-  uint32_t max_bounces; /* hits per particle before it is stopped (>= 1), e.g. 64      */
+  uint32_t max_bounces; /* hits per particle before it is stopped, 1 to 2^24-1, e.g. 64 */
   uint32_t precision;   /* TPMC_FP32 or TPMC_FP64                                       */
   uint64_t seed;        /* Philox key                                                   */
   uint32_t stream_id;   /* Philox counter word 2 (distinguishes runs sharing a seed)   */
@@ -235,9 +235,9 @@ tpmc_status tpmc_mesh_info(tpmc_ctx* ctx, tpmc_mesh_id mesh, tpmc_mesh_stats* ou
  * Particle ids 0..N-1 index the Philox counters, so the result depends only
  * on (mesh, params, N), never on the schedule.
  * Errors: EINVAL (non-finite or non-positive n, T_inf, m, V, T_W, A_ref; eps
- * outside [0,1]; zero dir; max_bounces = 0; N = 0 or N > 2^34; a mesh vertex
- * outside the given CV; a fixed-point overflow bound that no quantum >= 2^-40
- * satisfies), ENOTFOUND, ENOMEM, ECUDA. */
+ * outside [0,1]; zero dir; max_bounces = 0 or above 2^24 - 1; N = 0 or
+ * N > 2^34; a mesh vertex outside the given CV; a fixed-point overflow bound
+ * that no quantum >= 2^-40 satisfies), ENOTFOUND, ENOMEM, ECUDA. */
 tpmc_status tpmc_trace(tpmc_ctx* ctx, tpmc_mesh_id mesh, const tpmc_params* params, uint64_t N,
                        tpmc_result* out);
 

@@ -79,7 +79,9 @@ tpmc_status validate_params(const tpmc_params* p) {
   for (int i = 0; i < 3; ++i)
     if (!std::isfinite(p->ref_point[i]) || !std::isfinite(p->center[i])) return fail(TPMC_EINVAL, "non-finite point");
   if (!std::isfinite(p->r_cv)) return fail(TPMC_EINVAL, "r_cv must be finite");
-  if (p->max_bounces < 1) return fail(TPMC_EINVAL, "max_bounces must be >= 1");
+  // the trace kernel keeps a particle's hit count in 24 bits beside its id
+  if (p->max_bounces < 1 || p->max_bounces > (1u << 24) - 1)
+    return fail(TPMC_EINVAL, "max_bounces must be in [1, 2^24 - 1]");
   if (p->precision != TPMC_FP32 && p->precision != TPMC_FP64) return fail(TPMC_EINVAL, "unknown precision");
   if (p->cv_kind > TPMC_CV_BOX_MAXWELL) return fail(TPMC_EINVAL, "unknown cv_kind");
   if (!std::isfinite(p->l_ref)) return fail(TPMC_EINVAL, "l_ref must be finite");

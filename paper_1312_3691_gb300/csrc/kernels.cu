@@ -1136,6 +1136,9 @@ struct LaneAcc {
   uint32_t hits, hit_particles, truncated, particles;
   int q;
   uint32_t d2hi;
+  // the lane's particle: its id (bits 0-39) and the hits so far (bits 40-63),
+  // kept here rather than in registers the traversal loop needs
+  unsigned long long pb;
 };
 
 __device__ __forceinline__ void lane_reset(LaneAcc& a, int q) {
@@ -1401,9 +1404,8 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
 
   // lane's particle
   bool has = false, tdone = true;
-  uint64_t pid = 0;
   int qi = -1;
-  uint32_t bounce = 0, last = 0xFFFFFFFFu;
+  uint32_t last = 0xFFFFFFFFu;
   R dvp[3] = {0, 0, 0};
   Ray<R> ray;
   using TV = std::conditional_t<(W > 2), TravW<R>, Trav<R>>;
@@ -1416,6 +1418,8 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
     // ---- 1. lanes whose ray is finished: re-emit, or finish the particle
     if (has && tdone) {
       const QueryDev& q = a.queries[qi];
+      const uint64_t pid = acc.pb & ((1ull << kSlotPidBits) - 1);
+      uint32_t bounce = (uint32_t)(acc.pb >> kSlotPidBits);
       bool finish = true;
       if (tv.best != 0xFFFFFFFFu) {
         const uint32_t hit = tv.best;
@@ -1450,6 +1454,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
         ++acc.hits;
         if (bounce == 0) ++acc.hit_particles;
         ++bounce;
+        acc.pb += 1ull << kSlotPidBits;
         last = hit;
         if (bounce >= q.max_bounces) {
           ++acc.truncated;
@@ -1529,7 +1534,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
       if (((need >> lane) & 1u) && rank < take) {
         R pos[3], vel[3];
         const uint64_t pq = slot_load<R>(queue[(q_head + rank) & (kQueue - 1)], pos, vel);
-        pid = pq & ((1ull << kSlotPidBits) - 1);
+        const uint64_t pid = pq & ((1ull << kSlotPidBits) - 1);
         const int nq = (int)(pq >> kSlotPidBits);
         if (nq != acc.q) {
           if constexpr (COUNT) {
@@ -1546,7 +1551,7 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
         begin_trav<W>(ray, tv, a.mesh);
         tdone = a.mesh.n_nodes == 0;
         has = true;
-        bounce = 0;
+        acc.pb = pid;  // no hits yet
         last = 0xFFFFFFFFu;
         dvp[0] = dvp[1] = dvp[2] = (R)0;
         if (!ray_meets_box<R>(ray, a.mesh)) {

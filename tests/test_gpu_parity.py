@@ -259,7 +259,7 @@ def test_invalid_arguments_are_rejected(T, ctx):
     good = dict(**W.base_state(), dir=(0, 0, 1), eps_diffuse=1.0, A_ref=1.0, r_cv=1.5)
     try:
         for bad in [dict(n=-1.0), dict(V=float("nan")), dict(eps_diffuse=1.5), dict(dir=(0, 0, 0)),
-                    dict(r_cv=0.5), dict(max_bounces=0), dict(A_ref=0.0)]:
+                    dict(r_cv=0.5), dict(max_bounces=0), dict(max_bounces=1 << 24), dict(A_ref=0.0)]:
             with pytest.raises(T.TpmcError) as e:
                 T.tpmc_trace(ctx, mesh, T.make_params(**{**good, **bad}), 100)
             assert e.value.status == T.TPMC_EINVAL
@@ -272,8 +272,10 @@ def test_invalid_arguments_are_rejected(T, ctx):
         with pytest.raises(T.TpmcError) as e:
             T.tpmc_mesh_load(ctx, xyz, np.array([[0, 1, 10_000]], np.uint32))
         assert e.value.status == T.TPMC_EINVAL
-        # the context is still usable after the errors
+        # the context is still usable after the errors, and the largest bounce limit is accepted
         res = T.tpmc_trace(ctx, mesh, T.make_params(**good), 1000)
+        assert res["n_particles"] == 1000
+        res = T.tpmc_trace(ctx, mesh, T.make_params(**{**good, "max_bounces": (1 << 24) - 1}), 1000)
         assert res["n_particles"] == 1000
     finally:
         T.tpmc_mesh_unload(ctx, mesh)
