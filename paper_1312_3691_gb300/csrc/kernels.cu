@@ -13,7 +13,8 @@
 //                    particle misses or reaches max_bounces.  R = float (FP32
 //                    path) or double; MINB = register-capped occupancy; CLL:
 //                    with the CLL branch; W: BVH width; COUNT: with the
-//                    node-visit and triangle-test counters.
+//                    node-visit and triangle-test counters and the
+//                    per-particle records (verification launches).
 //   finalize_kernel  FP64 reduction to force, torque, C_D and its error.
 //   panels_kernel    FP64 per-triangle pressure and shear.
 //
@@ -1406,7 +1407,8 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
   bool has = false, tdone = true;
   int qi = -1;
   uint32_t last = 0xFFFFFFFFu;
-  R dvp[3] = {0, 0, 0};
+  R dvp[3] = {0, 0, 0};  // the particle's summed momentum change (records only)
+  R dpart = 0;           // its drag component, summed over its hits (for sigma)
   Ray<R> ray;
   using TV = std::conditional_t<(W > 2), TravW<R>, Trav<R>>;
   using SE = std::conditional_t<(W > 2), uint2, StackE<R>>;
@@ -1431,7 +1433,11 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
         reemit<R, CLL>(q, HitConst<R>::cw(q), pid, bounce, nrm, t1, v);
         R dv[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) { dv[i] = v_in[i] - v[i]; dvp[i] += dv[i]; }
+        for (int i = 0; i < 3; ++i) {
+          dv[i] = v_in[i] - v[i];
+          if constexpr (COUNT) dvp[i] += dv[i];
+        }
+        dpart += dv[0] * HitConst<R>::vhat(q, 0) + dv[1] * HitConst<R>::vhat(q, 1) + dv[2] * HitConst<R>::vhat(q, 2);
         const R r0 = hp[0] - HitConst<R>::ref(q, 0), r1 = hp[1] - HitConst<R>::ref(q, 1),
                 r2 = hp[2] - HitConst<R>::ref(q, 2);
         const R tq[3] = {r1 * dv[2] - r2 * dv[1], r2 * dv[0] - r0 * dv[2], r0 * dv[1] - r1 * dv[0]};
@@ -1450,7 +1456,8 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
           for (int i = 0; i < 3; ++i)
             if (qf[i]) atomicAdd(reinterpret_cast<unsigned long long*>(pp + i), (unsigned long long)qf[i]);
         }
-        if (a.rec.tri != nullptr && bounce < a.rec.K) a.rec.tri[(size_t)pid * a.rec.K + bounce] = hit;
+        if constexpr (COUNT)
+          if (a.rec.tri != nullptr && bounce < a.rec.K) a.rec.tri[(size_t)pid * a.rec.K + bounce] = hit;
         ++acc.hits;
         if (bounce == 0) ++acc.hit_particles;
         ++bounce;
@@ -1476,12 +1483,9 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
         }
       }
       if (finish) {
-        R d = 0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) d += dvp[i] * HitConst<R>::vhat(q, i);
-        if (d != (R)0) lane_add_d2(acc, quantize_sq(d * d * HitConst<R>::scale2(q)));
+        if (dpart != (R)0) lane_add_d2(acc, quantize_sq(dpart * dpart * HitConst<R>::scale2(q)));
         ++acc.particles;
-        if (a.rec.n_hits != nullptr) {
+        if (COUNT && a.rec.n_hits != nullptr) {
           a.rec.n_hits[pid] = bounce;
           a.rec.truncated[pid] = (tv.best != 0xFFFFFFFFu && bounce >= q.max_bounces) ? 1u : 0u;
 #pragma unroll
@@ -1554,9 +1558,10 @@ __global__ void __launch_bounds__(MINB > 0 ? 128 : 256, MINB > 0 ? MINB : (sizeo
         acc.pb = pid;  // no hits yet
         last = 0xFFFFFFFFu;
         dvp[0] = dvp[1] = dvp[2] = (R)0;
+        dpart = (R)0;
         if (!ray_meets_box<R>(ray, a.mesh)) {
           ++acc.particles;
-          if (a.rec.n_hits != nullptr) {
+          if (COUNT && a.rec.n_hits != nullptr) {
             a.rec.n_hits[pid] = 0;
             a.rec.truncated[pid] = 0;
 #pragma unroll
@@ -2014,7 +2019,7 @@ cudaError_t launch_trace(const TraceArgs& args, uint32_t variant, const LaunchCf
   // launch's counting flag whether the counters are compiled in
   variant = (variant & ~(kVariantWide4 | kVariantWide8 | kVariantCount)) |
             (args.mesh.width == 8 ? kVariantWide8 : (args.mesh.width == 4 ? kVariantWide4 : 0u)) |
-            (args.count_work ? kVariantCount : 0u);
+            (args.count_work || args.rec.n_hits != nullptr || args.rec.tri != nullptr ? kVariantCount : 0u);
   const size_t smem = trace_smem_bytes(cfg, args.mesh.n_nodes, variant);
   const uint32_t grid = (uint32_t)num_sms * cfg.blocks_per_sm;
   const TraceFn f = pick_trace(variant, cfg.block, cfg.blocks_per_sm);

@@ -211,8 +211,9 @@ struct LaunchCfg {
 // kVariantCll when the launch holds a query with the CLL surface model (so
 // that launches without one run code compiled without that branch), plus the
 // mesh's BVH layout (kVariantWide4 / kVariantWide8 for compressed wide nodes),
-// plus kVariantCount when the launch counts node visits and triangle tests
-// (launches that do not count run code without the two counters, which the
+// plus kVariantCount when the launch counts node visits and triangle tests or
+// writes per-particle records (launches that do neither run code without the
+// two counters and without each particle's momentum-change vector, which the
 // 64-register build otherwise keeps live through the traversal loop).
 constexpr uint32_t kVariantCll = 2u;
 constexpr uint32_t kVariantWide4 = 4u, kVariantWide8 = 8u;
