@@ -321,7 +321,16 @@ def test_results_are_deterministic_and_schedule_independent(T, ctx):
         assert r["n_hits"] == r1["n_hits"] and r["n_truncated"] == r1["n_truncated"]
 
 
+def _same_physics(a, b):
+    for k in ("sum_dv_q", "sum_rdv_q", "n_hits", "n_hit_particles", "n_truncated", "n_particles", "CD", "CD_sigma"):
+        assert a[k] == b[k], (k, a[k], b[k])
+
+
 def test_counters_count_traversal_work(T, ctx):
+    """Launches that count or write records run their own kernel build (with
+    the counters and each particle's momentum-change vector); the physics must
+    not depend on it: the same integer sums and sigma bit for bit, on a convex
+    body and on the multi-bounce satellite."""
     xyz, tri = M.cylinder()
     mesh = T.tpmc_mesh_load(ctx, xyz, tri)
     try:
@@ -334,7 +343,23 @@ def test_counters_count_traversal_work(T, ctx):
         T.tpmc_mesh_unload(ctx, mesh)
     segs = r["n_particles"] + r["n_hits"]
     assert r["n_node_visits"] >= segs and r["n_tri_tests"] > 0
-    assert r0["n_node_visits"] == 0 and r0["sum_dv_q"] == r["sum_dv_q"]
+    assert r0["n_node_visits"] == 0
+    _same_physics(r, r0)
+    case = W.satellite_case(N=60_011)
+    mesh = T.tpmc_mesh_load(ctx, case["xyz"], case["tri"])
+    try:
+        p = T.make_params(**case["params"])
+        plain = T.tpmc_trace(ctx, mesh, p, case["N"])
+        T.tpmc_set_counters(ctx, True)
+        counted = T.tpmc_trace(ctx, mesh, p, case["N"])
+        T.tpmc_set_counters(ctx, False)
+        recorded, rec = T.tpmc_trace_records(ctx, mesh, p, case["N"], K=8)
+    finally:
+        T.tpmc_mesh_unload(ctx, mesh)
+    assert plain["n_hits"] > plain["n_hit_particles"]  # some particles hit more than once
+    _same_physics(plain, counted)
+    _same_physics(plain, recorded)
+    assert int(rec["n_hits"].sum()) == plain["n_hits"]
 
 
 # ------------------------------------------------------- sweep and serving
